@@ -1,0 +1,349 @@
+/*
+ * lbm_oracle.c -- plain, slow FP64 CPU reference of the hybrid lattice
+ * Boltzmann Bloch-Torrey scheme (Naughton, Tennyson & Georgiadis,
+ * arXiv 1907.00908).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle the CUDA path is checked
+ * against.  It shares no code, header, table or helper with the library under
+ * paper_1907_00908_gb300/; only tests, the smoke check and the CPU-baseline leg
+ * of the benchmark load it.  It is deliberately unoptimised: every step of one
+ * time step is a separate sweep over the lattice, in the order the paper gives
+ * (Eq. LBM_process_list_2): collision -> boundary/buffer layers -> streaming
+ * (with the half-link membrane rule) -> reaction.
+ *
+ * Lattice: D3Q7, directions 0=(0,0,0), 1=+x, 2=-x, 3=+y, 4=-y, 5=+z, 6=-z.
+ * Weights: the paper gives D2Q5 only (Sec. 2.3: omega_0 = eps_D, omega_i =
+ * eps_D/2, eps_D = 1/3).  For D3Q7 the same pattern with the isotropy
+ * condition sum_i omega_i e_ia e_ib = eps_D delta_ab gives eps_D = 1/4,
+ * omega_0 = 1/4, omega_1..6 = 1/8; this reproduces the tau = 0.58 the paper
+ * quotes for its 3-D code (Sec. 3.5: D = 2.0, dt = 0.010, dx = 1.0).
+ *
+ * Grid: nx*ny*nz unique nodes, x fastest; node n sits at x_n = n*dx.
+ * A periodic axis of N nodes has period L = N*dx (the paper's node N, which
+ * duplicates node 0, is dropped).  Buffer layers at n = -1 and n = N are held
+ * explicitly in a padded copy of the post-collision state.
+ *
+ * Units: um, ms.  gG[a] = gamma*G0_a in rad/(um*ms); D in um^2/ms; T2 in ms
+ * (INFINITY allowed); kappa in um/ms (0 = impermeable, INFINITY = no membrane).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+enum { Q = 7 };
+static const int EX[Q] = {0, 1, -1, 0, 0, 0, 0};
+static const int EY[Q] = {0, 0, 0, 1, -1, 0, 0};
+static const int EZ[Q] = {0, 0, 0, 0, 0, 1, -1};
+static const int OPP[Q] = {0, 2, 1, 4, 3, 6, 5};
+/* D3Q7: eps_D = 1/4, omega_0 = eps_D, omega_i = eps_D / 2 (Sec. 2.3 weights) */
+static const double EPS_D = 0.25;
+static const double W[Q] = {0.25, 0.125, 0.125, 0.125, 0.125, 0.125, 0.125};
+
+enum { BC_PERIODIC = 0, BC_MIRROR = 1 };
+
+/* Reflection of a lattice direction across a face normal to axis a: the axis-a
+ * component flips, the others are unchanged.  For the direction that crosses
+ * the face this is the opposite direction i-bar (Sec. 2.4.4). */
+static int reflect_dir(int i, int axis)
+{
+    int e[3] = {EX[i], EY[i], EZ[i]};
+    e[axis] = -e[axis];
+    for (int j = 0; j < Q; ++j)
+        if (EX[j] == e[0] && EY[j] == e[1] && EZ[j] == e[2]) return j;
+    return -1;
+}
+
+/* Padded layout: (nx+2) x (ny+2) x (nz+2) nodes, coordinate -1..N on each
+ * axis; Q complex populations per node. */
+typedef struct {
+    int nx, ny, nz;
+    int px, py, pz;
+} grid_t;
+
+static size_t pidx(const grid_t* g, int x, int y, int z)
+{
+    return ((size_t)(z + 1) * g->py + (size_t)(y + 1)) * g->px + (size_t)(x + 1);
+}
+
+static size_t sidx(const grid_t* g, int x, int y, int z)
+{
+    return ((size_t)z * g->ny + (size_t)y) * g->nx + (size_t)x;
+}
+
+/* Eq. tau_def: tau = 1/2 + dt*D / (eps_D dx^2). */
+static double tau_of(double D, double dt, double dx)
+{
+    return 0.5 + dt * D / (EPS_D * dx * dx);
+}
+
+/* Eqs. P_def and B5: P = eps_D dx / (2 kappa dt); reflected share r = P/(1+P),
+ * transmitted share s = 1/(1+P).  kappa = 0 -> P = inf (bounce-back);
+ * kappa = inf -> P = 0 (plain streaming). */
+static void membrane_shares(double kappa, double dt, double dx, double* r, double* s)
+{
+    if (kappa == 0.0) { *r = 1.0; *s = 0.0; return; }
+    if (isinf(kappa)) { *r = 0.0; *s = 1.0; return; }
+    double P = EPS_D * dx / (2.0 * kappa * dt);
+    *r = P / (1.0 + P);
+    *s = 1.0 / (1.0 + P);
+}
+
+/* Scalar parameters as the oracle derives them: out = {tau, r, s}. */
+void lbm_oracle_params(double D, double dt, double dx, double kappa, double* out)
+{
+    out[0] = tau_of(D, dt, dx);
+    membrane_shares(kappa, dt, dx, &out[1], &out[2]);
+}
+
+/*
+ * Membrane/phase mask, the oracle's own builder.  Encoding (shared contract
+ * with the library, each side written independently):
+ *   bit (i-1), i = 1..6: the link from x to its neighbour x + e_i is a
+ *     membrane, i.e. that neighbour exists (a periodic wrap counts; a mirror
+ *     face has no neighbour) and its compartment label differs from x's
+ *     (half-link membranes on every label change, Sec. 2.4.2 with
+ *     Delta_m = 0.5, theta = 0);
+ *   bits 6-7: phase id phase_of_label[label[x]] (0..3).
+ */
+int lbm_oracle_mask(int nx, int ny, int nz, const int32_t* labels, int n_labels,
+                    const uint8_t* phase_of_label, const int* bc, uint8_t* mask_out)
+{
+    grid_t g = {nx, ny, nz, nx + 2, ny + 2, nz + 2};
+    int dims[3] = {nx, ny, nz};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t s = sidx(&g, x, y, z);
+                int32_t L = labels[s];
+                if (L < 0 || L >= n_labels) return -1;
+                if (phase_of_label[L] > 3) return -1;
+                unsigned m = (unsigned)phase_of_label[L] << 6;
+                for (int i = 1; i < Q; ++i) {
+                    int c[3] = {x + EX[i], y + EY[i], z + EZ[i]};
+                    int inside = 1;
+                    for (int a = 0; a < 3; ++a) {
+                        if (c[a] < 0 || c[a] >= dims[a]) {
+                            if (bc[a] == BC_PERIODIC)
+                                c[a] = (c[a] + dims[a]) % dims[a];
+                            else
+                                inside = 0;
+                        }
+                    }
+                    if (!inside) continue;
+                    if (labels[sidx(&g, c[0], c[1], c[2])] != L) m |= 1u << (i - 1);
+                }
+                mask_out[s] = (uint8_t)m;
+            }
+    return 0;
+}
+
+/*
+ * One complete run from the initial condition M = 1 + 0i (Sec. 2.1) to
+ * t = n_steps * dt.
+ *
+ * f[k] is the waveform sample used during step k (G(t^k) = G0 f(t^k),
+ * Eq. reaction_LBM); the periodic phase uses F_k = sum_{m<k} f[m] dt
+ * (Eq. periodic_phi).
+ *
+ * Outputs (each may be NULL):
+ *   Z_out[2]          : sum over sites of M(x, t^K), K = n_steps (Re, Im);
+ *   field_out[2N]     : M(x, t^K) per site (Re, Im interleaved);
+ *   series_out[2K]    : sum over sites of M(x, t^{k+1}) after each step;
+ *   state_out[2*7*N]  : g_i(x, t^K) per site, direction-major within a site.
+ * Returns 0, or -1 on invalid input.
+ */
+int lbm_oracle_run(int nx, int ny, int nz, double dx,
+                   const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
+                   const int* bc, int n_phases, const double* D, const double* T2,
+                   double kappa, double dt, long n_steps, const double* f,
+                   const double* gG, int n_threads,
+                   double* Z_out, double* field_out, double* series_out, double* state_out)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0) return -1;
+    if (n_phases < 1 || n_phases > 4) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (bc[a] != BC_PERIODIC && bc[a] != BC_MIRROR) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    grid_t g = {nx, ny, nz, nx + 2, ny + 2, nz + 2};
+    const int dims[3] = {nx, ny, nz};
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t NP = (size_t)g.px * g.py * g.pz;
+
+    for (size_t s = 0; s < N; ++s) {
+        if (labels[s] < 0 || labels[s] >= n_labels) return -1;
+        if (phase_of_label[labels[s]] >= n_phases) return -1;
+    }
+
+    /* Mirror BC with a gradient that is neither normal nor parallel to the
+     * face is not covered by the paper (Sec. 2.4.4). */
+    int mirror_conj[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        if (bc[a] != BC_MIRROR || gG[a] == 0.0) continue;
+        for (int b = 0; b < 3; ++b)
+            if (b != a && gG[b] != 0.0) return -1;
+        mirror_conj[a] = 1;
+    }
+
+    double tau[4], decay[4];
+    for (int p = 0; p < n_phases; ++p) {
+        if (!(D[p] > 0.0)) return -1;
+        tau[p] = tau_of(D[p], dt, dx);
+        decay[p] = exp(-dt / T2[p]); /* T2 = inf -> 1 */
+    }
+    double r, s;
+    membrane_shares(kappa, dt, dx, &r, &s);
+
+    cplx* gs = malloc(sizeof(cplx) * Q * N);     /* g_i(x, t^k)             */
+    cplx* gh = malloc(sizeof(cplx) * Q * NP);    /* hat g_i with buffers    */
+    int32_t* lab = malloc(sizeof(int32_t) * NP); /* labels with buffers     */
+    uint8_t* ph = malloc(N);
+    if (!gs || !gh || !lab || !ph) { free(gs); free(gh); free(lab); free(ph); return -1; }
+
+    /* Labels of the buffer nodes: periodic -> the wrapped node; mirror -> the
+     * boundary node itself (Sec. 2.4.4: the buffer node's geometry equals the
+     * boundary node's), so a mirror face is never a membrane. */
+    for (size_t i = 0; i < NP; ++i) lab[i] = -1;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                lab[pidx(&g, x, y, z)] = labels[sidx(&g, x, y, z)];
+                ph[sidx(&g, x, y, z)] = phase_of_label[labels[sidx(&g, x, y, z)]];
+            }
+    for (int a = 0; a < 3; ++a) {
+        int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+        for (int u = 0; u < dims[o2]; ++u)
+            for (int v = 0; v < dims[o1]; ++v) {
+                int lo[3], hi[3], slo[3], shi[3];
+                lo[a] = -1; hi[a] = dims[a];
+                lo[o1] = hi[o1] = slo[o1] = shi[o1] = v;
+                lo[o2] = hi[o2] = slo[o2] = shi[o2] = u;
+                if (bc[a] == BC_PERIODIC) { slo[a] = dims[a] - 1; shi[a] = 0; }
+                else { slo[a] = 0; shi[a] = dims[a] - 1; }
+                lab[pidx(&g, lo[0], lo[1], lo[2])] = labels[sidx(&g, slo[0], slo[1], slo[2])];
+                lab[pidx(&g, hi[0], hi[1], hi[2])] = labels[sidx(&g, shi[0], shi[1], shi[2])];
+            }
+    }
+
+    /* Initial condition M = 1 + 0i at equilibrium: g_i = omega_i M (Eq. g_eq). */
+    for (size_t x = 0; x < N; ++x)
+        for (int i = 0; i < Q; ++i) gs[x * Q + i] = W[i];
+
+    double F = 0.0; /* F_k = sum_{m<k} f_m dt */
+    for (long k = 0; k < n_steps; ++k) {
+        /* 1. Collision (Eq. collision_LBM), M = sum_i g_i (Eq. M'summation). */
+#pragma omp parallel for
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t si = sidx(&g, x, y, z), pi = pidx(&g, x, y, z);
+                    cplx M = 0;
+                    for (int i = 0; i < Q; ++i) M += gs[si * Q + i];
+                    double t = tau[ph[si]];
+                    for (int i = 0; i < Q; ++i) {
+                        cplx gi = gs[si * Q + i];
+                        gh[pi * Q + i] = gi - (gi - W[i] * M) / t;
+                    }
+                }
+
+        /* 2. Buffer layers (Sec. 2.4.3 Eq. collision_BC; Sec. 2.4.4). */
+        for (int a = 0; a < 3; ++a) {
+            int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+            double L = dims[a] * dx;
+            double phi = gG[a] * L * F; /* Eq. periodic_phi, per axis */
+            cplx wrap_lo = cexp(I * phi), wrap_hi = cexp(-I * phi);
+            /* mirror, G normal to the face: hat g_i(x_m) =
+             * conj( hat g_ibar(x_n) exp(i gamma (x_n + x_m - 2 x_o).G0 F) ),
+             * origin x_o = 0 (where G0.x = 0). */
+            double xlo = (0 + (-1)) * dx, xhi = ((dims[a] - 1) + dims[a]) * dx;
+            cplx rot_lo = cexp(I * gG[a] * xlo * F), rot_hi = cexp(I * gG[a] * xhi * F);
+            for (int u = 0; u < dims[o2]; ++u)
+                for (int v = 0; v < dims[o1]; ++v) {
+                    int lo[3], hi[3], c0[3], cN[3];
+                    lo[a] = -1; hi[a] = dims[a]; c0[a] = 0; cN[a] = dims[a] - 1;
+                    lo[o1] = hi[o1] = c0[o1] = cN[o1] = v;
+                    lo[o2] = hi[o2] = c0[o2] = cN[o2] = u;
+                    size_t plo = pidx(&g, lo[0], lo[1], lo[2]), phi_ = pidx(&g, hi[0], hi[1], hi[2]);
+                    size_t p0 = pidx(&g, c0[0], c0[1], c0[2]), pN = pidx(&g, cN[0], cN[1], cN[2]);
+                    for (int i = 0; i < Q; ++i) {
+                        if (bc[a] == BC_PERIODIC) {
+                            gh[plo * Q + i] = wrap_lo * gh[pN * Q + i];
+                            gh[phi_ * Q + i] = wrap_hi * gh[p0 * Q + i];
+                        } else {
+                            int ri = reflect_dir(i, a);
+                            if (mirror_conj[a]) {
+                                gh[plo * Q + i] = conj(gh[p0 * Q + ri] * rot_lo);
+                                gh[phi_ * Q + i] = conj(gh[pN * Q + ri] * rot_hi);
+                            } else {
+                                gh[plo * Q + i] = gh[p0 * Q + ri];
+                                gh[phi_ * Q + i] = gh[pN * Q + ri];
+                            }
+                        }
+                    }
+                }
+        }
+
+        /* 3. Streaming (Eq. streaming_LBM), with the half-link membrane rule
+         *    on links whose end nodes carry different labels (Eqs. B2a_text,
+         *    B2b_text with the B5 coefficients): the population arriving at x
+         *    in direction i is s * (what streams in) + r * (what x sent out
+         *    towards the membrane, reflected). */
+        /* 4. Reaction (Eq. reaction_LBM), x_n = n dx. */
+        double fk = f[k];
+#pragma omp parallel for
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    size_t si = sidx(&g, x, y, z), pi = pidx(&g, x, y, z);
+                    int Lx = lab[pi];
+                    cplx gbar[Q];
+                    gbar[0] = gh[pi * Q + 0];
+                    for (int i = 1; i < Q; ++i) {
+                        size_t py_ = pidx(&g, x - EX[i], y - EY[i], z - EZ[i]);
+                        if (lab[py_] != Lx)
+                            gbar[i] = s * gh[py_ * Q + i] + r * gh[pi * Q + OPP[i]];
+                        else
+                            gbar[i] = gh[py_ * Q + i];
+                    }
+                    double xdotG = (x * dx) * gG[0] + (y * dx) * gG[1] + (z * dx) * gG[2];
+                    cplx fac = cexp(-I * xdotG * fk * dt) * decay[ph[si]];
+                    for (int i = 0; i < Q; ++i) gs[si * Q + i] = fac * gbar[i];
+                }
+        F += fk * dt;
+
+        if (series_out) {
+            cplx Z = 0;
+            for (size_t x = 0; x < N; ++x)
+                for (int i = 0; i < Q; ++i) Z += gs[x * Q + i];
+            series_out[2 * k] = creal(Z);
+            series_out[2 * k + 1] = cimag(Z);
+        }
+    }
+
+    /* 5. Signal: Z = sum_x M(x, t^K) (Sec. 2.1: S from the summed M). */
+    cplx Z = 0;
+    for (size_t x = 0; x < N; ++x) {
+        cplx M = 0;
+        for (int i = 0; i < Q; ++i) M += gs[x * Q + i];
+        Z += M;
+        if (field_out) { field_out[2 * x] = creal(M); field_out[2 * x + 1] = cimag(M); }
+        if (state_out)
+            for (int i = 0; i < Q; ++i) {
+                state_out[2 * (x * Q + i)] = creal(gs[x * Q + i]);
+                state_out[2 * (x * Q + i) + 1] = cimag(gs[x * Q + i]);
+            }
+    }
+    if (Z_out) { Z_out[0] = creal(Z); Z_out[1] = cimag(Z); }
+    free(gs); free(gh); free(lab); free(ph);
+    return 0;
+}

@@ -1,0 +1,280 @@
+"""Seeded synthetic tissue geometries and gradient-direction sets.
+
+This module only makes inputs: int32 compartment-label volumes (x fastest,
+shape [nz, ny, nx]) with a phase id per label, and direction / b-value lists.
+It holds none of the lattice scheme's arithmetic, so the CUDA path and the
+FP64 oracle can both be fed from it.  Every generator is deterministic in its
+seed (numpy PCG64).
+
+Node n of an axis sits at x_n = n*dx, the lattice convention of the solver.
+
+Geometries follow the tissue models of the paper (Sec. 2.1: fibres in an
+extracellular matrix; Sec. 3.5: z-aligned cylinders; Sec. 3.8: cells from a
+micrograph, here replaced by a Voronoi tessellation):
+
+* ``planes``     -- parallel slabs normal to one axis (restricted-diffusion tests)
+* ``cylinders``  -- non-overlapping z-aligned cylinders, gamma-distributed radii
+* ``spheres``    -- non-overlapping sphere pack, uniform radii
+* ``voronoi_tissue`` -- Voronoi cells + extracellular band + vessel tubes
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+PHASE_EX = 0  # extracellular
+PHASE_IN = 1  # intracellular
+
+
+@dataclass
+class Geometry:
+    labels: np.ndarray            # int32 [nz, ny, nx]
+    phase_of_label: np.ndarray    # uint8 [n_labels]
+    dx: float
+    info: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return self.labels.shape
+
+    @property
+    def n_sites(self):
+        return int(self.labels.size)
+
+    def phase_fractions(self, n_phases=None):
+        ph = self.phase_of_label[self.labels]
+        n = n_phases or int(self.phase_of_label.max()) + 1
+        return np.bincount(ph.ravel(), minlength=n) / ph.size
+
+
+def uniform(n, dx=1.0):
+    """Single compartment, single phase: free diffusion."""
+    nz, ny, nx = (n, n, n) if np.isscalar(n) else n
+    return Geometry(np.zeros((nz, ny, nx), np.int32), np.zeros(1, np.uint8), dx, {"kind": "uniform"})
+
+
+def planes(shape, dx, widths, axis=0, phases=None):
+    """Slabs normal to ``axis`` (0 = x); slab j has ``widths[j]`` nodes and label j.
+
+    The walls sit at the half-links between slabs, so slab j is
+    ``widths[j]*dx`` thick.  The widths repeat to fill the axis.
+    """
+    nz, ny, nx = shape
+    n_ax = (nx, ny, nz)[axis]
+    lab1 = np.empty(n_ax, np.int32)
+    pos, j = 0, 0
+    while pos < n_ax:
+        w = widths[j % len(widths)]
+        lab1[pos:pos + w] = j
+        pos += w
+        j += 1
+    n_labels = j
+    if axis == 0:
+        labels = np.broadcast_to(lab1[None, None, :], shape)
+    elif axis == 1:
+        labels = np.broadcast_to(lab1[None, :, None], shape)
+    else:
+        labels = np.broadcast_to(lab1[:, None, None], shape)
+    if phases is None:
+        pol = np.zeros(n_labels, np.uint8)
+    else:
+        pol = np.array([phases[i % len(phases)] for i in range(n_labels)], np.uint8)
+    return Geometry(np.ascontiguousarray(labels, np.int32), pol, dx, {"kind": "planes", "widths": list(widths)})
+
+
+def _relax_periodic(centers, radii, box, gap, max_iter=4000, rng=None):
+    """Place discs/spheres without overlap in a periodic box.
+
+    Radii are grown from 60 % to full size in steps; after each growth step
+    overlapping pairs are pushed apart along their centre line (minimum
+    image) until none overlap.  Returns the centres and the iterations used.
+    """
+    c = centers.copy()
+    dim = c.shape[1]
+    total = 0
+    for scale in np.linspace(0.6, 1.0, 9):
+        rad = radii * scale
+        for it in range(max_iter):
+            d = c[:, None, :] - c[None, :, :]
+            d -= box * np.round(d / box)
+            dist = np.sqrt((d * d).sum(-1))
+            need = rad[:, None] + rad[None, :] + gap
+            np.fill_diagonal(dist, np.inf)
+            if (dist >= need).all():
+                break
+            ov = need + 1e-6 - dist  # push slightly past contact
+            ov[ov < 0] = 0.0
+            total += 1
+            dist_safe = np.where(dist > 1e-12, dist, 1.0)
+            u = d / dist_safe[..., None]
+            coinc = dist < 1e-12
+            if coinc.any() and rng is not None:
+                rnd = rng.normal(size=u.shape)
+                rnd /= np.linalg.norm(rnd, axis=-1, keepdims=True)
+                u = np.where(coinc[..., None], rnd, u)
+            w = rad[None, :] ** dim / (rad[:, None] ** dim + rad[None, :] ** dim)
+            c += 0.55 * ((ov * w)[..., None] * u).sum(1)
+            c %= box
+        else:
+            raise RuntimeError("packing relaxation did not converge; lower the target fraction")
+    return c, total
+
+
+def cylinders(n, dx, mean_radius=3.0, cv=0.3, fraction=0.6, seed=0, gap=None):
+    """z-aligned non-overlapping cylinders in a periodic n x n x n box.
+
+    Radii ~ Gamma(shape 1/cv^2, scale mean*cv^2), sampled until the summed
+    cross-section reaches ``fraction`` of the box area, then placed at random
+    and relaxed until no two overlap (periodic).  Label 0 = extracellular,
+    label j >= 1 = cylinder j (phase 1).  The achieved voxel fraction is in
+    ``info``.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = n * dx
+    gap = 0.0 if gap is None else gap
+    k = 1.0 / (cv * cv)
+    radii = []
+    area = 0.0
+    while area < fraction * L * L:
+        r = float(rng.gamma(k, mean_radius / k))
+        r = min(max(r, 2.0 * dx), 0.3 * L)
+        radii.append(r)
+        area += math.pi * r * r
+    radii = np.array(sorted(radii, reverse=True))
+    # trim the last disc so the analytic fraction is not overshot by much
+    centers = rng.uniform(0, L, size=(len(radii), 2))
+    centers, iters = _relax_periodic(centers, radii, L, gap, rng=rng)
+    ys = np.arange(n) * dx
+    lab2 = np.zeros((n, n), np.int32)
+    for j, (c, r) in enumerate(zip(centers, radii)):
+        dxv = ys[None, :] - c[0]
+        dyv = ys[:, None] - c[1]
+        dxv -= L * np.round(dxv / L)
+        dyv -= L * np.round(dyv / L)
+        inside = dxv * dxv + dyv * dyv < r * r
+        lab2[inside & (lab2 == 0)] = j + 1
+    labels = np.ascontiguousarray(np.broadcast_to(lab2[None], (n, n, n)), np.int32)
+    pol = np.full(len(radii) + 1, PHASE_IN, np.uint8)
+    pol[0] = PHASE_EX
+    g = Geometry(labels, pol, dx, {"kind": "cylinders", "n_cyl": len(radii), "seed": seed,
+                                   "target_fraction": fraction, "relax_iters": iters})
+    g.info["intra_fraction"] = float((lab2 > 0).mean())
+    return g
+
+
+def spheres(n, dx, rmin=2.0, rmax=6.0, fraction=0.5, seed=0, gap=None):
+    """Non-overlapping sphere pack in a periodic n^3 box, radii ~ U(rmin, rmax).
+
+    Label 0 = extracellular, label j >= 1 = sphere j (phase 1).  Radii are drawn
+    until the summed volume reaches ``fraction`` of the box, positions relaxed
+    until no overlap (periodic).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny, nz = (n, n, n) if np.isscalar(n) else n
+    box = np.array([nx, ny, nz], np.float64) * dx
+    vol = float(np.prod(box))
+    gap = 0.0 if gap is None else gap
+    radii = []
+    v = 0.0
+    rcap = 0.45 * float(box.min())
+    while v < fraction * vol:
+        r = min(float(rng.uniform(rmin, rmax)), rcap)
+        radii.append(r)
+        v += 4.0 / 3.0 * math.pi * r ** 3
+    radii = np.array(sorted(radii, reverse=True))
+    centers = rng.uniform(0, 1, size=(len(radii), 3)) * box
+    centers, iters = _relax_periodic(centers, radii, box, gap, rng=rng)
+    labels = np.zeros((nz, ny, nx), np.int32)
+    ax = [np.arange(m) * dx for m in (nx, ny, nz)]
+    for j, (c, r) in enumerate(zip(centers, radii)):
+        lo = [int(math.floor((c[a] - r) / dx)) for a in range(3)]
+        hi = [int(math.ceil((c[a] + r) / dx)) + 1 for a in range(3)]
+        idx = [np.arange(lo[a], hi[a]) for a in range(3)]
+        d = []
+        for a in range(3):
+            p = idx[a] * dx - c[a]
+            d.append(p)
+        rr = d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2
+        inside = rr < r * r
+        zi = idx[2] % nz
+        yi = idx[1] % ny
+        xi = idx[0] % nx
+        sub = labels[np.ix_(zi, yi, xi)]
+        sub = np.where(inside & (sub == 0), j + 1, sub)
+        labels[np.ix_(zi, yi, xi)] = sub
+    pol = np.full(len(radii) + 1, PHASE_IN, np.uint8)
+    pol[0] = PHASE_EX
+    g = Geometry(labels, pol, dx, {"kind": "spheres", "n_spheres": len(radii), "seed": seed,
+                                   "target_fraction": fraction, "relax_iters": iters})
+    g.info["intra_fraction"] = float((labels > 0).mean())
+    return g
+
+
+def voronoi_tissue(n, dx, cell_diam=10.0, ecs_fraction=0.2, n_vessels=4, vessel_radius=3.0,
+                   seed=0, chunk=1 << 22):
+    """Voronoi cells with an extracellular band and straight vessel tubes.
+
+    Seeds have density 1/(pi/6 d^3) so the mean cell volume matches a sphere
+    of diameter ``cell_diam``; ties go to the lowest seed index.  A site is
+    extracellular where (d2 - d1) < w, with w the ``ecs_fraction`` quantile of
+    d2 - d1 (d1, d2: distances to the nearest and second-nearest seed).
+    Vessels are z-aligned tubes of ``vessel_radius`` at seeded (x, y).
+    Labels: 0 = extracellular (phase 1), 1..n_cells = cells (phase 0),
+    n_cells+1.. = vessels (phase 2).
+    """
+    from scipy.spatial import cKDTree
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = n * dx
+    n_cells = max(2, int(round(L ** 3 / (math.pi / 6.0 * cell_diam ** 3))))
+    seeds = rng.uniform(0, L, size=(n_cells, 3))
+    tree = cKDTree(seeds)
+    coords = np.arange(n, dtype=np.float64) * dx
+    N = n ** 3
+    near = np.empty(N, np.int32)
+    gapd = np.empty(N, np.float32)
+    plane = n * n
+    zs_per = max(1, chunk // plane)
+    X, Y = np.meshgrid(coords, coords, indexing="xy")
+    xy = np.stack([X.ravel(), Y.ravel()], 1)
+    for z0 in range(0, n, zs_per):
+        z1 = min(n, z0 + zs_per)
+        pts = np.concatenate([np.concatenate([xy, np.full((plane, 1), coords[z])], 1) for z in range(z0, z1)])
+        d, i = tree.query(pts, k=2, workers=-1)
+        near[z0 * plane:z1 * plane] = i[:, 0]
+        gapd[z0 * plane:z1 * plane] = d[:, 1] - d[:, 0]
+    w = float(np.quantile(gapd, ecs_fraction))
+    labels = (near + 1).astype(np.int32)
+    labels[gapd < w] = 0
+    labels = labels.reshape(n, n, n)
+    vx = rng.uniform(0, L, size=(n_vessels, 2))
+    lab2 = np.full((n, n), -1, np.int32)
+    for j, c in enumerate(vx):
+        inside = (coords[None, :] - c[0]) ** 2 + (coords[:, None] - c[1]) ** 2 < vessel_radius ** 2
+        lab2[inside & (lab2 < 0)] = n_cells + 1 + j
+    vmask = lab2 >= 0
+    labels[:, vmask] = lab2[vmask][None, :]
+    pol = np.zeros(n_cells + 1 + n_vessels, np.uint8)
+    pol[0] = 1
+    pol[n_cells + 1:] = 2
+    g = Geometry(np.ascontiguousarray(labels), pol, dx, {"kind": "voronoi", "n_cells": n_cells,
+                                                          "n_vessels": n_vessels, "ecs_width_um": w,
+                                                          "seed": seed})
+    return g
+
+
+def directions_on_sphere(n, seed=0):
+    """``n`` unit vectors, normalised Gaussian triples (uniform on the sphere)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def crop(geom: Geometry, n):
+    """Corner crop n^3 of a geometry (labels renumbered compactly)."""
+    lab = geom.labels[:n, :n, :n]
+    uniq, inv = np.unique(lab, return_inverse=True)
+    return Geometry(inv.reshape(lab.shape).astype(np.int32), geom.phase_of_label[uniq].copy(), geom.dx,
+                    dict(geom.info, cropped=n))
