@@ -1,0 +1,330 @@
+"""Benchmark of the fused hybrid-LBM Bloch-Torrey sweep on GB300.
+
+Workload (large tissue model): 512^3 lattice, dx = 0.25 um, seeded Voronoi
+cell tessellation (mean cell diameter 10 um) with ~20 % extracellular band and
+4 vessel tubes, 3 phases (cells D = 1.0, extracellular D = 2.5, vessels
+D = 3.0 um^2/ms; T2 50/80/80 ms), permeable membranes on every compartment
+boundary (kappa = 0.01 um/ms), mirroring outer boundaries, PGSE b = 1000
+s/mm^2, delta = 10 ms, Delta = 30 ms, dt = 0.0015625 ms, three orthogonal
+gradient directions run as one batch (one launch per time step).
+
+A "step" is one time step of the whole batch: every site of the lattice
+updated once for each of the 3 directions.  value = MLUPS = sites x members x
+steps / s.  Inputs (15 GB of state per direction) are far larger than L2.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "tissue512_voronoi_mirror_3dir"
+N_EDGE = 512
+DX = 0.25
+DT = 0.0015625
+B = 1000.0
+DELTA, BIG_DELTA = 10.0, 30.0
+D = [1.0, 2.5, 3.0]
+T2 = [50.0, 80.0, 80.0]
+KAPPA = 0.01
+BYTES_PER_SITE = 113  # 7 complex64 read + 7 written + 1 mask byte (algorithmic)
+METRIC = "MLUPS (fused sweep, FP32, 3-direction batch)"
+
+
+def _rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def geometry(n=N_EDGE, seed=2024):
+    from paper_1907_00908_gb300 import synth
+    return synth.voronoi_tissue(n, DX, cell_diam=10.0, ecs_fraction=0.2, n_vessels=4, vessel_radius=3.0, seed=seed)
+
+
+def sequences():
+    from paper_1907_00908_gb300 import lbmbt
+    out = []
+    for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        gG, f = lbmbt.pgse(B, DELTA, BIG_DELTA, DT, d)
+        out.append((gG, f))
+    return out
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "sweep_common.cuh", "lbmbt_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per sweep launch from the committed ncu summary, or None
+    when the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    if j.get("source_hash") != sweep_source_hash():
+        return None
+    return float(j["bytes_per_site_member"]) * N_EDGE ** 3 * 3
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/lbmbt_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(geom, seqs, steps=24):
+    """The FP64 oracle on a 128^3 corner crop of the same tissue, the first
+    `steps` steps of each of the 3 PGSE sequences, all host cores."""
+    import oracle
+    from paper_1907_00908_gb300 import synth
+    crop = synth.crop(geom, 128)
+    cores = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    for gG, f in seqs:
+        oracle.run(crop.labels, DX, crop.phase_of_label, [1, 1, 1], D, T2, KAPPA, DT, f[:steps], gG, threads=cores)
+    t = time.perf_counter() - t0
+    sites = crop.n_sites * len(seqs) * steps
+    return {"value": sites / t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"128^3 corner crop of the tissue, {steps} steps x 3 directions, FP64, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _rank()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1907_00908_gb300 import synth
+    oracle.build()
+    geom = synth.crop(geometry(), 128)
+    from oracle import pgse
+    seqs = [pgse(B, DELTA, BIG_DELTA, DT, d) for d in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    cores = os.cpu_count() or 1
+    per_step = 2
+
+    def one():
+        for gG, f in seqs:
+            oracle.run(geom.labels, DX, geom.phase_of_label, [1, 1, 1], D, T2, KAPPA, DT, f[:per_step], gG,
+                       threads=cores)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    t = time.perf_counter() - t0
+    sites = geom.n_sites * 3 * per_step * args.steps
+    v = sites / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "128^3 crop, 2 lattice steps x 3 directions per step"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": "128^3 corner crop of the 512^3 tissue, 2 lattice steps x 3 directions per "
+                                       "bench step"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--spt", type=int, default=0)
+    ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1907_00908_gb300 import lbmbt
+
+    rank, world, local = _rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    t_geo = time.perf_counter()
+    geom = geometry(args.n)
+    t_geo = time.perf_counter() - t_geo
+    seqs = sequences()
+    K_total = len(seqs[0][1])
+    assert args.warmup + args.steps <= K_total
+    n_sites = geom.n_sites
+    nm = len(seqs)
+
+    s = lbmbt.Solver(local, stream)
+    if args.block:
+        s.set_option(lbmbt.OPT_BLOCK, args.block)
+    if args.spt:
+        s.set_option(lbmbt.OPT_SPT, args.spt)
+    s.set_geometry(geom.labels, geom.phase_of_label, DX, (1, 1, 1))
+    s.set_phases(D, T2)
+    s.set_sequence(DT, seqs[0][1], seqs[0][0])
+    members = lbmbt.Solver.members([g for g, _ in seqs], 0, KAPPA)
+    s.prepare(members)
+    s.advance(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = s.launch_count()
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sig = s.advance(args.steps, want_signal=True, n_members=nm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = s.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms = float(t.item())
+    value = n_sites * nm * args.steps * world / (ms * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / args.steps
+    achieved = BYTES_PER_SITE * n_sites * nm / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API: host labels (pinned) -> mask,
+    # sequence upload, batch set-up and the same K steps, signal to the host.
+    e2e = None
+    if not args.no_e2e:
+        lab_pinned = torch.from_numpy(geom.labels).pin_memory()
+        s2 = lbmbt.Solver(local, stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        h0 = time.perf_counter()
+        s2.set_geometry(lab_pinned.numpy(), geom.phase_of_label, DX, (1, 1, 1))
+        s2.set_phases(D, T2)
+        s2.set_sequence(DT, seqs[0][1], seqs[0][0])
+        s2.prepare(members)
+        sig2 = s2.advance(args.steps, want_signal=True, n_members=nm)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - h0
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        s2.close()
+        h2d = n_sites * 4 + geom.phase_of_label.size + K_total * (4 + 8) + nm * 200
+        d2h = nm * 16
+        e2e = {"value": n_sites * nm * args.steps * world / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": te, "includes": "label upload + mask build + sequence upload + set-up + K steps + signal"}
+        del sig2
+    s.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(geom, seqs)
+
+    if rank == 0:
+        tr = traffic_per_launch()
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [args.n] * 3, "dx_um": DX, "dt_ms": DT, "members": nm,
+                       "bc": "mirror", "phases": 3, "kappa_um_ms": KAPPA, "b_s_mm2": B,
+                       "l2": "state of 15 GB per direction, far larger than L2; no flush needed",
+                       "sites_per_step": n_sites * nm, "geometry_gen_s": round(t_geo, 1)},
+            "signal_after_timed_steps": [float(x) for x in sig[:, 2]],
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": tr, "peak_source": peak_kind,
+                         "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_kernel"},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

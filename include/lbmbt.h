@@ -1,0 +1,200 @@
+/*
+ * lbmbt.h -- C ABI of the GB300 (sm_103a) hybrid lattice-Boltzmann
+ * Bloch-Torrey library (Naughton, Tennyson & Georgiadis, arXiv 1907.00908).
+ *
+ * The library advances the complex transverse magnetisation M(x, t) of the
+ * Bloch-Torrey equation (Sec. 2.1, Eq. LBM-B-Teq) with the paper's hybrid
+ * lattice Boltzmann scheme (Sec. 2.3, Eq. LBM_process_list_2) on a D3Q7
+ * lattice and returns the diffusion-MRI signal at the echo.  Every time step
+ * is one fused pass over the lattice: streaming with the outer boundary
+ * conditions (Sec. 2.4.3 modified periodic, Sec. 2.4.4 mirroring) and the
+ * half-link permeable-membrane rule (Sec. 2.4.2, Eqs. B5 and P_def), the
+ * reaction (Eq. reaction_LBM: gradient phase and T2 decay) and the BGK
+ * collision (Eq. collision_LBM) with a relaxation time per phase
+ * (Eq. tau_def).  Arithmetic is FP32; the signal is summed in FP64.
+ *
+ * Conventions (all entry points):
+ *  - Units: um, ms.  b in s/mm^2 (as in the paper); gamma*G0 in rad/(um ms);
+ *    D in um^2/ms; T2 in ms (INFINITY = no decay); kappa in um/ms
+ *    (0 = impermeable, INFINITY = no membrane).
+ *  - Volumes are [nz][ny][nx], x fastest; node n of an axis sits at n*dx.
+ *    A periodic axis of n nodes has period n*dx.
+ *  - D3Q7 weights: eps_D = 1/4, omega_0 = 1/4, omega_1..6 = 1/8.
+ *  - Every call returns an int status: LBMBT_OK (0) or a negative code.
+ *    lbmbt_last_error(ctx) gives a message for the last failed call on ctx.
+ *    No call aborts the process; device-side checks report LBMBT_EDEVICE.
+ *  - Ownership: the caller owns every buffer it passes; the library copies
+ *    what it keeps.  Device pointers must be on the context's device; work
+ *    is issued on the stream given to lbmbt_create, and each call returns
+ *    after that stream has finished the call's work.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LBMBT_H
+#define LBMBT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBMBT_OK = 0,
+    LBMBT_EINVAL = -1,       /* invalid argument                                */
+    LBMBT_ENOMEM = -2,       /* device or host allocation failed                */
+    LBMBT_ECUDA = -3,        /* CUDA runtime error (message has the CUDA text)  */
+    LBMBT_EUNSTABLE = -4,    /* tau <= 1/2 (Eq. tau_def)                        */
+    LBMBT_EUNSUPPORTED = -5, /* mirror face with a gradient neither normal nor
+                                parallel to it (Sec. 2.4.4)                     */
+    LBMBT_EDEVICE = -6,      /* a device-side check failed (e.g. bad label)     */
+    LBMBT_ESTATE = -7        /* call order: geometry/phases/sequence missing    */
+};
+
+enum { LBMBT_BC_PERIODIC = 0, LBMBT_BC_MIRROR = 1 };
+
+typedef struct lbmbt_ctx lbmbt_ctx;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out is NULL on error. */
+int lbmbt_create(lbmbt_ctx** out, int device, void* cuda_stream);
+
+/* Free the context and every device buffer it holds.  NULL is accepted. */
+int lbmbt_destroy(lbmbt_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next
+ * call on ctx.  ctx == NULL gives the message of the last failed create. */
+const char* lbmbt_last_error(const lbmbt_ctx* ctx);
+
+/* Library version string. */
+const char* lbmbt_version(void);
+
+/*
+ * Geometry (Sec. 2.1 phases; Sec. 2.4.2 membranes; Secs. 2.4.3-2.4.4 outer
+ * boundaries).  labels: int32 compartment id per node, [nz][ny][nx], host or
+ * device memory (labels_on_device != 0 means device).  phase_of_label[n_labels]
+ * (host): phase id (0..3) of each label.  bc[3]: per axis x, y, z,
+ * LBMBT_BC_PERIODIC or LBMBT_BC_MIRROR.  Every link between two nodes with
+ * different labels carries a membrane at its midpoint (Delta_m = 1/2,
+ * theta = 0); a mirror face never does.  The library builds, on the device,
+ * one byte per node: bit (i-1), i = 1..6, set iff the link to the neighbour
+ * across +e_i (D3Q7 order +x,-x,+y,-y,+z,-z) is a membrane; bits 6-7 hold the
+ * phase id.
+ *
+ * lbmbt_set_geometry replaces all geometries by this one (index 0);
+ * lbmbt_add_geometry appends one and returns its index in *index_out (for
+ * batched runs over several geometries).  Errors: EINVAL for bad sizes, a
+ * label outside [0, n_labels) (reported by the device check as EDEVICE), or
+ * a phase id > 3.
+ */
+int lbmbt_set_geometry(lbmbt_ctx* ctx, int nx, int ny, int nz, double dx_um,
+                       const int32_t* labels, int labels_on_device, int n_labels,
+                       const uint8_t* phase_of_label, const int bc[3]);
+int lbmbt_add_geometry(lbmbt_ctx* ctx, int nx, int ny, int nz, double dx_um,
+                       const int32_t* labels, int labels_on_device, int n_labels,
+                       const uint8_t* phase_of_label, const int bc[3], int* index_out);
+
+/* Copy the per-node mask byte of geometry `index` (encoding above) to host
+ * memory mask_out[nz*ny*nx]. */
+int lbmbt_get_mask(lbmbt_ctx* ctx, int index, uint8_t* mask_out);
+
+/* Piecewise-uniform diffusivity and T2 per phase (Sec. 2.1), n_phases 1..4.
+ * tau_p = 1/2 + dt D_p / (eps_D dx^2) (Eq. tau_def) is checked at run time:
+ * tau <= 1/2 gives EUNSTABLE. */
+int lbmbt_set_phases(lbmbt_ctx* ctx, int n_phases, const double* D_um2_ms, const double* T2_ms);
+
+/* Membrane permeability kappa (Eq. permeability_flux) for plain runs and the
+ * default of batched members.  The link rule uses P = eps_D dx/(2 kappa dt)
+ * (Eq. P_def): a share s = 1/(1+P) crosses, r = P/(1+P) is reflected
+ * (Eq. B5). */
+int lbmbt_set_permeability(lbmbt_ctx* ctx, double kappa_um_ms);
+
+/* Gradient sequence G(t) = G0 f(t) (Sec. 2.1).  f[k] (host, n_steps values) is
+ * the waveform used during step k (Eq. reaction_LBM at t^k = k dt); the
+ * periodic boundary phase uses F_k = sum_{m<k} f[m] dt (Eq. periodic_phi).
+ * gamma_G0[3] = gamma*G0 in rad/(um ms).  The run ends at t = n_steps*dt. */
+int lbmbt_set_sequence(lbmbt_ctx* ctx, double dt_ms, int64_t n_steps, const double* f,
+                       const double gamma_G0[3]);
+
+/* PGSE helper (Sec. 2.1, Fig. 2): from b (s/mm^2), delta, Delta, dt and a
+ * direction, gamma_G0_out = sqrt(b/(delta^2 (Delta - delta/3))) * unit(dir)
+ * and the effective waveform sampled at t^k = k dt: +1 on [0, delta), -1 on
+ * [Delta, Delta + delta), 0 elsewhere, ending at TE = Delta + delta.
+ * *n_steps_out = (Delta + delta)/dt; f_out (host, may be NULL to query the
+ * length) receives n_steps values.  delta/dt and Delta/dt must be integers
+ * (within 1e-9) else EINVAL. */
+int lbmbt_pgse(double b_s_mm2, double delta_ms, double Delta_ms, double dt_ms,
+               const double dir[3], double gamma_G0_out[3], int64_t* n_steps_out, double* f_out);
+
+/*
+ * Plain run from M = 1 (Sec. 2.1) over the set sequence on geometry 0.
+ * signal_out[3] (host) = {Re Z, Im Z, |Z|/N} with Z = sum_x M(x, t_end)
+ * (FP64 sum).  field_out_dev: device complex64 [N] receiving M(x, t_end), or
+ * NULL.  series_out: host [n_steps][2] receiving Z after every step, or NULL.
+ */
+int lbmbt_run(lbmbt_ctx* ctx, double* signal_out, void* field_out_dev, double* series_out);
+
+/* One member of a batched run: its gradient (direction x amplitude), the
+ * geometry it runs on (index from set/add_geometry) and its permeability. */
+typedef struct {
+    double gamma_G0[3];
+    int geometry;
+    double kappa_um_ms;
+} lbmbt_member;
+
+/*
+ * Batched run: n_members independent runs that share the set waveform f, dt
+ * and phases, advanced together by one launch per time step over a work list
+ * of (member, tile) (captured in a CUDA graph when enabled).  Members on the
+ * same geometry share its mask.  signal_out (host) [n_members][3] as in
+ * lbmbt_run; series_out (host) [n_members][n_steps][2] or NULL.
+ */
+int lbmbt_run_batch(lbmbt_ctx* ctx, int n_members, const lbmbt_member* members,
+                    double* signal_out, double* series_out);
+
+/*
+ * Gradient of S = |Z|/N at t_end with respect to the per-phase D_p and T2_p
+ * and the permeability kappa, for the plain run (geometry 0, set gradient),
+ * by a hand-written adjoint (reverse-time) sweep: the forward states are
+ * checkpointed every `checkpoint_every` steps (<= 0: 64) and recomputed
+ * segment by segment.  signal_out[3] as in lbmbt_run; dS_dD[n_phases],
+ * dS_dT2[n_phases] (host; T2 = INFINITY gives 0), dS_dkappa[1] (host).
+ */
+int lbmbt_grad(lbmbt_ctx* ctx, int checkpoint_every, double* signal_out,
+               double* dS_dD, double* dS_dT2, double* dS_dkappa);
+
+/* Batched form of lbmbt_grad: per member signal_out[n][3], dS_dD[n][n_phases],
+ * dS_dT2[n][n_phases], dS_dkappa[n]. */
+int lbmbt_grad_batch(lbmbt_ctx* ctx, int n_members, const lbmbt_member* members,
+                     int checkpoint_every, double* signal_out, double* dS_dD,
+                     double* dS_dT2, double* dS_dkappa);
+
+/* Options. */
+enum {
+    LBMBT_OPT_GRAPH = 1,     /* 1 (default): replay step loops as CUDA graphs   */
+    LBMBT_OPT_AUTOTUNE = 2,  /* 1: time launch shapes on first use (default 0)  */
+    LBMBT_OPT_BLOCK = 3,     /* threads per block of the sweep (64..1024)       */
+    LBMBT_OPT_SPT = 4        /* sites per thread of the sweep (1, 2 or 4)       */
+};
+int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
+int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);
+
+/*
+ * Low-level timing hook: advance the set-up plain or batched work by
+ * `n_steps` sweeps from its current state without re-initialising (the first
+ * call after lbmbt_prepare starts from M = 1).  Used by benchmarks to time the
+ * steady-state sweep; lbmbt_prepare allocates and initialises.
+ * n_members/members as in lbmbt_run_batch (n_members = 0: the plain run).
+ * Signal partials are reduced on the last of the steps when want_signal != 0
+ * and written to signal_out[n][3] (host) if not NULL.
+ */
+int lbmbt_prepare(lbmbt_ctx* ctx, int n_members, const lbmbt_member* members);
+int lbmbt_advance(lbmbt_ctx* ctx, int64_t n_steps, int want_signal, double* signal_out);
+
+/* Number of kernel launches the library issued on ctx since creation. */
+int lbmbt_launch_count(lbmbt_ctx* ctx, int64_t* count_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMBT_H */

@@ -1,0 +1,292 @@
+// adjoint.cu -- reverse-time (adjoint) sweep of the hybrid LBM step for
+// d S / d(D_p, T2_p, kappa), S = |Z|/N, Z = sum_x M(x, t^K).
+//
+// One forward step k maps the post-collision state u^k to u^(k+1):
+//   g'^k    = S_k u^k               stream + outer BC + membranes (real-linear)
+//   g^(k+1) = (1 + q_k) g'^k        reaction, q_k = exp(i theta)(1 - eps) - 1
+//   u^(k+1) = C g^(k+1)             BGK collision, real coefficients
+// With lambda^k = dS/du^k held as complex numbers (d/dRe + i d/dIm), the
+// transposes are
+//   C^T:   mu_j = (1 - omega) lambda_j + omega sum_i w_i lambda_i
+//   R^T:   nu   = conj(1 + q) mu
+//   S^T:   lambda_j(y) = sum over the forward consumers of u_j(y):
+//            plain link         -> conj(fac) nu_j(y + e_j)
+//            membrane link      -> s conj(fac) nu_j(y + e_j) + r nu_jbar(y)
+//            mirror, plain      -> nu_jbar(y)
+//            mirror, conjugate  -> conj(nu_jbar(y)) fac    (the map z -> conj(z) c
+//                                                          is its own transpose)
+// and lambda^K = Z / (N |Z|) at every population.  The parameters enter
+//   omega_p = 1/tau_p : d u/d omega = w M - g            (sites of phase p)
+//   eps_p             : d g/d eps   = -exp(i theta) g'   (sites of phase p)
+//   s = 1/(1+P)       : d g'_i/d s  = v_i - o_i          (membrane links; v the
+//                       population streaming across, o = u_ibar of the site)
+// so dS/d(omega, eps, s) = sum_k <adjoint, derivative>, <a, b> = Re(conj(a) b).
+//
+// adjoint_kernel performs nu^k -> nu^(k-1) in one pass per site: it pulls
+// nu^k from the downstream neighbours (lambda^k), recomputes g'^(k-1) and
+// g^k from u^(k-1) (an upstream pull, as the forward sweep), accumulates the
+// three sensitivities and writes nu^(k-1).
+#include "lbmbt_internal.cuh"
+#include "sweep_common.cuh"
+
+namespace lbmbt {
+namespace {
+
+__device__ __forceinline__ float dotc(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+
+// Transposed stream of direction J = 1 + 2*AX + (SIGN > 0 ? 0 : 1) into site y
+// (index s): reads the adjoint of the population's consumer.
+template <int AX, int SIGN>
+__device__ __forceinline__ float2 adj_pull(const float2* __restrict__ nu, unsigned P, unsigned s, int coord, int dim,
+                                           unsigned stride, int bc, float2 fac_lo, float2 fac_hi, bool memb,
+                                           float sh)
+{
+    constexpr int J = 1 + 2 * AX + (SIGN > 0 ? 0 : 1);
+    constexpr int JB = (SIGN > 0) ? J + 1 : J - 1;
+    const bool cr = (SIGN > 0) ? (coord == dim - 1) : (coord == 0);
+    if (cr && bc != BC_PER) {
+        // mirror: u_J(y) feeds g'_JB(y), which crosses the high face (J = +e)
+        // or the low face (J = -e).
+        float2 v = __ldg(nu + (size_t)JB * P + s);
+        if (bc == BC_MIR_CONJ) {
+            v.y = -v.y;
+            v = cmul(v, SIGN > 0 ? fac_hi : fac_lo);
+        }
+        return v;
+    }
+    unsigned nb = (SIGN > 0) ? s + stride : s - stride;
+    float2 f = make_float2(1.f, 0.f);
+    if (cr) {  // periodic: the consumer is the wrapped node, pulling across its face
+        nb = (SIGN > 0) ? s - (unsigned)(dim - 1) * stride : s + (unsigned)(dim - 1) * stride;
+        f = (SIGN > 0) ? fac_lo : fac_hi;
+    }
+    float2 v = __ldg(nu + (size_t)J * P + nb);
+    if (cr) v = cmul(v, make_float2(f.x, -f.y));
+    if (memb) {
+        const float2 o = __ldg(nu + (size_t)JB * P + s);
+        v.x = o.x + sh * (v.x - o.x);
+        v.y = o.y + sh * (v.y - o.y);
+    }
+    return v;
+}
+
+__device__ __forceinline__ float2 pull_dir(int i, const float2* __restrict__ src, unsigned P, unsigned s, int x,
+                                           int y, int z, int nx, int ny, int nz, unsigned sxy, const int* bc,
+                                           const float2 (*fac)[2])
+{
+    switch (i) {
+    case 1: return pull<0, +1>(src, P, s, x, nx, 1u, bc[0], fac[0][0]);
+    case 2: return pull<0, -1>(src, P, s, x, nx, 1u, bc[0], fac[0][1]);
+    case 3: return pull<1, +1>(src, P, s, y, ny, (unsigned)nx, bc[1], fac[1][0]);
+    case 4: return pull<1, -1>(src, P, s, y, ny, (unsigned)nx, bc[1], fac[1][1]);
+    case 5: return pull<2, +1>(src, P, s, z, nz, sxy, bc[2], fac[2][0]);
+    default: return pull<2, -1>(src, P, s, z, nz, sxy, bc[2], fac[2][1]);
+    }
+}
+
+template <int SPT>
+__global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a, double Fk)
+{
+    __shared__ MemberDesc sd;
+    __shared__ float2 facP[3][2];   // factors of step k-1 (forward recompute)
+    __shared__ float2 facK[3][2];   // factors of step k (transposed stream)
+    __shared__ float2 sL;
+    __shared__ float s_red[NGACC][32];
+
+    if (threadIdx.x == 0) {
+        const int m = find_member(a.tile_start, a.n_members, blockIdx.x);
+        sd = a.members[m];
+        boundary_factors(sd, a.Fprev, facP);
+        boundary_factors(sd, Fk, facK);
+        const double2 L = a.lam_init[m];
+        sL = make_float2((float)L.x, (float)L.y);
+    }
+    __syncthreads();
+
+    const unsigned P = (unsigned)sd.plane;
+    const float2* __restrict__ u = sd.state + (size_t)a.fwd_slot * 7 * P;
+    const float2* __restrict__ nu = sd.adj + (size_t)a.lam_parity * 7 * P;
+    float2* __restrict__ out = sd.adj + (size_t)(a.lam_parity ^ 1) * 7 * P;
+    const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
+    const unsigned sxy = (unsigned)nx * ny;
+    const unsigned N = (unsigned)sd.N;
+    const unsigned base = (unsigned)(blockIdx.x - sd.tile0) * blockDim.x * SPT;
+    const float sh = sd.s_share;
+    const float fk = a.fprev;
+    float acc[NGACC];
+#pragma unroll
+    for (int j = 0; j < NGACC; ++j) acc[j] = 0.f;
+
+#pragma unroll
+    for (int jj = 0; jj < SPT; ++jj) {
+        const unsigned s = base + jj * blockDim.x + threadIdx.x;
+        if (s >= N) break;
+        const unsigned row = s / nx;
+        const int x = (int)(s - row * nx);
+        const int z = (int)(row / ny);
+        const int y = (int)(row - (unsigned)z * ny);
+        const unsigned mk = sd.mask[s];
+        const int ph = mk >> 6;
+
+        // forward recompute of g'^(k-1) at this site (as the forward sweep)
+        float2 gp[Q];
+        gp[0] = __ldg(u + s);
+        gp[1] = pull<0, +1>(u, P, s, x, nx, 1u, sd.bc[0], facP[0][0]);
+        gp[2] = pull<0, -1>(u, P, s, x, nx, 1u, sd.bc[0], facP[0][1]);
+        gp[3] = pull<1, +1>(u, P, s, y, ny, (unsigned)nx, sd.bc[1], facP[1][0]);
+        gp[4] = pull<1, -1>(u, P, s, y, ny, (unsigned)nx, sd.bc[1], facP[1][1]);
+        gp[5] = pull<2, +1>(u, P, s, z, nz, sxy, sd.bc[2], facP[2][0]);
+        gp[6] = pull<2, -1>(u, P, s, z, nz, sxy, sd.bc[2], facP[2][1]);
+        if (mk & 0x3fu) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int ib = (i & 1) ? i + 1 : i - 1;
+                if (mk & (1u << (ib - 1))) {
+                    const float2 o = __ldg(u + (size_t)ib * P + s);
+                    gp[i].x = o.x + sh * (gp[i].x - o.x);
+                    gp[i].y = o.y + sh * (gp[i].y - o.y);
+                }
+            }
+        }
+        const float ep = sd.eps[ph];
+        float cm1 = 0.f, sn = 0.f;
+        if (fk != 0.f) {
+            const float th = fk * (sd.ctheta[0] * (float)x + sd.ctheta[1] * (float)y + sd.ctheta[2] * (float)z);
+            float sh2, ch2;
+            sincosf(0.5f * th, &sh2, &ch2);
+            cm1 = -2.f * sh2 * sh2;
+            sn = 2.f * sh2 * ch2;
+        }
+        const float qr = cm1 - ep * (1.f + cm1), qi = sn * (1.f - ep);
+        float Mr = 0.f, Mi = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) { Mr += gp[i].x; Mi += gp[i].y; }
+        {   // M of g = (1 + q) g'
+            const float r0 = Mr, i0 = Mi;
+            Mr = r0 + (r0 * qr - i0 * qi);
+            Mi = i0 + (r0 * qi + i0 * qr);
+        }
+
+        // lambda^k at this site
+        float2 lam[Q];
+        if (a.first) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) lam[i] = sL;
+        } else {
+            lam[0] = __ldg(nu + s);
+            lam[1] = adj_pull<0, +1>(nu, P, s, x, nx, 1u, sd.bc[0], facK[0][0], facK[0][1], mk & 1u, sh);
+            lam[2] = adj_pull<0, -1>(nu, P, s, x, nx, 1u, sd.bc[0], facK[0][0], facK[0][1], mk & 2u, sh);
+            lam[3] = adj_pull<1, +1>(nu, P, s, y, ny, (unsigned)nx, sd.bc[1], facK[1][0], facK[1][1], mk & 4u, sh);
+            lam[4] = adj_pull<1, -1>(nu, P, s, y, ny, (unsigned)nx, sd.bc[1], facK[1][0], facK[1][1], mk & 8u, sh);
+            lam[5] = adj_pull<2, +1>(nu, P, s, z, nz, sxy, sd.bc[2], facK[2][0], facK[2][1], mk & 16u, sh);
+            lam[6] = adj_pull<2, -1>(nu, P, s, z, nz, sxy, sd.bc[2], facK[2][0], facK[2][1], mk & 32u, sh);
+        }
+
+        // d/d omega: <lambda_i, w_i M - g_i>, g_i = (1 + q) g'_i
+        float dOm = 0.f;
+        float lwr = 0.f, lwi = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float w = i == 0 ? W0 : WI;
+            const float gr = gp[i].x + (gp[i].x * qr - gp[i].y * qi);
+            const float gi = gp[i].y + (gp[i].x * qi + gp[i].y * qr);
+            dOm += lam[i].x * (w * Mr - gr) + lam[i].y * (w * Mi - gi);
+            lwr += w * lam[i].x;
+            lwi += w * lam[i].y;
+        }
+        // mu = C^T lambda; d/d eps: <mu_i, -exp(i theta) g'_i>; nu = conj(1+q) mu
+        const float om = sd.omega[ph];
+        float dEp = 0.f;
+        const float er = 1.f + cm1, ei = sn;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float mr = lam[i].x + om * (lwr - lam[i].x);
+            const float mi = lam[i].y + om * (lwi - lam[i].y);
+            dEp -= mr * (er * gp[i].x - ei * gp[i].y) + mi * (er * gp[i].y + ei * gp[i].x);
+            // conj(1 + q) * mu
+            lam[i].x = mr + (mr * qr + mi * qi);
+            lam[i].y = mi + (mi * qr - mr * qi);
+            __stcs(out + (size_t)i * P + s, lam[i]);
+        }
+        // d/d s on membrane links of step k-1: <nu_i, v_i - o_i>
+        float dS = 0.f;
+        if (mk & 0x3fu) {
+            for (int i = 1; i < Q; ++i) {
+                const int ib = (i & 1) ? i + 1 : i - 1;
+                if (mk & (1u << (ib - 1))) {
+                    const float2 v = pull_dir(i, u, P, s, x, y, z, nx, ny, nz, sxy, sd.bc, facP);
+                    const float2 o = __ldg(u + (size_t)ib * P + s);
+                    dS += dotc(lam[i], make_float2(v.x - o.x, v.y - o.y));
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            acc[p] += (ph == p) ? dOm : 0.f;
+            acc[4 + p] += (ph == p) ? dEp : 0.f;
+        }
+        acc[8] += dS;
+    }
+
+    // block reduction: FP32 within warps, FP64 across warps and steps
+#pragma unroll
+    for (int j = 0; j < NGACC; ++j)
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+#pragma unroll
+        for (int j = 0; j < NGACC; ++j) s_red[j][w] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < NGACC) {
+        double t = 0.0;
+        const int nw = blockDim.x >> 5;
+        for (int q = 0; q < nw; ++q) t += (double)s_red[threadIdx.x][q];
+        a.gacc[(size_t)blockIdx.x * NGACC + threadIdx.x] += t;
+    }
+}
+
+__global__ void reduce_grad_kernel(const double* __restrict__ gacc, const long long* __restrict__ tile_start,
+                                   double* __restrict__ out)
+{
+    __shared__ double sh[NGACC][128];
+    const int m = blockIdx.x;
+    double v[NGACC];
+#pragma unroll
+    for (int j = 0; j < NGACC; ++j) v[j] = 0.0;
+    for (long long t = tile_start[m] + threadIdx.x; t < tile_start[m + 1]; t += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < NGACC; ++j) v[j] += gacc[t * NGACC + j];
+#pragma unroll
+    for (int j = 0; j < NGACC; ++j) sh[j][threadIdx.x] = v[j];
+    __syncthreads();
+    for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int j = 0; j < NGACC; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < NGACC) out[m * NGACC + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint(const AdjointArgs& a, double Fk, long long n_tiles, int block, int spt, cudaStream_t st)
+{
+    if (block > 256) return cudaErrorInvalidValue;
+    switch (spt) {
+    case 1: adjoint_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a, Fk); break;
+    case 2: adjoint_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a, Fk); break;
+    case 4: adjoint_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a, Fk); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int n_members, double* out,
+                               cudaStream_t st)
+{
+    reduce_grad_kernel<<<n_members, 128, 0, st>>>(gacc, tile_start, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmbt

@@ -1,0 +1,949 @@
+// api.cu -- host side of the C ABI declared in include/lbmbt.h.
+//
+// A context owns: the geometries (device mask bytes), the phase table, the
+// sequence tables (f_k as float, F_k = sum_{m<k} f_m dt as double, both on
+// the device), and the work of the current prepared run: member descriptors,
+// the tile prefix of the work list, state buffers, per-tile partial sums and
+// the step-control word.  Time steps are issued as sweep launches; with the
+// graph option a chunk of sweeps is captured once per prepared run and
+// replayed (the step index lives on the device, so one graph serves any k).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lbmbt.h"
+#include "lbmbt_internal.cuh"
+
+using namespace lbmbt;
+
+namespace {
+
+struct Geom {
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0;
+    int bc[3] = {0, 0, 0};
+    long long N = 0;
+    int max_phase = 0;
+    uint8_t* d_mask = nullptr;
+};
+
+constexpr int GRAPH_CHUNK = 16;
+
+}  // namespace
+
+struct lbmbt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t owned_stream = nullptr;
+    std::string err;
+    std::vector<Geom> geoms;
+    int n_phases = 0;
+    double D[4] = {0, 0, 0, 0};
+    double T2[4] = {0, 0, 0, 0};
+    double kappa = INFINITY;
+    // sequence
+    double dt = 0;
+    long long n_steps = 0;
+    std::vector<double> f;
+    double gG[3] = {0, 0, 0};
+    float* d_f = nullptr;
+    double* d_F = nullptr;
+    // options
+    int use_graph = 1;
+    int autotune = 0;
+    int block = 256;
+    int spt = 2;
+    long long launches = 0;
+    // prepared run
+    int n_members = 0;
+    std::vector<lbmbt_member> members;
+    std::vector<MemberDesc> descs;
+    std::vector<long long> tile_start;
+    long long n_tiles = 0;
+    int tile_block = 0, tile_spt = 0;
+    MemberDesc* d_desc = nullptr;
+    long long* d_tile_start = nullptr;
+    size_t cap_desc = 0, cap_ts = 0;
+    double2* d_partial = nullptr;
+    size_t cap_partial = 0;
+    double2* d_Z = nullptr;
+    size_t cap_Z = 0;
+    double2* d_series = nullptr;
+    size_t cap_series = 0;
+    float2* d_state = nullptr;
+    size_t cap_state = 0;  // bytes
+    int n_slots = 2;
+    StepCtl* d_ctl = nullptr;
+    int* d_err = nullptr;
+    long long k_cur = 0;
+    bool prepared = false;
+    bool series_mode = false;
+    void* field_dev = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_series = -1;
+    // adjoint buffers
+    float2* d_ck = nullptr;
+    size_t cap_ck = 0;
+    float2* d_seg = nullptr;
+    size_t cap_seg = 0;
+    double* d_gacc = nullptr;
+    size_t cap_gacc = 0;
+    double* d_gout = nullptr;
+    size_t cap_gout = 0;
+    double2* d_laminit = nullptr;
+    size_t cap_laminit = 0;
+};
+
+static std::string g_create_error;
+
+static int fail(lbmbt_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CU(c, call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? LBMBT_ENOMEM : LBMBT_ECUDA,       \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+    } while (0)
+
+template <class T>
+static int grow(lbmbt_ctx* c, T** p, size_t* cap, size_t bytes)
+{
+    if (*cap >= bytes && *p) return LBMBT_OK;
+    if (*p) { cudaFree(*p); *p = nullptr; *cap = 0; }
+    if (bytes == 0) return LBMBT_OK;
+    CU(c, cudaMalloc((void**)p, bytes));
+    *cap = bytes;
+    return LBMBT_OK;
+}
+
+static void drop_graph(lbmbt_ctx* c)
+{
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    c->graph_series = -1;
+}
+
+static int set_device(lbmbt_ctx* c)
+{
+    CU(c, cudaSetDevice(c->device));
+    return LBMBT_OK;
+}
+
+// ------------------------------------------------------------------ basics
+extern "C" const char* lbmbt_version(void) { return "lbmbt 0.1 (sm_103a)"; }
+
+extern "C" int lbmbt_create(lbmbt_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(nullptr, LBMBT_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return fail(nullptr, LBMBT_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= n) return fail(nullptr, LBMBT_EINVAL, "device %d out of range (%d)", device, n);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, LBMBT_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    lbmbt_ctx* c = new lbmbt_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (!c->stream) {
+        // The legacy default stream cannot be captured into a graph; use an
+        // owned blocking stream, which still orders with the legacy stream.
+        if (cudaStreamCreate(&c->owned_stream) != cudaSuccess) {
+            delete c;
+            return fail(nullptr, LBMBT_ECUDA, "stream creation failed");
+        }
+        c->stream = c->owned_stream;
+    }
+    if (cudaMalloc(&c->d_ctl, sizeof(StepCtl)) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
+        lbmbt_destroy(c);
+        return fail(nullptr, LBMBT_ENOMEM, "allocation of control words failed");
+    }
+    *out = c;
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_destroy(lbmbt_ctx* c)
+{
+    if (!c) return LBMBT_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    drop_graph(c);
+    for (auto& g : c->geoms) cudaFree(g.d_mask);
+    cudaFree(c->d_f); cudaFree(c->d_F);
+    cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
+    cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
+    cudaFree(c->d_ck); cudaFree(c->d_seg); cudaFree(c->d_gacc); cudaFree(c->d_gout); cudaFree(c->d_laminit);
+    if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
+    delete c;
+    return LBMBT_OK;
+}
+
+extern "C" const char* lbmbt_last_error(const lbmbt_ctx* c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+static int sync(lbmbt_ctx* c)
+{
+    CU(c, cudaStreamSynchronize(c->stream));
+    return LBMBT_OK;
+}
+
+// ---------------------------------------------------------------- geometry
+static int make_geom(lbmbt_ctx* c, int nx, int ny, int nz, double dx, const int32_t* labels, int on_dev,
+                     int n_labels, const uint8_t* pol, const int bc[3], Geom* out)
+{
+    if (nx < 1 || ny < 1 || nz < 1) return fail(c, LBMBT_EINVAL, "grid sizes must be >= 1");
+    const long long N = (long long)nx * ny * nz;
+    if (N > (1LL << 28)) return fail(c, LBMBT_EINVAL, "grid of %lld sites exceeds 2^28", N);
+    if (!(dx > 0) || !std::isfinite(dx)) return fail(c, LBMBT_EINVAL, "dx must be positive");
+    if (!labels || !pol || !bc || n_labels < 1) return fail(c, LBMBT_EINVAL, "labels/phase table missing");
+    int maxp = 0;
+    for (int i = 0; i < n_labels; ++i) {
+        if (pol[i] > 3) return fail(c, LBMBT_EINVAL, "phase_of_label[%d] = %d > 3", i, (int)pol[i]);
+        if (pol[i] > maxp) maxp = pol[i];
+    }
+    for (int a = 0; a < 3; ++a)
+        if (bc[a] != LBMBT_BC_PERIODIC && bc[a] != LBMBT_BC_MIRROR)
+            return fail(c, LBMBT_EINVAL, "bc[%d] = %d invalid", a, bc[a]);
+    int rc = set_device(c);
+    if (rc) return rc;
+    int32_t* d_lab = nullptr;
+    uint8_t* d_pol = nullptr;
+    uint8_t* d_mask = nullptr;
+    auto cleanup = [&]() { cudaFree(d_lab); cudaFree(d_pol); };
+    if (!on_dev) {
+        if (cudaMalloc(&d_lab, N * sizeof(int32_t)) != cudaSuccess) { cleanup(); return fail(c, LBMBT_ENOMEM, "label buffer"); }
+        if (cudaMemcpyAsync(d_lab, labels, N * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            cleanup(); return fail(c, LBMBT_ECUDA, "label upload failed");
+        }
+    }
+    if (cudaMalloc(&d_pol, n_labels) != cudaSuccess || cudaMalloc(&d_mask, N) != cudaSuccess) {
+        cleanup(); cudaFree(d_mask); return fail(c, LBMBT_ENOMEM, "mask buffer");
+    }
+    cudaMemcpyAsync(d_pol, pol, n_labels, cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    cudaError_t e = launch_build_mask(on_dev ? labels : d_lab, d_pol, n_labels, nx, ny, nz, bc, d_mask, c->d_err,
+                                      c->stream);
+    c->launches++;
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) { cudaFree(d_mask); return fail(c, LBMBT_ECUDA, "mask build: %s", cudaGetErrorString(e)); }
+    if (herr) { cudaFree(d_mask); return fail(c, LBMBT_EDEVICE, "a label is outside [0, %d)", n_labels); }
+    out->nx = nx; out->ny = ny; out->nz = nz; out->dx = dx; out->N = N; out->max_phase = maxp;
+    for (int a = 0; a < 3; ++a) out->bc[a] = bc[a];
+    out->d_mask = d_mask;
+    return LBMBT_OK;
+}
+
+static void invalidate_run(lbmbt_ctx* c)
+{
+    c->prepared = false;
+    drop_graph(c);
+}
+
+extern "C" int lbmbt_set_geometry(lbmbt_ctx* c, int nx, int ny, int nz, double dx, const int32_t* labels,
+                                  int on_dev, int n_labels, const uint8_t* pol, const int bc[3])
+{
+    if (!c) return LBMBT_EINVAL;
+    Geom g;
+    int rc = make_geom(c, nx, ny, nz, dx, labels, on_dev, n_labels, pol, bc, &g);
+    if (rc) return rc;
+    invalidate_run(c);
+    for (auto& o : c->geoms) cudaFree(o.d_mask);
+    c->geoms.clear();
+    c->geoms.push_back(g);
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_add_geometry(lbmbt_ctx* c, int nx, int ny, int nz, double dx, const int32_t* labels,
+                                  int on_dev, int n_labels, const uint8_t* pol, const int bc[3], int* index_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    Geom g;
+    int rc = make_geom(c, nx, ny, nz, dx, labels, on_dev, n_labels, pol, bc, &g);
+    if (rc) return rc;
+    invalidate_run(c);
+    c->geoms.push_back(g);
+    if (index_out) *index_out = (int)c->geoms.size() - 1;
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_get_mask(lbmbt_ctx* c, int index, uint8_t* mask_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (index < 0 || index >= (int)c->geoms.size()) return fail(c, LBMBT_EINVAL, "geometry %d not set", index);
+    if (!mask_out) return fail(c, LBMBT_EINVAL, "mask_out is NULL");
+    int rc = set_device(c);
+    if (rc) return rc;
+    const Geom& g = c->geoms[index];
+    CU(c, cudaMemcpyAsync(mask_out, g.d_mask, g.N, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+// ------------------------------------------------------------ physics setup
+extern "C" int lbmbt_set_phases(lbmbt_ctx* c, int n, const double* D, const double* T2)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (n < 1 || n > 4 || !D || !T2) return fail(c, LBMBT_EINVAL, "need 1..4 phases with D and T2");
+    for (int p = 0; p < n; ++p) {
+        if (!(D[p] > 0) || !std::isfinite(D[p])) return fail(c, LBMBT_EINVAL, "D[%d] must be positive", p);
+        if (!(T2[p] > 0)) return fail(c, LBMBT_EINVAL, "T2[%d] must be positive", p);
+    }
+    c->n_phases = n;
+    for (int p = 0; p < 4; ++p) { c->D[p] = p < n ? D[p] : 1.0; c->T2[p] = p < n ? T2[p] : INFINITY; }
+    invalidate_run(c);
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_set_permeability(lbmbt_ctx* c, double kappa)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!(kappa >= 0)) return fail(c, LBMBT_EINVAL, "kappa must be >= 0 (INFINITY allowed)");
+    c->kappa = kappa;
+    invalidate_run(c);
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_set_sequence(lbmbt_ctx* c, double dt, int64_t n_steps, const double* f, const double gG[3])
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(c, LBMBT_EINVAL, "dt must be positive");
+    if (n_steps < 1 || n_steps > (1LL << 30)) return fail(c, LBMBT_EINVAL, "n_steps out of range");
+    if (!f || !gG) return fail(c, LBMBT_EINVAL, "f / gamma_G0 missing");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(gG[a])) return fail(c, LBMBT_EINVAL, "gamma_G0 not finite");
+    for (long long k = 0; k < n_steps; ++k)
+        if (!std::isfinite(f[k])) return fail(c, LBMBT_EINVAL, "f[%lld] not finite", k);
+    int rc = set_device(c);
+    if (rc) return rc;
+    invalidate_run(c);
+    c->dt = dt;
+    c->n_steps = n_steps;
+    c->f.assign(f, f + n_steps);
+    for (int a = 0; a < 3; ++a) c->gG[a] = gG[a];
+    std::vector<float> ff(n_steps);
+    std::vector<double> FF(n_steps + 1);
+    double F = 0.0;
+    for (long long k = 0; k < n_steps; ++k) {
+        ff[k] = (float)f[k];
+        FF[k] = F;                  // F_k = sum_{m<k} f_m dt (Eq. periodic_phi)
+        F += f[k] * dt;
+    }
+    FF[n_steps] = F;
+    cudaFree(c->d_f); cudaFree(c->d_F);
+    c->d_f = nullptr; c->d_F = nullptr;
+    CU(c, cudaMalloc(&c->d_f, n_steps * sizeof(float)));
+    CU(c, cudaMalloc(&c->d_F, (n_steps + 1) * sizeof(double)));
+    CU(c, cudaMemcpyAsync(c->d_f, ff.data(), n_steps * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->d_F, FF.data(), (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    return sync(c);
+}
+
+extern "C" int lbmbt_pgse(double b, double delta, double Delta, double dt, const double dir[3], double gG_out[3],
+                          int64_t* n_steps_out, double* f_out)
+{
+    if (!dir || !gG_out || !n_steps_out) return LBMBT_EINVAL;
+    if (!(dt > 0) || !(delta > 0) || !(Delta >= delta) || !(b >= 0)) return LBMBT_EINVAL;
+    const double nd = delta / dt, nD = Delta / dt;
+    if (std::fabs(nd - std::round(nd)) > 1e-9 * std::fmax(1.0, nd) ||
+        std::fabs(nD - std::round(nD)) > 1e-9 * std::fmax(1.0, nD))
+        return LBMBT_EINVAL;
+    const long long id = (long long)std::llround(nd), iD = (long long)std::llround(nD);
+    const double nrm = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(nrm > 0)) return LBMBT_EINVAL;
+    // b [s/mm^2] * 1e-3 = b [ms/um^2];  b = (gamma G0)^2 delta^2 (Delta - delta/3)  (Sec. 2.1)
+    const double g = b > 0 ? std::sqrt(b * 1e-3 / (delta * delta * (Delta - delta / 3.0))) : 0.0;
+    for (int a = 0; a < 3; ++a) gG_out[a] = g * dir[a] / nrm;
+    *n_steps_out = iD + id;
+    if (f_out)
+        for (long long k = 0; k < iD + id; ++k) f_out[k] = k < id ? 1.0 : (k >= iD ? -1.0 : 0.0);
+    return LBMBT_OK;
+}
+
+// ------------------------------------------------------------- run set-up
+static int build_worklist(lbmbt_ctx* c, int block, int spt)
+{
+    const long long tile = (long long)block * spt;
+    c->tile_start.assign(c->n_members + 1, 0);
+    for (int m = 0; m < c->n_members; ++m) {
+        const long long N = c->descs[m].N;
+        c->descs[m].tile0 = c->tile_start[m];
+        c->tile_start[m + 1] = c->tile_start[m] + (N + tile - 1) / tile;
+    }
+    c->n_tiles = c->tile_start[c->n_members];
+    if (c->n_tiles > 0x7fffffffLL) return fail(c, LBMBT_EINVAL, "work list too long");
+    int rc = grow(c, &c->d_desc, &c->cap_desc, sizeof(MemberDesc) * c->n_members);
+    if (!rc) rc = grow(c, &c->d_tile_start, &c->cap_ts, sizeof(long long) * (c->n_members + 1));
+    if (!rc) rc = grow(c, &c->d_partial, &c->cap_partial, sizeof(double2) * c->n_tiles);
+    if (rc) return rc;
+    CU(c, cudaMemcpyAsync(c->d_desc, c->descs.data(), sizeof(MemberDesc) * c->n_members, cudaMemcpyHostToDevice,
+                          c->stream));
+    CU(c, cudaMemcpyAsync(c->d_tile_start, c->tile_start.data(), sizeof(long long) * (c->n_members + 1),
+                          cudaMemcpyHostToDevice, c->stream));
+    c->tile_block = block;
+    c->tile_spt = spt;
+    drop_graph(c);
+    return sync(c);
+}
+
+static SweepArgs sweep_args(lbmbt_ctx* c)
+{
+    SweepArgs a;
+    a.members = c->d_desc;
+    a.tile_start = c->d_tile_start;
+    a.n_members = c->n_members;
+    a.ctl = c->d_ctl;
+    a.f = c->d_f;
+    a.F = c->d_F;
+    a.partial = c->d_partial;
+    return a;
+}
+
+static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base = 0, int slot_mod = 2)
+{
+    StepCtl h;
+    h.k = (int)c->k_cur;
+    h.done = 0;
+    h.sig_step = sig_step;
+    h.field_step = field_step;
+    h.slot_base = slot_base;
+    h.slot_mod = slot_mod;
+    h.series = c->series_mode ? 1 : 0;
+    h.err = 0;
+    CU(c, launch_set_ctl(c->d_ctl, h, c->stream));
+    c->launches++;
+    return LBMBT_OK;
+}
+
+static int init_state(lbmbt_ctx* c)
+{
+    SweepArgs a = sweep_args(c);
+    CU(c, launch_init(a, c->n_tiles, c->tile_block, c->tile_spt, 0, c->stream));
+    c->launches++;
+    c->k_cur = 0;
+    return LBMBT_OK;
+}
+
+// Issue one step: sweep (+ per-step reduce in series mode).
+static int issue_step(lbmbt_ctx* c)
+{
+    SweepArgs a = sweep_args(c);
+    CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
+    c->launches++;
+    if (c->series_mode) {
+        CU(c, launch_reduce(c->d_partial, c->d_tile_start, c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
+                            c->stream));
+        c->launches++;
+    }
+    return LBMBT_OK;
+}
+
+static int autotune(lbmbt_ctx* c)
+{
+    static const int cand[][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2}, {256, 2}, {512, 2}, {128, 4}, {256, 4}};
+    cudaEvent_t e0, e1;
+    CU(c, cudaEventCreate(&e0));
+    CU(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bb = c->block, bs = c->spt;
+    const bool saved_series = c->series_mode;
+    c->series_mode = false;
+    for (auto& cd : cand) {
+        int rc = build_worklist(c, cd[0], cd[1]);
+        if (rc) return rc;
+        rc = init_state(c);
+        if (!rc) rc = write_ctl(c, -1, -1);
+        if (rc) return rc;
+        issue_step(c);
+        CU(c, cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < 4; ++r) issue_step(c);
+        CU(c, cudaEventRecord(e1, c->stream));
+        CU(c, cudaEventSynchronize(e1));
+        float ms = 0;
+        CU(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bb = cd[0]; bs = cd[1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->series_mode = saved_series;
+    c->block = bb;
+    c->spt = bs;
+    return LBMBT_OK;
+}
+
+static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool series, void* field_dev)
+{
+    if (c->geoms.empty()) return fail(c, LBMBT_ESTATE, "no geometry set");
+    if (c->n_phases == 0) return fail(c, LBMBT_ESTATE, "phases not set");
+    if (c->n_steps == 0) return fail(c, LBMBT_ESTATE, "sequence not set");
+    if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
+    if (field_dev && n_members != 1) return fail(c, LBMBT_EINVAL, "field output needs a single member");
+    int rc = set_device(c);
+    if (rc) return rc;
+    std::vector<MemberDesc> descs(n_members);
+    size_t max_plane = 0;
+    for (int m = 0; m < n_members; ++m) {
+        const lbmbt_member& mm = mem[m];
+        if (mm.geometry < 0 || mm.geometry >= (int)c->geoms.size())
+            return fail(c, LBMBT_EINVAL, "member %d: geometry %d not set", m, mm.geometry);
+        const Geom& g = c->geoms[mm.geometry];
+        if (g.max_phase >= c->n_phases)
+            return fail(c, LBMBT_ESTATE, "geometry %d uses phase %d but %d phases are set", mm.geometry, g.max_phase,
+                        c->n_phases);
+        if (!(mm.kappa_um_ms >= 0)) return fail(c, LBMBT_EINVAL, "member %d: kappa must be >= 0", m);
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(mm.gamma_G0[a])) return fail(c, LBMBT_EINVAL, "member %d: gradient not finite", m);
+        MemberDesc& d = descs[m];
+        memset(&d, 0, sizeof d);
+        d.mask = g.d_mask;
+        d.N = g.N;
+        d.plane = (g.N + 63) / 64 * 64;
+        d.nx = g.nx; d.ny = g.ny; d.nz = g.nz;
+        d.dx = g.dx;
+        for (int a = 0; a < 3; ++a) {
+            d.gG[a] = mm.gamma_G0[a];
+            d.ctheta[a] = (float)(-mm.gamma_G0[a] * g.dx * c->dt);
+            if (g.bc[a] == LBMBT_BC_PERIODIC) d.bc[a] = BC_PER;
+            else if (mm.gamma_G0[a] == 0.0) d.bc[a] = BC_MIR;
+            else {
+                for (int b = 0; b < 3; ++b)
+                    if (b != a && mm.gamma_G0[b] != 0.0)
+                        return fail(c, LBMBT_EUNSUPPORTED,
+                                    "member %d: mirror face on axis %d with a gradient neither normal nor parallel "
+                                    "to it (Sec. 2.4.4)", m, a);
+                d.bc[a] = BC_MIR_CONJ;
+            }
+        }
+        for (int p = 0; p < 4; ++p) {
+            const double tau = 0.5 + c->dt * c->D[p] / (EPS_D * g.dx * g.dx);   // Eq. tau_def
+            if (p < c->n_phases && !(tau > 0.5))
+                return fail(c, LBMBT_EUNSTABLE, "phase %d: tau = %.17g <= 1/2", p, tau);
+            d.omega[p] = (float)(1.0 / tau);
+            d.eps[p] = std::isinf(c->T2[p]) ? 0.f : (float)(-std::expm1(-c->dt / c->T2[p]));
+        }
+        const double kap = mm.kappa_um_ms;
+        const double cP = EPS_D * g.dx / (2.0 * c->dt);   // P = cP / kappa  (Eq. P_def)
+        d.s_share = std::isinf(kap) ? 1.f : (float)(kap / (kap + cP));
+        if ((size_t)d.plane > max_plane) max_plane = d.plane;
+    }
+    invalidate_run(c);
+    c->n_members = n_members;
+    c->members.assign(mem, mem + n_members);
+    c->descs = descs;
+    c->series_mode = series;
+    c->n_slots = 2;
+    // state: n_slots * 7 planes per member
+    size_t total = 0;
+    for (auto& d : c->descs) total += (size_t)c->n_slots * 7 * d.plane * sizeof(float2);
+    rc = grow(c, &c->d_state, &c->cap_state, total);
+    if (rc) return rc;
+    size_t off = 0;
+    for (auto& d : c->descs) {
+        d.state = c->d_state + off / sizeof(float2);
+        off += (size_t)c->n_slots * 7 * d.plane * sizeof(float2);
+    }
+    if (field_dev) c->descs[0].field = (float2*)field_dev;
+    rc = grow(c, &c->d_Z, &c->cap_Z, sizeof(double2) * n_members);
+    if (!rc && series) rc = grow(c, &c->d_series, &c->cap_series, sizeof(double2) * n_members * c->n_steps);
+    if (rc) return rc;
+    if (c->autotune) {
+        rc = autotune(c);
+        if (rc) return rc;
+    }
+    rc = build_worklist(c, c->block, c->spt);
+    if (rc) return rc;
+    rc = init_state(c);
+    if (rc) return rc;
+    c->field_dev = field_dev;
+    c->prepared = true;
+    return LBMBT_OK;
+}
+
+static int capture_graph(lbmbt_ctx* c)
+{
+    drop_graph(c);
+    cudaGraph_t g;
+    CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = c->launches;
+    for (int i = 0; i < GRAPH_CHUNK; ++i) {
+        int rc = issue_step(c);
+        if (rc) {
+            cudaStreamEndCapture(c->stream, &g);
+            return rc;
+        }
+    }
+    c->launches = before;  // counted when replayed
+    CU(c, cudaStreamEndCapture(c->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->graph = nullptr; return fail(c, LBMBT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+    c->graph_series = c->series_mode ? 1 : 0;
+    return LBMBT_OK;
+}
+
+// Advance n steps; the signal (and field) of the last step is produced when asked.
+static int advance(lbmbt_ctx* c, long long n, bool want_signal)
+{
+    if (!c->prepared) return fail(c, LBMBT_ESTATE, "no prepared run");
+    if (n < 0 || c->k_cur + n > c->n_steps)
+        return fail(c, LBMBT_EINVAL, "advance past the end of the sequence (%lld + %lld > %lld)", c->k_cur, n,
+                    c->n_steps);
+    if (n == 0) return LBMBT_OK;
+    const long long last = c->k_cur + n - 1;
+    int rc = write_ctl(c, want_signal ? (int)last : -1, (c->field_dev && last == c->n_steps - 1) ? (int)last : -1);
+    if (rc) return rc;
+    long long left = n;
+    if (c->use_graph && n >= GRAPH_CHUNK) {
+        if (!c->graph || c->graph_series != (c->series_mode ? 1 : 0)) {
+            rc = capture_graph(c);
+            if (rc) return rc;
+        }
+        const int per = c->series_mode ? 2 : 1;
+        while (left >= GRAPH_CHUNK) {
+            CU(c, cudaGraphLaunch(c->graph, c->stream));
+            c->launches += GRAPH_CHUNK * per;
+            left -= GRAPH_CHUNK;
+        }
+    }
+    while (left > 0) {
+        rc = issue_step(c);
+        if (rc) return rc;
+        --left;
+    }
+    c->k_cur += n;
+    if (want_signal && !c->series_mode) {
+        CU(c, launch_reduce(c->d_partial, c->d_tile_start, c->n_members, c->d_Z, nullptr, 0, c->d_ctl, c->stream));
+        c->launches++;
+    }
+    return LBMBT_OK;
+}
+
+static int fetch_signal(lbmbt_ctx* c, double* signal_out, double* series_out)
+{
+    std::vector<double2> Z(c->n_members);
+    CU(c, cudaMemcpyAsync(Z.data(), c->d_Z, sizeof(double2) * c->n_members, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double2> ser;
+    if (series_out && c->series_mode) {
+        ser.resize((size_t)c->n_members * c->n_steps);
+        CU(c, cudaMemcpyAsync(ser.data(), c->d_series, sizeof(double2) * ser.size(), cudaMemcpyDeviceToHost,
+                              c->stream));
+    }
+    int rc = sync(c);
+    if (rc) return rc;
+    for (int m = 0; m < c->n_members; ++m) {
+        const double N = (double)c->descs[m].N;
+        if (signal_out) {
+            signal_out[3 * m] = Z[m].x;
+            signal_out[3 * m + 1] = Z[m].y;
+            signal_out[3 * m + 2] = std::hypot(Z[m].x, Z[m].y) / N;
+        }
+    }
+    if (series_out && c->series_mode)
+        for (size_t i = 0; i < ser.size(); ++i) { series_out[2 * i] = ser[i].x; series_out[2 * i + 1] = ser[i].y; }
+    return LBMBT_OK;
+}
+
+// ---------------------------------------------------------------- runs
+static lbmbt_member plain_member(lbmbt_ctx* c)
+{
+    lbmbt_member m;
+    for (int a = 0; a < 3; ++a) m.gamma_G0[a] = c->gG[a];
+    m.geometry = 0;
+    m.kappa_um_ms = c->kappa;
+    return m;
+}
+
+extern "C" int lbmbt_run(lbmbt_ctx* c, double* signal_out, void* field_out_dev, double* series_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!signal_out) return fail(c, LBMBT_EINVAL, "signal_out is NULL");
+    lbmbt_member m = plain_member(c);
+    int rc = prepare(c, 1, &m, series_out != nullptr, field_out_dev);
+    if (!rc) rc = advance(c, c->n_steps, true);
+    if (!rc) rc = fetch_signal(c, signal_out, series_out);
+    return rc;
+}
+
+extern "C" int lbmbt_run_batch(lbmbt_ctx* c, int n_members, const lbmbt_member* members, double* signal_out,
+                               double* series_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!members || !signal_out) return fail(c, LBMBT_EINVAL, "members / signal_out is NULL");
+    int rc = prepare(c, n_members, members, series_out != nullptr, nullptr);
+    if (!rc) rc = advance(c, c->n_steps, true);
+    if (!rc) rc = fetch_signal(c, signal_out, series_out);
+    return rc;
+}
+
+extern "C" int lbmbt_prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* members)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (n_members == 0) {
+        lbmbt_member m = plain_member(c);
+        int rc = prepare(c, 1, &m, false, nullptr);
+        return rc ? rc : sync(c);
+    }
+    if (!members) return fail(c, LBMBT_EINVAL, "members is NULL");
+    int rc = prepare(c, n_members, members, false, nullptr);
+    return rc ? rc : sync(c);
+}
+
+extern "C" int lbmbt_advance(lbmbt_ctx* c, int64_t n_steps, int want_signal, double* signal_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    int rc = advance(c, n_steps, want_signal != 0);
+    if (rc) return rc;
+    if (want_signal && signal_out) return fetch_signal(c, signal_out, nullptr);
+    return sync(c);
+}
+
+extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
+{
+    if (!c) return LBMBT_EINVAL;
+    switch (opt) {
+    case LBMBT_OPT_GRAPH: c->use_graph = v != 0; break;
+    case LBMBT_OPT_AUTOTUNE: c->autotune = v != 0; break;
+    case LBMBT_OPT_BLOCK:
+        if (v < 64 || v > 512 || (v & 31)) return fail(c, LBMBT_EINVAL, "block must be a multiple of 32 in 64..512");
+        c->block = (int)v;
+        break;
+    case LBMBT_OPT_SPT:
+        if (v != 1 && v != 2 && v != 4) return fail(c, LBMBT_EINVAL, "sites per thread must be 1, 2 or 4");
+        c->spt = (int)v;
+        break;
+    default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
+    }
+    invalidate_run(c);
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
+{
+    if (!c || !v) return LBMBT_EINVAL;
+    switch (opt) {
+    case LBMBT_OPT_GRAPH: *v = c->use_graph; break;
+    case LBMBT_OPT_AUTOTUNE: *v = c->autotune; break;
+    case LBMBT_OPT_BLOCK: *v = c->block; break;
+    case LBMBT_OPT_SPT: *v = c->spt; break;
+    default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
+    }
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_launch_count(lbmbt_ctx* c, int64_t* out)
+{
+    if (!c || !out) return LBMBT_EINVAL;
+    *out = c->launches;
+    return LBMBT_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+static size_t grad_bytes_per_member(const lbmbt_ctx* c, long long plane, int ck)
+{
+    const long long n_ck = (c->n_steps + ck - 1) / ck;
+    return (size_t)(2 + n_ck + ck + 1) * 7 * plane * sizeof(float2);
+}
+
+// One group of members: checkpointed forward pass, then segments in reverse:
+// recompute the segment's forward levels from its checkpoint, then run the
+// adjoint sweep back through it.
+static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, double* sig, double* dD, double* dT2,
+                      double* dk)
+{
+    const int saved_block = c->block;
+    if (c->block > 256) c->block = 256;
+    int rc = prepare(c, n, mem, false, nullptr);
+    c->block = saved_block;
+    if (rc) return rc;
+    const long long K = c->n_steps;
+    const long long n_ck = (K + ck - 1) / ck;
+    size_t lvl_total = 0;
+    for (auto& d : c->descs) lvl_total += (size_t)7 * d.plane;
+    rc = grow(c, &c->d_ck, &c->cap_ck, lvl_total * n_ck * sizeof(float2));
+    if (!rc) rc = grow(c, &c->d_seg, &c->cap_seg, lvl_total * (ck + 1) * sizeof(float2));
+    if (!rc) rc = grow(c, &c->d_gacc, &c->cap_gacc, sizeof(double) * NGACC * c->n_tiles);
+    if (!rc) rc = grow(c, &c->d_gout, &c->cap_gout, sizeof(double) * NGACC * n);
+    if (!rc) rc = grow(c, &c->d_laminit, &c->cap_laminit, sizeof(double2) * n);
+    if (rc) return rc;
+    // per-member bases of checkpoints and segment levels
+    std::vector<float2*> ckb(n), segb(n);
+    {
+        size_t oc = 0, os = 0;
+        for (int m = 0; m < n; ++m) {
+            const size_t lv = (size_t)7 * c->descs[m].plane;
+            ckb[m] = c->d_ck + oc;
+            segb[m] = c->d_seg + os;
+            oc += lv * n_ck;
+            os += lv * (ck + 1);
+        }
+    }
+    auto copy_level = [&](int m, const float2* from, float2* to) -> int {
+        const size_t lv = (size_t)7 * c->descs[m].plane;
+        CU(c, cudaMemcpyAsync(to, from, lv * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+        return LBMBT_OK;
+    };
+    // forward with checkpoints u^0, u^ck, u^2ck, ...
+    rc = write_ctl(c, (int)(K - 1), -1);
+    if (rc) return rc;
+    for (int m = 0; m < n; ++m)
+        if ((rc = copy_level(m, c->descs[m].state, ckb[m]))) return rc;
+    for (long long k = 0; k < K; ++k) {
+        if ((rc = issue_step(c))) return rc;
+        const long long kn = k + 1;
+        if (kn % ck == 0 && kn < K)
+            for (int m = 0; m < n; ++m) {
+                const size_t lv = (size_t)7 * c->descs[m].plane;
+                if ((rc = copy_level(m, c->descs[m].state + (kn & 1) * lv, ckb[m] + (kn / ck) * lv))) return rc;
+            }
+    }
+    c->k_cur = K;
+    CU(c, launch_reduce(c->d_partial, c->d_tile_start, n, c->d_Z, nullptr, 0, c->d_ctl, c->stream));
+    c->launches++;
+    std::vector<double2> Z(n);
+    CU(c, cudaMemcpyAsync(Z.data(), c->d_Z, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = sync(c))) return rc;
+    std::vector<double2> L(n);
+    for (int m = 0; m < n; ++m) {
+        const double N = (double)c->descs[m].N;
+        const double a = std::hypot(Z[m].x, Z[m].y);
+        sig[3 * m] = Z[m].x;
+        sig[3 * m + 1] = Z[m].y;
+        sig[3 * m + 2] = a / N;
+        L[m] = a > 0 ? make_double2(Z[m].x / (N * a), Z[m].y / (N * a)) : make_double2(0.0, 0.0);
+    }
+    CU(c, cudaMemcpyAsync(c->d_laminit, L.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, c->stream));
+    // descriptors for the reverse pass: forward levels in the segment buffer,
+    // adjoint ping-pong in the (now free) forward state
+    std::vector<MemberDesc> rd = c->descs;
+    for (int m = 0; m < n; ++m) {
+        rd[m].adj = c->descs[m].state;
+        rd[m].state = segb[m];
+    }
+    CU(c, cudaMemcpyAsync(c->d_desc, rd.data(), sizeof(MemberDesc) * n, cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * NGACC * c->n_tiles, c->stream));
+    std::vector<double> F(K + 1);
+    F[0] = 0.0;
+    for (long long k = 0; k < K; ++k) F[k + 1] = F[k] + c->f[k] * c->dt;
+    AdjointArgs aa;
+    aa.members = c->d_desc;
+    aa.tile_start = c->d_tile_start;
+    aa.n_members = n;
+    aa.lam_init = c->d_laminit;
+    aa.gacc = c->d_gacc;
+    int parity = 1;
+    for (long long seg = n_ck - 1; seg >= 0; --seg) {
+        const long long k0 = seg * ck, k1 = std::min(K, k0 + ck);
+        for (int m = 0; m < n; ++m) {
+            const size_t lv = (size_t)7 * c->descs[m].plane;
+            if ((rc = copy_level(m, ckb[m] + seg * lv, segb[m]))) return rc;
+        }
+        if (k1 - k0 - 1 > 0) {
+            c->k_cur = k0;
+            if ((rc = write_ctl(c, -1, -1, (int)k0, ck + 1))) return rc;
+            for (long long k = k0; k < k1 - 1; ++k)
+                if ((rc = issue_step(c))) return rc;
+        }
+        for (long long k = k1; k > k0; --k) {
+            aa.k = (int)k;
+            aa.first = (k == K) ? 1 : 0;
+            aa.fwd_slot = (int)(k - 1 - k0);
+            aa.lam_parity = parity;
+            aa.fprev = (float)c->f[k - 1];
+            aa.Fprev = F[k - 1];
+            CU(c, launch_adjoint(aa, F[k], c->n_tiles, c->tile_block, c->tile_spt, c->stream));
+            c->launches++;
+            parity ^= 1;
+        }
+    }
+    CU(c, launch_reduce_grad(c->d_gacc, c->d_tile_start, n, c->d_gout, c->stream));
+    c->launches++;
+    std::vector<double> G((size_t)NGACC * n);
+    CU(c, cudaMemcpyAsync(G.data(), c->d_gout, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = sync(c))) return rc;
+    c->prepared = false;  // descriptors now describe the reverse pass
+    // chain rule to the physical parameters
+    for (int m = 0; m < n; ++m) {
+        const double dx = c->descs[m].dx, dt = c->dt;
+        const double* g = &G[(size_t)NGACC * m];
+        for (int p = 0; p < c->n_phases; ++p) {
+            const double tau = 0.5 + dt * c->D[p] / (EPS_D * dx * dx);
+            const double om = 1.0 / tau;
+            dD[(size_t)m * c->n_phases + p] = g[p] * (-om * om * dt / (EPS_D * dx * dx));
+            const double T2 = c->T2[p];
+            if (std::isinf(T2)) {
+                dT2[(size_t)m * c->n_phases + p] = 0.0;
+            } else {
+                const double one_m_eps = std::exp(-dt / T2);
+                dT2[(size_t)m * c->n_phases + p] = g[4 + p] * (-one_m_eps * dt / (T2 * T2));
+            }
+        }
+        const double kap = mem[m].kappa_um_ms;
+        const double cP = EPS_D * dx / (2.0 * dt);
+        dk[m] = std::isinf(kap) ? 0.0 : g[8] * cP / ((kap + cP) * (kap + cP));
+    }
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member* members, int checkpoint_every,
+                                double* signal_out, double* dS_dD, double* dS_dT2, double* dS_dkappa)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!members || !signal_out || !dS_dD || !dS_dT2 || !dS_dkappa)
+        return fail(c, LBMBT_EINVAL, "NULL argument");
+    if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
+    if (c->geoms.empty() || c->n_phases == 0 || c->n_steps == 0) return fail(c, LBMBT_ESTATE, "set-up incomplete");
+    const int ck = checkpoint_every > 0 ? checkpoint_every : 64;
+    int rc = set_device(c);
+    if (rc) return rc;
+    // group members so one group's levels fit in the free device memory
+    size_t free_b = 0, total_b = 0;
+    CU(c, cudaMemGetInfo(&free_b, &total_b));
+    const size_t held = c->cap_state + c->cap_ck + c->cap_seg;
+    const size_t budget = (size_t)((double)(free_b + held) * 0.8);
+    int m0 = 0;
+    while (m0 < n_members) {
+        size_t used = 0;
+        int m1 = m0;
+        while (m1 < n_members) {
+            const lbmbt_member& mm = members[m1];
+            if (mm.geometry < 0 || mm.geometry >= (int)c->geoms.size())
+                return fail(c, LBMBT_EINVAL, "member %d: geometry %d not set", m1, mm.geometry);
+            const long long plane = (c->geoms[mm.geometry].N + 63) / 64 * 64;
+            const size_t b = grad_bytes_per_member(c, plane, ck);
+            if (m1 > m0 && used + b > budget) break;
+            used += b;
+            ++m1;
+        }
+        if (used > budget) return fail(c, LBMBT_ENOMEM, "one member needs %zu bytes for the adjoint", used);
+        rc = grad_group(c, m1 - m0, members + m0, ck, signal_out + 3 * m0, dS_dD + (size_t)m0 * c->n_phases,
+                        dS_dT2 + (size_t)m0 * c->n_phases, dS_dkappa + m0);
+        if (rc) return rc;
+        m0 = m1;
+    }
+    return LBMBT_OK;
+}
+
+extern "C" int lbmbt_grad(lbmbt_ctx* c, int checkpoint_every, double* signal_out, double* dS_dD, double* dS_dT2,
+                          double* dS_dkappa)
+{
+    if (!c) return LBMBT_EINVAL;
+    lbmbt_member m = plain_member(c);
+    return lbmbt_grad_batch(c, 1, &m, checkpoint_every, signal_out, dS_dD, dS_dT2, dS_dkappa);
+}

@@ -1,0 +1,288 @@
+"""ctypes binding of ``liblbmbt.so`` (C ABI in ``include/lbmbt.h``).
+
+Argument marshalling only: every step of the sweep runs in the CUDA library.
+Loading fails loudly if the library is missing -- there is no CPU fallback.
+The low-level functions keep the C names; ``Solver`` is a thin convenience
+wrapper that owns one context and accepts numpy arrays / torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbmbt.so")
+
+LBMBT_OK = 0
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5: "EUNSUPPORTED",
+          -6: "EDEVICE", -7: "ESTATE"}
+BC_PERIODIC = 0
+BC_MIRROR = 1
+OPT_GRAPH, OPT_AUTOTUNE, OPT_BLOCK, OPT_SPT = 1, 2, 3, 4
+
+# every entry point declared in include/lbmbt.h
+EXPORTS = [
+    "lbmbt_create", "lbmbt_destroy", "lbmbt_last_error", "lbmbt_version", "lbmbt_set_geometry",
+    "lbmbt_add_geometry", "lbmbt_get_mask", "lbmbt_set_phases", "lbmbt_set_permeability",
+    "lbmbt_set_sequence", "lbmbt_pgse", "lbmbt_run", "lbmbt_run_batch", "lbmbt_grad",
+    "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
+    "lbmbt_launch_count",
+]
+
+
+class LbmbtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Member(ctypes.Structure):
+    """``lbmbt_member``: gradient, geometry index, permeability of one batch member."""
+    _fields_ = [("gamma_G0", ctypes.c_double * 3), ("geometry", ctypes.c_int), ("kappa_um_ms", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load ``liblbmbt.so``; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"liblbmbt.so not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+            sig = {
+                "lbmbt_create": [ctypes.POINTER(P), I, P],
+                "lbmbt_destroy": [P],
+                "lbmbt_set_geometry": [P, I, I, I, D, P, I, I, P, P],
+                "lbmbt_add_geometry": [P, I, I, I, D, P, I, I, P, P, ctypes.POINTER(I)],
+                "lbmbt_get_mask": [P, I, P],
+                "lbmbt_set_phases": [P, I, P, P],
+                "lbmbt_set_permeability": [P, D],
+                "lbmbt_set_sequence": [P, D, I64, P, P],
+                "lbmbt_pgse": [D, D, D, D, P, P, ctypes.POINTER(I64), P],
+                "lbmbt_run": [P, P, P, P],
+                "lbmbt_run_batch": [P, I, P, P, P],
+                "lbmbt_grad": [P, I, P, P, P, P],
+                "lbmbt_grad_batch": [P, I, P, I, P, P, P, P],
+                "lbmbt_set_option": [P, I, I64],
+                "lbmbt_get_option": [P, I, ctypes.POINTER(I64)],
+                "lbmbt_prepare": [P, I, P],
+                "lbmbt_advance": [P, I64, I, P],
+                "lbmbt_launch_count": [P, ctypes.POINTER(I64)],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = I
+            L.lbmbt_last_error.argtypes = [P]
+            L.lbmbt_last_error.restype = ctypes.c_char_p
+            L.lbmbt_version.argtypes = []
+            L.lbmbt_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    """Host numpy array, torch tensor (host or device) or raw int -> void*."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(type(a))
+
+
+def pgse(b_s_mm2, delta, Delta, dt, direction=(1.0, 0.0, 0.0)):
+    """``lbmbt_pgse``: returns (gamma_G0[3], f[K])."""
+    L = lib()
+    d = np.ascontiguousarray(direction, np.float64)
+    g = np.zeros(3)
+    n = ctypes.c_int64(0)
+    rc = L.lbmbt_pgse(b_s_mm2, delta, Delta, dt, _p(d), _p(g), ctypes.byref(n), None)
+    if rc:
+        raise LbmbtError(rc, "lbmbt_pgse: invalid PGSE parameters")
+    f = np.empty(n.value)
+    L.lbmbt_pgse(b_s_mm2, delta, Delta, dt, _p(d), _p(g), ctypes.byref(n), _p(f))
+    return g, f
+
+
+class Solver:
+    """One library context (device + stream) with numpy/torch marshalling."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.L = lib()
+        h = ctypes.c_void_p()
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        rc = self.L.lbmbt_create(ctypes.byref(h), int(device), s)
+        if rc:
+            raise LbmbtError(rc, self.L.lbmbt_last_error(None).decode())
+        self.h = h
+        self.n_sites = []
+        self.n_steps = 0
+        self.n_phases = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lbmbt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, rc, what):
+        if rc:
+            raise LbmbtError(rc, f"{what}: {self.L.lbmbt_last_error(self.h).decode()}")
+
+    # --- set-up -------------------------------------------------------------
+    def set_geometry(self, labels, phase_of_label, dx, bc=(0, 0, 0), add=False):
+        """labels: int32 [nz, ny, nx] numpy (host) or torch CUDA tensor (device)."""
+        on_dev = hasattr(labels, "is_cuda") and labels.is_cuda
+        if on_dev:
+            import torch
+            assert labels.dtype == torch.int32 and labels.is_contiguous()
+            nz, ny, nx = labels.shape
+        else:
+            labels = np.ascontiguousarray(labels, np.int32)
+            nz, ny, nx = labels.shape
+        pol = np.ascontiguousarray(phase_of_label, np.uint8)
+        bcv = np.ascontiguousarray(bc, np.int32)
+        if add:
+            idx = ctypes.c_int(0)
+            self._chk(self.L.lbmbt_add_geometry(self.h, nx, ny, nz, float(dx), _p(labels), int(on_dev),
+                                                int(pol.size), _p(pol), _p(bcv), ctypes.byref(idx)),
+                      "add_geometry")
+            self.n_sites.append(nx * ny * nz)
+            return idx.value
+        self._chk(self.L.lbmbt_set_geometry(self.h, nx, ny, nz, float(dx), _p(labels), int(on_dev),
+                                            int(pol.size), _p(pol), _p(bcv)), "set_geometry")
+        self.n_sites = [nx * ny * nz]
+        self.shape = (nz, ny, nx)
+        return 0
+
+    def add_geometry(self, labels, phase_of_label, dx, bc=(0, 0, 0)):
+        return self.set_geometry(labels, phase_of_label, dx, bc, add=True)
+
+    def get_mask(self, index=0, shape=None):
+        n = self.n_sites[index]
+        out = np.empty(n, np.uint8)
+        self._chk(self.L.lbmbt_get_mask(self.h, index, _p(out)), "get_mask")
+        return out.reshape(shape) if shape is not None else out
+
+    def set_phases(self, D, T2):
+        Dv = np.ascontiguousarray(np.atleast_1d(D), np.float64)
+        T2v = np.ascontiguousarray(np.atleast_1d(T2), np.float64)
+        self._chk(self.L.lbmbt_set_phases(self.h, int(Dv.size), _p(Dv), _p(T2v)), "set_phases")
+        self.n_phases = int(Dv.size)
+
+    def set_permeability(self, kappa):
+        self._chk(self.L.lbmbt_set_permeability(self.h, float(kappa)), "set_permeability")
+
+    def set_sequence(self, dt, f, gG):
+        fv = np.ascontiguousarray(f, np.float64)
+        gv = np.ascontiguousarray(gG, np.float64)
+        self._chk(self.L.lbmbt_set_sequence(self.h, float(dt), int(fv.size), _p(fv), _p(gv)), "set_sequence")
+        self.n_steps = int(fv.size)
+
+    def set_option(self, opt, value):
+        self._chk(self.L.lbmbt_set_option(self.h, int(opt), int(value)), "set_option")
+
+    def get_option(self, opt):
+        v = ctypes.c_int64(0)
+        self._chk(self.L.lbmbt_get_option(self.h, int(opt), ctypes.byref(v)), "get_option")
+        return v.value
+
+    # --- runs ---------------------------------------------------------------
+    def run(self, field=None, series=False):
+        """Plain run.  ``field``: torch complex64 CUDA tensor [N] (or None).
+        Returns dict(Z, S[, series])."""
+        sig = np.zeros(3)
+        ser = np.zeros(2 * self.n_steps) if series else None
+        self._chk(self.L.lbmbt_run(self.h, _p(sig), _p(field), _p(ser)), "run")
+        out = {"Z": complex(sig[0], sig[1]), "S": float(sig[2])}
+        if series:
+            out["series"] = ser[0::2] + 1j * ser[1::2]
+        return out
+
+    @staticmethod
+    def members(gGs, geometry=0, kappa=math.inf):
+        gGs = np.atleast_2d(np.asarray(gGs, np.float64))
+        n = gGs.shape[0]
+        geo = np.broadcast_to(np.asarray(geometry), (n,))
+        kap = np.broadcast_to(np.asarray(kappa, np.float64), (n,))
+        arr = (Member * n)()
+        for i in range(n):
+            arr[i].gamma_G0[:] = [float(v) for v in gGs[i]]
+            arr[i].geometry = int(geo[i])
+            arr[i].kappa_um_ms = float(kap[i])
+        return arr
+
+    def run_batch(self, members, series=False):
+        n = len(members)
+        sig = np.zeros(3 * n)
+        ser = np.zeros(2 * n * self.n_steps) if series else None
+        self._chk(self.L.lbmbt_run_batch(self.h, n, members, _p(sig), _p(ser)), "run_batch")
+        sig = sig.reshape(n, 3)
+        out = {"Z": sig[:, 0] + 1j * sig[:, 1], "S": sig[:, 2].copy()}
+        if series:
+            s = ser.reshape(n, self.n_steps, 2)
+            out["series"] = s[..., 0] + 1j * s[..., 1]
+        return out
+
+    def grad(self, checkpoint_every=64):
+        sig = np.zeros(3)
+        dD = np.zeros(self.n_phases)
+        dT2 = np.zeros(self.n_phases)
+        dk = np.zeros(1)
+        self._chk(self.L.lbmbt_grad(self.h, int(checkpoint_every), _p(sig), _p(dD), _p(dT2), _p(dk)), "grad")
+        return {"Z": complex(sig[0], sig[1]), "S": float(sig[2]), "dD": dD, "dT2": dT2, "dkappa": float(dk[0])}
+
+    def grad_batch(self, members, checkpoint_every=64):
+        n = len(members)
+        sig = np.zeros(3 * n)
+        dD = np.zeros(n * self.n_phases)
+        dT2 = np.zeros(n * self.n_phases)
+        dk = np.zeros(n)
+        self._chk(self.L.lbmbt_grad_batch(self.h, n, members, int(checkpoint_every), _p(sig), _p(dD), _p(dT2),
+                                          _p(dk)), "grad_batch")
+        sig = sig.reshape(n, 3)
+        return {"Z": sig[:, 0] + 1j * sig[:, 1], "S": sig[:, 2].copy(),
+                "dD": dD.reshape(n, -1), "dT2": dT2.reshape(n, -1), "dkappa": dk}
+
+    # --- timing hooks -------------------------------------------------------
+    def prepare(self, members=None):
+        if members is None:
+            self._chk(self.L.lbmbt_prepare(self.h, 0, None), "prepare")
+        else:
+            self._chk(self.L.lbmbt_prepare(self.h, len(members), members), "prepare")
+
+    def advance(self, n_steps, want_signal=False, n_members=1):
+        sig = np.zeros(3 * n_members) if want_signal else None
+        self._chk(self.L.lbmbt_advance(self.h, int(n_steps), int(bool(want_signal)), _p(sig)), "advance")
+        return sig.reshape(n_members, 3) if want_signal else None
+
+    def launch_count(self):
+        v = ctypes.c_int64(0)
+        self._chk(self.L.lbmbt_launch_count(self.h, ctypes.byref(v)), "launch_count")
+        return v.value

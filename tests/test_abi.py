@@ -1,0 +1,65 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/lbmbt.h, and its host-only helpers agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_00908_gb300 import lbmbt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lbmbt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbmbt_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = lbmbt.lib()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(lbmbt.EXPORTS)
+
+
+def test_version_string():
+    assert b"sm_103a" in lbmbt.lib().lbmbt_version()
+
+
+@pytest.mark.parametrize("b,delta,Delta,dt,d", [
+    (1000.0, 5.0, 20.0, 0.0125, (1, 0, 0)),
+    (3000.0, 10.0, 30.0, 0.00625, (0.3, -0.5, 0.8)),
+    (0.0, 2.0, 6.0, 0.05, (0, 0, 1)),
+])
+def test_pgse_matches_oracle(b, delta, Delta, dt, d):
+    g1, f1 = lbmbt.pgse(b, delta, Delta, dt, d)
+    g2, f2 = oracle.pgse(b, delta, Delta, dt, d)
+    assert np.array_equal(f1, f2)
+    np.testing.assert_allclose(g1, g2, rtol=1e-15, atol=0)
+
+
+def test_pgse_rejects_non_integer_timing():
+    with pytest.raises(lbmbt.LbmbtError):
+        lbmbt.pgse(1000.0, 5.003, 20.0, 0.0125)
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(lbmbt.LbmbtError) as e:
+        lbmbt.Solver(0)
+    assert e.value.code in (-1, -3)
+
+
+def test_null_arguments_rejected():
+    L = lbmbt.lib()
+    assert L.lbmbt_create(None, 0, None) == -1
+    assert L.lbmbt_destroy(None) == 0
+    assert L.lbmbt_run(None, None, None, None) == -1

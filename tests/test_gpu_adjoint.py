@@ -1,0 +1,161 @@
+"""GPU adjoint sweep: dS/d(D_p, T2_p, kappa) against central finite
+differences (h = 1e-3 relative) of the FP64 oracle and of the GPU forward."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_00908_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+INF = math.inf
+H = 1e-3
+
+
+@pytest.fixture(scope="module")
+def lb():
+    from paper_1907_00908_gb300 import lbmbt
+    lbmbt.lib()
+    return lbmbt
+
+
+def _setup(lb, geom, bc, D, T2, kap, dt, f, gG):
+    s = lb.Solver(0)
+    s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, bc)
+    s.set_phases(D, T2)
+    s.set_permeability(kap)
+    s.set_sequence(dt, f, gG)
+    return s
+
+
+def _fd(fun, D, T2, kap):
+    """Central differences of S in every parameter (relative step H)."""
+    out = {"dD": [], "dT2": [], "dkappa": None}
+    for p in range(len(D)):
+        Dp, Dm = list(D), list(D)
+        Dp[p] *= 1 + H
+        Dm[p] *= 1 - H
+        out["dD"].append((fun(Dp, T2, kap) - fun(Dm, T2, kap)) / (2 * H * D[p]))
+    for p in range(len(T2)):
+        if math.isinf(T2[p]):
+            out["dT2"].append(0.0)
+            continue
+        Tp, Tm = list(T2), list(T2)
+        Tp[p] *= 1 + H
+        Tm[p] *= 1 - H
+        out["dT2"].append((fun(D, Tp, kap) - fun(D, Tm, kap)) / (2 * H * T2[p]))
+    out["dkappa"] = (fun(D, T2, kap * (1 + H)) - fun(D, T2, kap * (1 - H))) / (2 * H * kap)
+    return out
+
+
+def _logvec(g, D, T2, kap):
+    """Gradient in log-parameters, theta * dS/dtheta, as one vector."""
+    return np.concatenate([np.asarray(g["dD"]) * D,
+                           np.asarray(g["dT2"]) * np.where(np.isinf(T2), 0.0, T2),
+                           [g["dkappa"] * kap]])
+
+
+CASES = {
+    "cylinders_periodic": dict(geom=lambda: synth.cylinders(24, 1.0, fraction=0.5, seed=3), bc=(0, 0, 0),
+                               D=[2.0, 1.0], T2=[80.0, 50.0], kap=0.05, dt=0.05, b=1500.0,
+                               delta=2.0, Delta=6.0, d=(1, 1, 0)),
+    "spheres_oblique": dict(geom=lambda: synth.spheres(20, 1.0, rmin=2.0, rmax=3.5, fraction=0.45, seed=4),
+                            bc=(0, 0, 0), D=[2.0, 1.0], T2=[80.0, 50.0], kap=0.02, dt=0.05, b=2500.0,
+                            delta=2.0, Delta=5.0, d=(0.3, -0.5, 0.8)),
+    "voronoi_mirror": dict(geom=lambda: synth.crop(synth.voronoi_tissue(40, 0.5, cell_diam=6.0, vessel_radius=1.5,
+                                                                        seed=2), 22),
+                           bc=(1, 1, 1), D=[1.0, 2.5, 3.0], T2=[50.0, 80.0, 80.0], kap=0.01, dt=0.025,
+                           b=1000.0, delta=1.0, Delta=3.0, d=(1, 0, 0)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_matches_oracle_finite_differences(lb, name):
+    c = CASES[name]
+    geom = c["geom"]()
+    gG, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
+    s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gG)
+    g = s.grad(checkpoint_every=16)
+    s.close()
+
+    def S(D, T2, kap):
+        return oracle.run(geom.labels, geom.dx, geom.phase_of_label, c["bc"], D, T2, kap, c["dt"], f, gG)["S"]
+
+    fd = _fd(S, c["D"], c["T2"], c["kap"])
+    a = _logvec(g, c["D"], c["T2"], c["kap"])
+    b = _logvec(fd, c["D"], c["T2"], c["kap"])
+    err = np.abs(a - b).max() / np.abs(b).max()
+    print(name, "adjoint", a, "fd", b, "err", err)
+    assert err < 1e-3
+    assert abs(g["S"] - S(c["D"], c["T2"], c["kap"])) < 1e-5 * g["S"]
+
+
+def test_adjoint_matches_gpu_forward_finite_differences(lb):
+    c = CASES["cylinders_periodic"]
+    geom = c["geom"]()
+    gG, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
+    s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gG)
+    g = s.grad()
+
+    def S(D, T2, kap):
+        s.set_phases(D, T2)
+        s.set_permeability(kap)
+        return s.run()["S"]
+
+    fd = _fd(S, c["D"], c["T2"], c["kap"])
+    s.close()
+    a = _logvec(g, c["D"], c["T2"], c["kap"])
+    b = _logvec(fd, c["D"], c["T2"], c["kap"])
+    assert np.abs(a - b).max() / np.abs(b).max() < 2e-2
+
+
+def test_checkpoint_interval_does_not_change_gradients(lb):
+    c = CASES["spheres_oblique"]
+    geom = c["geom"]()
+    gG, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
+    s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gG)
+    ref = s.grad(checkpoint_every=64)
+    for ck in (1, 7, 1000):
+        g = s.grad(checkpoint_every=ck)
+        np.testing.assert_array_equal(g["dD"], ref["dD"])
+        np.testing.assert_array_equal(g["dT2"], ref["dT2"])
+        assert g["dkappa"] == ref["dkappa"]
+    s.close()
+
+
+def test_grad_batch_matches_single(lb):
+    c = CASES["cylinders_periodic"]
+    geom = c["geom"]()
+    _, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
+    dirs = synth.directions_on_sphere(3, seed=5)
+    gGs = [oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], d)[0] for d in dirs]
+    s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gGs[0])
+    mem = lb.Solver.members(gGs, 0, c["kap"])
+    gb = s.grad_batch(mem, checkpoint_every=32)
+    for i, gG in enumerate(gGs):
+        s.set_sequence(c["dt"], f, gG)
+        g = s.grad(checkpoint_every=32)
+        np.testing.assert_allclose(gb["dD"][i], g["dD"], rtol=1e-12)
+        np.testing.assert_allclose(gb["dT2"][i], g["dT2"], rtol=1e-12)
+        assert gb["dkappa"][i] == pytest.approx(g["dkappa"], rel=1e-12)
+    s.close()
+
+
+def test_autograd_function(lb):
+    from paper_1907_00908_gb300.autograd import signal
+    c = CASES["cylinders_periodic"]
+    geom = c["geom"]()
+    gG, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
+    s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gG)
+    D = torch.tensor(c["D"], dtype=torch.float64, requires_grad=True)
+    T2 = torch.tensor(c["T2"], dtype=torch.float64, requires_grad=True)
+    kap = torch.tensor(c["kap"], dtype=torch.float64, requires_grad=True)
+    S = signal(s, D, T2, kap)
+    (2.0 * S).backward()
+    g = s.grad()
+    s.close()
+    np.testing.assert_allclose(D.grad.numpy(), 2.0 * g["dD"], rtol=1e-12)
+    np.testing.assert_allclose(T2.grad.numpy(), 2.0 * g["dT2"], rtol=1e-12)
+    assert float(kap.grad) == pytest.approx(2.0 * g["dkappa"], rel=1e-12)
