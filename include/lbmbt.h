@@ -32,6 +32,7 @@
 #ifndef LBMBT_H
 #define LBMBT_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -192,6 +193,40 @@ int lbmbt_advance(lbmbt_ctx* ctx, int64_t n_steps, int want_signal, double* sign
 
 /* Number of kernel launches the library issued on ctx since creation. */
 int lbmbt_launch_count(lbmbt_ctx* ctx, int64_t* count_out);
+
+/*
+ * Plain sweep that allocates no device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc (device
+ * memory owned by another allocator, loops that must not enter the driver's
+ * allocator, embeddings that forbid allocation after start-up).  It needs no
+ * context and runs the same kernels as lbmbt_run on buffers the caller owns:
+ *   mask_dev   device, one byte per node in the encoding of lbmbt_set_geometry
+ *              (e.g. copied from lbmbt_get_mask);
+ *   state_dev  device, 2 x 7 x plane complex64 values, plane = N rounded up
+ *              to a multiple of 64 (N = nx*ny*nz); with init != 0 (and k0 = 0)
+ *              level 0 is set to M = 1 at equilibrium first.  After the call
+ *              the state of step k0 + n_steps is in level (k0 + n_steps) % 2,
+ *              so calls can be chained with increasing k0;
+ *   f[n_total_steps] (host) the whole waveform, as in lbmbt_set_sequence; the
+ *              call performs steps k0 .. k0 + n_steps - 1 of it;
+ *   signal_out[3] (host) = {Re Z, Im Z, |Z|/N} at the end of the last step.
+ * Its working data (descriptor, step word, waveform tables, per-tile signal
+ * partials) lives in one fixed file-scope device array of 1.25 MiB that every
+ * GPU which loads the library holds until the process exits.  Limits:
+ * N <= 16,777,216 sites and n_total_steps <= 32,768; larger inputs are
+ * rejected with LBMBT_EINVAL and a message in errbuf (errbuf may be NULL).
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call outside any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (different streams or host
+ * threads without ordering) race and give wrong results.  Work is issued on
+ * cuda_stream (NULL = legacy default stream) and the call returns after it
+ * finished.
+ */
+int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const uint8_t* mask_dev, const int bc[3],
+                        int n_phases, const double* D_um2_ms, const double* T2_ms, double kappa_um_ms,
+                        double dt_ms, int64_t n_total_steps, const double* f, const double gamma_G0[3],
+                        void* state_dev, int64_t k0, int64_t n_steps, int init, double* signal_out,
+                        void* cuda_stream, char* errbuf, size_t errlen);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ EXPORTS = [
     "lbmbt_add_geometry", "lbmbt_get_mask", "lbmbt_set_phases", "lbmbt_set_permeability",
     "lbmbt_set_sequence", "lbmbt_pgse", "lbmbt_run", "lbmbt_run_batch", "lbmbt_grad",
     "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
-    "lbmbt_launch_count",
+    "lbmbt_launch_count", "lbmbt_sweep_noalloc",
 ]
 
 
@@ -82,6 +82,9 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = I
+            L.lbmbt_sweep_noalloc.argtypes = [I, I, I, D, P, P, I, P, P, D, D, I64, P, P, P, I64, I64, I, P, P,
+                                              ctypes.c_char_p, ctypes.c_size_t]
+            L.lbmbt_sweep_noalloc.restype = I
             L.lbmbt_last_error.argtypes = [P]
             L.lbmbt_last_error.restype = ctypes.c_char_p
             L.lbmbt_version.argtypes = []
@@ -115,6 +118,32 @@ def pgse(b_s_mm2, delta, Delta, dt, direction=(1.0, 0.0, 0.0)):
     f = np.empty(n.value)
     L.lbmbt_pgse(b_s_mm2, delta, Delta, dt, _p(d), _p(g), ctypes.byref(n), _p(f))
     return g, f
+
+
+def sweep_noalloc(mask_dev, shape, dx, bc, D, T2, kappa, dt, f, gG, state_dev, k0=0, n_steps=None, init=True,
+                  stream=None):
+    """``lbmbt_sweep_noalloc``: plain sweep on caller-owned device buffers
+    (mask uint8 [N], state complex64 [2*7*plane]) with no device allocation
+    inside the library.  Returns {Z, S} after step k0 + n_steps."""
+    L = lib()
+    nz, ny, nx = shape
+    bcv = np.ascontiguousarray(bc, np.int32)
+    Dv = np.ascontiguousarray(np.atleast_1d(D), np.float64)
+    T2v = np.ascontiguousarray(np.atleast_1d(T2), np.float64)
+    fv = np.ascontiguousarray(f, np.float64)
+    gv = np.ascontiguousarray(gG, np.float64)
+    n = fv.size - k0 if n_steps is None else n_steps
+    sig = np.zeros(3)
+    err = ctypes.create_string_buffer(256)
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = L.lbmbt_sweep_noalloc(nx, ny, nz, float(dx), _p(mask_dev), _p(bcv), int(Dv.size), _p(Dv), _p(T2v),
+                               float(kappa), float(dt), int(fv.size), _p(fv), _p(gv), _p(state_dev), int(k0), int(n),
+                               int(bool(init)), _p(sig), s, err, 256)
+    if rc:
+        raise LbmbtError(rc, "lbmbt_sweep_noalloc: " + err.value.decode())
+    return {"Z": complex(sig[0], sig[1]), "S": float(sig[2])}
 
 
 class Solver:
