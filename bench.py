@@ -72,7 +72,7 @@ def peaks():
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cu", "sweep_common.cuh", "lbmbt_internal.cuh"):
+    for f in ("sweep_tma.cu", "sweep_common.cuh", "lbmbt_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -315,7 +315,7 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr, "peak_source": peak_kind,
-                         "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_kernel"},
+                         "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_tma_kernel"},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

@@ -174,7 +174,14 @@ enum {
     LBMBT_OPT_GRAPH = 1,     /* 1 (default): replay step loops as CUDA graphs   */
     LBMBT_OPT_AUTOTUNE = 2,  /* 1: time launch shapes on first use (default 0)  */
     LBMBT_OPT_BLOCK = 3,     /* threads per block of the sweep (64..1024)       */
-    LBMBT_OPT_SPT = 4        /* sites per thread of the sweep (1, 2 or 4)       */
+    LBMBT_OPT_SPT = 4,       /* sites per thread of the sweep (1, 2 or 4)       */
+    LBMBT_OPT_KERNEL = 5,    /* 0 (default) auto, 1 register sweep, 2 bulk-copy
+                                (TMA) sweep; auto takes the bulk-copy sweep when
+                                every member has nx % 16 == 0 and nx <= 1024  */
+    LBMBT_OPT_KERNEL_USED = 6, /* read-only: 1 or 2 for the prepared run, else 0 */
+    LBMBT_OPT_STAGES = 7,    /* shared-memory stages of the bulk-copy sweep, 2..6 */
+    LBMBT_OPT_TMA_SHAPE = 8  /* bulk-copy consumers x sites per thread per unit:
+                                0 = 512 x 2, 1 = 384 x 3 (default), 2 = 256 x 4 */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

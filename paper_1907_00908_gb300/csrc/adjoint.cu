@@ -38,7 +38,7 @@ __device__ __forceinline__ float dotc(float2 a, float2 b) { return a.x * b.x + a
 // (index s): reads the adjoint of the population's consumer.
 template <int AX, int SIGN>
 __device__ __forceinline__ float2 adj_pull(const float2* __restrict__ nu, unsigned P, unsigned s, int coord, int dim,
-                                           unsigned stride, int bc, float2 fac_lo, float2 fac_hi, bool memb,
+                                           unsigned stride, int bc, const float2* __restrict__ fac, bool memb,
                                            float sh)
 {
     constexpr int J = 1 + 2 * AX + (SIGN > 0 ? 0 : 1);
@@ -50,18 +50,17 @@ __device__ __forceinline__ float2 adj_pull(const float2* __restrict__ nu, unsign
         float2 v = __ldg(nu + (size_t)JB * P + s);
         if (bc == BC_MIR_CONJ) {
             v.y = -v.y;
-            v = cmul(v, SIGN > 0 ? fac_hi : fac_lo);
+            v = cmul(v, __ldg(fac + 2 * AX + (SIGN > 0 ? 1 : 0)));
         }
         return v;
     }
     unsigned nb = (SIGN > 0) ? s + stride : s - stride;
-    float2 f = make_float2(1.f, 0.f);
-    if (cr) {  // periodic: the consumer is the wrapped node, pulling across its face
-        nb = (SIGN > 0) ? s - (unsigned)(dim - 1) * stride : s + (unsigned)(dim - 1) * stride;
-        f = (SIGN > 0) ? fac_lo : fac_hi;
-    }
+    if (cr) nb = (SIGN > 0) ? s - (unsigned)(dim - 1) * stride : s + (unsigned)(dim - 1) * stride;
     float2 v = __ldg(nu + (size_t)J * P + nb);
-    if (cr) v = cmul(v, make_float2(f.x, -f.y));
+    if (cr) {  // periodic: the consumer is the wrapped node, pulling across its face
+        const float2 f = __ldg(fac + 2 * AX + (SIGN > 0 ? 0 : 1));
+        v = cmul(v, make_float2(f.x, -f.y));
+    }
     if (memb) {
         const float2 o = __ldg(nu + (size_t)JB * P + s);
         v.x = o.x + sh * (v.x - o.x);
@@ -71,47 +70,45 @@ __device__ __forceinline__ float2 adj_pull(const float2* __restrict__ nu, unsign
 }
 
 __device__ __forceinline__ float2 pull_dir(int i, const float2* __restrict__ src, unsigned P, unsigned s, int x,
-                                           int y, int z, int nx, int ny, int nz, unsigned sxy, const int* bc,
-                                           const float2 (*fac)[2])
+                                           int y, int z, int nx, int ny, int nz, unsigned sxy, int bcx, int bcy,
+                                           int bcz, const float2* __restrict__ fac)
 {
     switch (i) {
-    case 1: return pull<0, +1>(src, P, s, x, nx, 1u, bc[0], fac[0][0]);
-    case 2: return pull<0, -1>(src, P, s, x, nx, 1u, bc[0], fac[0][1]);
-    case 3: return pull<1, +1>(src, P, s, y, ny, (unsigned)nx, bc[1], fac[1][0]);
-    case 4: return pull<1, -1>(src, P, s, y, ny, (unsigned)nx, bc[1], fac[1][1]);
-    case 5: return pull<2, +1>(src, P, s, z, nz, sxy, bc[2], fac[2][0]);
-    default: return pull<2, -1>(src, P, s, z, nz, sxy, bc[2], fac[2][1]);
+    case 1: return pull<0, +1>(src, P, s, x, nx, 1u, bcx, fac);
+    case 2: return pull<0, -1>(src, P, s, x, nx, 1u, bcx, fac);
+    case 3: return pull<1, +1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
+    case 4: return pull<1, -1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
+    case 5: return pull<2, +1>(src, P, s, z, nz, sxy, bcz, fac);
+    default: return pull<2, -1>(src, P, s, z, nz, sxy, bcz, fac);
     }
 }
 
 template <int SPT>
-__global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a, double Fk)
+__global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
 {
-    __shared__ MemberDesc sd;
-    __shared__ float2 facP[3][2];   // factors of step k-1 (forward recompute)
-    __shared__ float2 facK[3][2];   // factors of step k (transposed stream)
-    __shared__ float2 sL;
     __shared__ float s_red[NGACC][32];
 
-    if (threadIdx.x == 0) {
-        const int m = find_member(a.tile_start, a.n_members, blockIdx.x);
-        sd = a.members[m];
-        boundary_factors(sd, a.Fprev, facP);
-        boundary_factors(sd, Fk, facK);
+    const int m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, blockIdx.x);
+    const MemberDesc* __restrict__ sd = a.members + m;
+    const float2* __restrict__ facP = a.ftab + ((size_t)(a.k - 1) * a.n_members + m) * 6;  // step k-1
+    const float2* __restrict__ facK = a.ftab + ((size_t)a.k * a.n_members + m) * 6;        // step k
+    float2 sL = make_float2(0.f, 0.f);
+    if (a.first) {
         const double2 L = a.lam_init[m];
         sL = make_float2((float)L.x, (float)L.y);
     }
-    __syncthreads();
 
-    const unsigned P = (unsigned)sd.plane;
-    const float2* __restrict__ u = sd.state + (size_t)a.fwd_slot * 7 * P;
-    const float2* __restrict__ nu = sd.adj + (size_t)a.lam_parity * 7 * P;
-    float2* __restrict__ out = sd.adj + (size_t)(a.lam_parity ^ 1) * 7 * P;
-    const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
+    const unsigned P = (unsigned)sd->plane;
+    const float2* __restrict__ u = sd->state + (size_t)a.fwd_slot * 7 * P;
+    const float2* __restrict__ nu = sd->adj + (size_t)a.lam_parity * 7 * P;
+    float2* __restrict__ out = sd->adj + (size_t)(a.lam_parity ^ 1) * 7 * P;
+    const uint8_t* __restrict__ mask = sd->mask;
+    const int nx = sd->nx, ny = sd->ny, nz = sd->nz;
+    const int bcx = sd->bc[0], bcy = sd->bc[1], bcz = sd->bc[2];
     const unsigned sxy = (unsigned)nx * ny;
-    const unsigned N = (unsigned)sd.N;
-    const unsigned base = (unsigned)(blockIdx.x - sd.tile0) * blockDim.x * SPT;
-    const float sh = sd.s_share;
+    const unsigned N = (unsigned)sd->N;
+    const unsigned base = (unsigned)(blockIdx.x - sd->tile0) * blockDim.x * SPT;
+    const float sh = sd->s_share;
     const float fk = a.fprev;
     float acc[NGACC];
 #pragma unroll
@@ -121,51 +118,38 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a, doubl
     for (int jj = 0; jj < SPT; ++jj) {
         const unsigned s = base + jj * blockDim.x + threadIdx.x;
         if (s >= N) break;
-        const unsigned row = s / nx;
-        const int x = (int)(s - row * nx);
-        const int z = (int)(row / ny);
-        const int y = (int)(row - (unsigned)z * ny);
-        const unsigned mk = sd.mask[s];
+        int x, y, z;
+        coords(sd, s, nx, ny, x, y, z);
+        const unsigned mk = mask[s];
         const int ph = mk >> 6;
 
         // forward recompute of g'^(k-1) at this site (as the forward sweep)
         float2 gp[Q];
         gp[0] = __ldg(u + s);
-        gp[1] = pull<0, +1>(u, P, s, x, nx, 1u, sd.bc[0], facP[0][0]);
-        gp[2] = pull<0, -1>(u, P, s, x, nx, 1u, sd.bc[0], facP[0][1]);
-        gp[3] = pull<1, +1>(u, P, s, y, ny, (unsigned)nx, sd.bc[1], facP[1][0]);
-        gp[4] = pull<1, -1>(u, P, s, y, ny, (unsigned)nx, sd.bc[1], facP[1][1]);
-        gp[5] = pull<2, +1>(u, P, s, z, nz, sxy, sd.bc[2], facP[2][0]);
-        gp[6] = pull<2, -1>(u, P, s, z, nz, sxy, sd.bc[2], facP[2][1]);
+        gp[1] = pull<0, +1>(u, P, s, x, nx, 1u, bcx, facP);
+        gp[2] = pull<0, -1>(u, P, s, x, nx, 1u, bcx, facP);
+        gp[3] = pull<1, +1>(u, P, s, y, ny, (unsigned)nx, bcy, facP);
+        gp[4] = pull<1, -1>(u, P, s, y, ny, (unsigned)nx, bcy, facP);
+        gp[5] = pull<2, +1>(u, P, s, z, nz, sxy, bcz, facP);
+        gp[6] = pull<2, -1>(u, P, s, z, nz, sxy, bcz, facP);
         if (mk & 0x3fu) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ib = (i & 1) ? i + 1 : i - 1;
-                if (mk & (1u << (ib - 1))) {
-                    const float2 o = __ldg(u + (size_t)ib * P + s);
-                    gp[i].x = o.x + sh * (gp[i].x - o.x);
-                    gp[i].y = o.y + sh * (gp[i].y - o.y);
-                }
+                if (mk & (1u << (ib - 1))) gp[i] = mix(__ldg(u + (size_t)ib * P + s), gp[i], sh);
             }
         }
-        const float ep = sd.eps[ph];
-        float cm1 = 0.f, sn = 0.f;
-        if (fk != 0.f) {
-            const float th = fk * (sd.ctheta[0] * (float)x + sd.ctheta[1] * (float)y + sd.ctheta[2] * (float)z);
-            float sh2, ch2;
-            sincosf(0.5f * th, &sh2, &ch2);
-            cm1 = -2.f * sh2 * sh2;
-            sn = 2.f * sh2 * ch2;
-        }
-        const float qr = cm1 - ep * (1.f + cm1), qi = sn * (1.f - ep);
-        float Mr = 0.f, Mi = 0.f;
+        const float ep = sd->eps[ph];
+        const float2 rot = fk != 0.f ? rotation_m1(sd, fk, x, y, z) : make_float2(0.f, 0.f);
+        const float2 q = fk != 0.f ? reaction_q(rot, ep) : make_float2(-ep, 0.f);
+        const float qr = q.x, qi = q.y;
+        const float cm1 = rot.x, sn = rot.y;
+        // g = (1 + q) g' and M = sum g, in the forward sweep's order
+        float2 gg[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) { Mr += gp[i].x; Mi += gp[i].y; }
-        {   // M of g = (1 + q) g'
-            const float r0 = Mr, i0 = Mi;
-            Mr = r0 + (r0 * qr - i0 * qi);
-            Mi = i0 + (r0 * qi + i0 * qr);
-        }
+        for (int i = 0; i < Q; ++i) gg[i] = gp[i];
+        float Mr, Mi;
+        react(gg, q, Mr, Mi);
 
         // lambda^k at this site
         float2 lam[Q];
@@ -174,12 +158,12 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a, doubl
             for (int i = 0; i < Q; ++i) lam[i] = sL;
         } else {
             lam[0] = __ldg(nu + s);
-            lam[1] = adj_pull<0, +1>(nu, P, s, x, nx, 1u, sd.bc[0], facK[0][0], facK[0][1], mk & 1u, sh);
-            lam[2] = adj_pull<0, -1>(nu, P, s, x, nx, 1u, sd.bc[0], facK[0][0], facK[0][1], mk & 2u, sh);
-            lam[3] = adj_pull<1, +1>(nu, P, s, y, ny, (unsigned)nx, sd.bc[1], facK[1][0], facK[1][1], mk & 4u, sh);
-            lam[4] = adj_pull<1, -1>(nu, P, s, y, ny, (unsigned)nx, sd.bc[1], facK[1][0], facK[1][1], mk & 8u, sh);
-            lam[5] = adj_pull<2, +1>(nu, P, s, z, nz, sxy, sd.bc[2], facK[2][0], facK[2][1], mk & 16u, sh);
-            lam[6] = adj_pull<2, -1>(nu, P, s, z, nz, sxy, sd.bc[2], facK[2][0], facK[2][1], mk & 32u, sh);
+            lam[1] = adj_pull<0, +1>(nu, P, s, x, nx, 1u, bcx, facK, mk & 1u, sh);
+            lam[2] = adj_pull<0, -1>(nu, P, s, x, nx, 1u, bcx, facK, mk & 2u, sh);
+            lam[3] = adj_pull<1, +1>(nu, P, s, y, ny, (unsigned)nx, bcy, facK, mk & 4u, sh);
+            lam[4] = adj_pull<1, -1>(nu, P, s, y, ny, (unsigned)nx, bcy, facK, mk & 8u, sh);
+            lam[5] = adj_pull<2, +1>(nu, P, s, z, nz, sxy, bcz, facK, mk & 16u, sh);
+            lam[6] = adj_pull<2, -1>(nu, P, s, z, nz, sxy, bcz, facK, mk & 32u, sh);
         }
 
         // d/d omega: <lambda_i, w_i M - g_i>, g_i = (1 + q) g'_i
@@ -188,14 +172,12 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a, doubl
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float w = i == 0 ? W0 : WI;
-            const float gr = gp[i].x + (gp[i].x * qr - gp[i].y * qi);
-            const float gi = gp[i].y + (gp[i].x * qi + gp[i].y * qr);
-            dOm += lam[i].x * (w * Mr - gr) + lam[i].y * (w * Mi - gi);
+            dOm += lam[i].x * (w * Mr - gg[i].x) + lam[i].y * (w * Mi - gg[i].y);
             lwr += w * lam[i].x;
             lwi += w * lam[i].y;
         }
         // mu = C^T lambda; d/d eps: <mu_i, -exp(i theta) g'_i>; nu = conj(1+q) mu
-        const float om = sd.omega[ph];
+        const float om = sd->omega[ph];
         float dEp = 0.f;
         const float er = 1.f + cm1, ei = sn;
 #pragma unroll
@@ -214,7 +196,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a, doubl
             for (int i = 1; i < Q; ++i) {
                 const int ib = (i & 1) ? i + 1 : i - 1;
                 if (mk & (1u << (ib - 1))) {
-                    const float2 v = pull_dir(i, u, P, s, x, y, z, nx, ny, nz, sxy, sd.bc, facP);
+                    const float2 v = pull_dir(i, u, P, s, x, y, z, nx, ny, nz, sxy, bcx, bcy, bcz, facP);
                     const float2 o = __ldg(u + (size_t)ib * P + s);
                     dS += dotc(lam[i], make_float2(v.x - o.x, v.y - o.y));
                 }
@@ -270,13 +252,13 @@ __global__ void reduce_grad_kernel(const double* __restrict__ gacc, const long l
 
 }  // namespace
 
-cudaError_t launch_adjoint(const AdjointArgs& a, double Fk, long long n_tiles, int block, int spt, cudaStream_t st)
+cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, int spt, cudaStream_t st)
 {
     if (block > 256) return cudaErrorInvalidValue;
     switch (spt) {
-    case 1: adjoint_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a, Fk); break;
-    case 2: adjoint_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a, Fk); break;
-    case 4: adjoint_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a, Fk); break;
+    case 1: adjoint_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
+    case 2: adjoint_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
+    case 4: adjoint_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

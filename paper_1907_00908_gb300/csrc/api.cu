@@ -28,6 +28,7 @@ struct Geom {
     int bc[3] = {0, 0, 0};
     long long N = 0;
     int max_phase = 0;
+    int has_membranes = 0;
     uint8_t* d_mask = nullptr;
 };
 
@@ -55,6 +56,7 @@ struct lbmbt_ctx {
     // options
     int use_graph = 1;
     int autotune = 0;
+    int kernel_opt = 0;           // 0 auto, 1 register sweep, 2 bulk-copy sweep
     int block = 256;
     int spt = 2;
     long long launches = 0;
@@ -64,12 +66,29 @@ struct lbmbt_ctx {
     std::vector<MemberDesc> descs;
     std::vector<long long> tile_start;
     long long n_tiles = 0;
+    std::vector<long long> unit_start;
+    long long n_units = 0;
+    long long* d_unit_start = nullptr;
+    size_t cap_us = 0;
+    bool use_tma = false;
+    int tma_cap = 0;
+    int tma_capx = 0;
+    int tma_stages = 3;
+    int tma_variant = 1;
+    int tma_grid = 0;
+    int sm_count = 0;
     int tile_block = 0, tile_spt = 0;
     MemberDesc* d_desc = nullptr;
     long long* d_tile_start = nullptr;
     size_t cap_desc = 0, cap_ts = 0;
     double2* d_partial = nullptr;
     size_t cap_partial = 0;
+    float2* d_fac = nullptr;      // [2][n_members][6] boundary factors
+    size_t cap_fac = 0;
+    float2* d_ftab = nullptr;     // adjoint: [K+1][n_members][6]
+    size_t cap_ftab = 0;
+    float2* d_etab = nullptr;     // per-member rotation tables
+    size_t cap_etab = 0;
     double2* d_Z = nullptr;
     size_t cap_Z = 0;
     double2* d_series = nullptr;
@@ -99,6 +118,29 @@ struct lbmbt_ctx {
 };
 
 static std::string g_create_error;
+
+// Exact division of n < 2^28 by d (Granlund-Montgomery with 28-bit
+// dividends): l = ceil(log2 d), m = floor(2^(28+l)/d) + 1, q = (n*m) >> (28+l).
+static void div_magic(unsigned d, unsigned* m, int* s)
+{
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    *m = (unsigned)((1ull << (28 + l)) / d + 1);
+    *s = 28 + l;
+}
+
+// Per-axis rotation table of one member: (cos(c n) - 1, sin(c n)), c = -gG_a dx dt.
+static void rotation_table(const double gG[3], double dx, double dt, const int dims[3], std::vector<float2>& out)
+{
+    for (int a = 0; a < 3; ++a) {
+        const double c = -gG[a] * dx * dt;
+        for (int n = 0; n < dims[a]; ++n) {
+            const double t = c * n;
+            const double h = std::sin(0.5 * t);
+            out.push_back(make_float2((float)(-2.0 * h * h), (float)std::sin(t)));
+        }
+    }
+}
 
 static int fail(lbmbt_ctx* c, int code, const char* fmt, ...)
 {
@@ -186,6 +228,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaFree(c->d_f); cudaFree(c->d_F);
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
+    cudaFree(c->d_fac); cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab);
     cudaFree(c->d_ck); cudaFree(c->d_seg); cudaFree(c->d_gacc); cudaFree(c->d_gout); cudaFree(c->d_laminit);
     if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
     delete c;
@@ -245,8 +288,9 @@ static int make_geom(lbmbt_ctx* c, int nx, int ny, int nz, double dx, const int3
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cleanup();
     if (e != cudaSuccess) { cudaFree(d_mask); return fail(c, LBMBT_ECUDA, "mask build: %s", cudaGetErrorString(e)); }
-    if (herr) { cudaFree(d_mask); return fail(c, LBMBT_EDEVICE, "a label is outside [0, %d)", n_labels); }
+    if (herr & 1) { cudaFree(d_mask); return fail(c, LBMBT_EDEVICE, "a label is outside [0, %d)", n_labels); }
     out->nx = nx; out->ny = ny; out->nz = nz; out->dx = dx; out->N = N; out->max_phase = maxp;
+    out->has_membranes = (herr & 2) ? 1 : 0;
     for (int a = 0; a < 3; ++a) out->bc[a] = bc[a];
     out->d_mask = d_mask;
     return LBMBT_OK;
@@ -378,30 +422,73 @@ extern "C" int lbmbt_pgse(double b, double delta, double Delta, double dt, const
 }
 
 // ------------------------------------------------------------- run set-up
+// Row units of the bulk-copy sweep: rpu x-rows of one z-plane, about 512
+// sites per unit.  Eligible when every member has nx % 16 == 0 (16-byte
+// aligned rows and mask bytes) and a unit fits the shared-memory stages.
+static constexpr int TMA_TARGET_SITES = 1024;
+static constexpr int TMA_MAX_CAP = 1024;
+
+static bool tma_eligible(const lbmbt_ctx* c)
+{
+    for (auto& d : c->descs)
+        if (d.nx % 16 != 0 || d.nx > TMA_MAX_CAP) return false;
+    return true;
+}
+
 static int build_worklist(lbmbt_ctx* c, int block, int spt)
 {
     const long long tile = (long long)block * spt;
     c->tile_start.assign(c->n_members + 1, 0);
+    c->unit_start.assign(c->n_members + 1, 0);
+    const bool tma = (c->kernel_opt == 0 || c->kernel_opt == 2) && tma_eligible(c);
+    if (c->kernel_opt == 2 && !tma)
+        return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member", TMA_MAX_CAP);
+    int cap = 16, capx = 0;
     for (int m = 0; m < c->n_members; ++m) {
-        const long long N = c->descs[m].N;
-        c->descs[m].tile0 = c->tile_start[m];
-        c->tile_start[m + 1] = c->tile_start[m] + (N + tile - 1) / tile;
+        MemberDesc& d = c->descs[m];
+        d.tile0 = c->tile_start[m];
+        c->tile_start[m + 1] = c->tile_start[m] + (d.N + tile - 1) / tile;
+        d.rpu = std::max(1, std::min(d.ny, TMA_TARGET_SITES / std::max(1, d.nx)));
+        d.unit0 = c->unit_start[m];
+        c->unit_start[m + 1] = c->unit_start[m] + (long long)d.nz * ((d.ny + d.rpu - 1) / d.rpu);
+        cap = std::max(cap, d.rpu * d.nx);
+        (void)capx;   // the x rotation table is read through L1, not staged
     }
     c->n_tiles = c->tile_start[c->n_members];
+    c->n_units = c->unit_start[c->n_members];
     if (c->n_tiles > 0x7fffffffLL) return fail(c, LBMBT_EINVAL, "work list too long");
+    c->use_tma = tma;
+    if (tma) {
+        c->tma_cap = (cap + 15) / 16 * 16;
+        c->tma_capx = (capx + 15) / 16 * 16;
+        int per_sm = 0;
+        CU(c, tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, &per_sm));
+        if (per_sm < 1) return fail(c, LBMBT_EINVAL, "bulk-copy sweep does not fit on an SM");
+        if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+        c->tma_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_units);
+    }
+    const long long n_part = std::max(c->n_tiles, c->n_units * tma_partials_per_unit(c->tma_variant));
     int rc = grow(c, &c->d_desc, &c->cap_desc, sizeof(MemberDesc) * c->n_members);
     if (!rc) rc = grow(c, &c->d_tile_start, &c->cap_ts, sizeof(long long) * (c->n_members + 1));
-    if (!rc) rc = grow(c, &c->d_partial, &c->cap_partial, sizeof(double2) * c->n_tiles);
+    if (!rc) rc = grow(c, &c->d_unit_start, &c->cap_us, sizeof(long long) * (c->n_members + 1));
+    if (!rc) rc = grow(c, &c->d_partial, &c->cap_partial, sizeof(double2) * n_part);
+    if (!rc) rc = grow(c, &c->d_fac, &c->cap_fac, sizeof(float2) * 12 * c->n_members);
     if (rc) return rc;
     CU(c, cudaMemcpyAsync(c->d_desc, c->descs.data(), sizeof(MemberDesc) * c->n_members, cudaMemcpyHostToDevice,
                           c->stream));
     CU(c, cudaMemcpyAsync(c->d_tile_start, c->tile_start.data(), sizeof(long long) * (c->n_members + 1),
+                          cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->d_unit_start, c->unit_start.data(), sizeof(long long) * (c->n_members + 1),
                           cudaMemcpyHostToDevice, c->stream));
     c->tile_block = block;
     c->tile_spt = spt;
     drop_graph(c);
     return sync(c);
 }
+
+// Work list the signal partials of the current sweep kernel are indexed by.
+static const long long* part_start(const lbmbt_ctx* c) { return c->use_tma ? c->d_unit_start : c->d_tile_start; }
+static int part_per(const lbmbt_ctx* c) { return c->use_tma ? tma_partials_per_unit(c->tma_variant) : 1; }
 
 static SweepArgs sweep_args(lbmbt_ctx* c)
 {
@@ -413,6 +500,7 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.f = c->d_f;
     a.F = c->d_F;
     a.partial = c->d_partial;
+    a.fac = c->d_fac;
     return a;
 }
 
@@ -427,7 +515,7 @@ static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base =
     h.slot_mod = slot_mod;
     h.series = c->series_mode ? 1 : 0;
     h.err = 0;
-    CU(c, launch_set_ctl(c->d_ctl, h, c->stream));
+    CU(c, launch_ctl(c->d_ctl, h, 1, c->d_desc, c->n_members, c->d_F, c->d_fac, c->stream));
     c->launches++;
     return LBMBT_OK;
 }
@@ -441,14 +529,24 @@ static int init_state(lbmbt_ctx* c)
     return LBMBT_OK;
 }
 
-// Issue one step: sweep (+ per-step reduce in series mode).
+// Issue one step: sweep, then the control kernel (k += 1 and the next step's
+// boundary factors), plus the per-step reduce in series mode.
 static int issue_step(lbmbt_ctx* c)
 {
     SweepArgs a = sweep_args(c);
-    CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
-    c->launches++;
+    if (c->use_tma) {
+        a.tile_start = c->d_unit_start;
+        CU(c, launch_sweep_tma(a, c->n_units, c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_grid,
+                               c->stream));
+    } else {
+        CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
+    }
+    StepCtl none;
+    memset(&none, 0, sizeof none);
+    CU(c, launch_ctl(c->d_ctl, none, 0, c->d_desc, c->n_members, c->d_F, c->d_fac, c->stream));
+    c->launches += 2;
     if (c->series_mode) {
-        CU(c, launch_reduce(c->d_partial, c->d_tile_start, c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
+        CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
                             c->stream));
         c->launches++;
     }
@@ -541,6 +639,12 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         const double kap = mm.kappa_um_ms;
         const double cP = EPS_D * g.dx / (2.0 * c->dt);   // P = cP / kappa  (Eq. P_def)
         d.s_share = std::isinf(kap) ? 1.f : (float)(kap / (kap + cP));
+        d.axes = 0;
+        for (int a = 0; a < 3; ++a)
+            if (d.ctheta[a] != 0.f) d.axes |= 1 << a;
+        d.memb = g.has_membranes;
+        div_magic((unsigned)g.nx, &d.div_m[0], &d.div_s[0]);
+        div_magic((unsigned)g.ny, &d.div_m[1], &d.div_s[1]);
         if ((size_t)d.plane > max_plane) max_plane = d.plane;
     }
     invalidate_run(c);
@@ -560,6 +664,22 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         off += (size_t)c->n_slots * 7 * d.plane * sizeof(float2);
     }
     if (field_dev) c->descs[0].field = (float2*)field_dev;
+    {   // rotation tables
+        std::vector<float2> et;
+        std::vector<size_t> off(n_members);
+        for (int m = 0; m < n_members; ++m) {
+            off[m] = et.size();
+            const MemberDesc& d = c->descs[m];
+            const int dims[3] = {d.nx, d.ny, d.nz};
+            rotation_table(d.gG, d.dx, c->dt, dims, et);
+            if (et.size() & 1) et.push_back(make_float2(0.f, 0.f));  // 16-byte aligned tables
+        }
+        rc = grow(c, &c->d_etab, &c->cap_etab, et.size() * sizeof(float2));
+        if (rc) return rc;
+        CU(c, cudaMemcpyAsync(c->d_etab, et.data(), et.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+        for (int m = 0; m < n_members; ++m) c->descs[m].etab = c->d_etab + off[m];
+        CU(c, cudaStreamSynchronize(c->stream));
+    }
     rc = grow(c, &c->d_Z, &c->cap_Z, sizeof(double2) * n_members);
     if (!rc && series) rc = grow(c, &c->d_series, &c->cap_series, sizeof(double2) * n_members * c->n_steps);
     if (rc) return rc;
@@ -615,7 +735,7 @@ static int advance(lbmbt_ctx* c, long long n, bool want_signal)
             rc = capture_graph(c);
             if (rc) return rc;
         }
-        const int per = c->series_mode ? 2 : 1;
+        const int per = c->series_mode ? 3 : 2;
         while (left >= GRAPH_CHUNK) {
             CU(c, cudaGraphLaunch(c->graph, c->stream));
             c->launches += GRAPH_CHUNK * per;
@@ -629,14 +749,26 @@ static int advance(lbmbt_ctx* c, long long n, bool want_signal)
     }
     c->k_cur += n;
     if (want_signal && !c->series_mode) {
-        CU(c, launch_reduce(c->d_partial, c->d_tile_start, c->n_members, c->d_Z, nullptr, 0, c->d_ctl, c->stream));
+        CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), c->n_members, c->d_Z, nullptr, 0, c->d_ctl, c->stream));
         c->launches++;
     }
     return LBMBT_OK;
 }
 
+// Device-side error word of the step control (a bounded wait that timed out).
+static int check_device_error(lbmbt_ctx* c)
+{
+    int err = 0;
+    CU(c, cudaMemcpyAsync(&err, &c->d_ctl->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(c, cudaStreamSynchronize(c->stream));
+    if (err) return fail(c, LBMBT_EDEVICE, "a device-side wait timed out (error word %d)", err);
+    return LBMBT_OK;
+}
+
 static int fetch_signal(lbmbt_ctx* c, double* signal_out, double* series_out)
 {
+    int rc0 = check_device_error(c);
+    if (rc0) return rc0;
     std::vector<double2> Z(c->n_members);
     CU(c, cudaMemcpyAsync(Z.data(), c->d_Z, sizeof(double2) * c->n_members, cudaMemcpyDeviceToHost, c->stream));
     std::vector<double2> ser;
@@ -711,7 +843,7 @@ extern "C" int lbmbt_advance(lbmbt_ctx* c, int64_t n_steps, int want_signal, dou
     int rc = advance(c, n_steps, want_signal != 0);
     if (rc) return rc;
     if (want_signal && signal_out) return fetch_signal(c, signal_out, nullptr);
-    return sync(c);
+    return check_device_error(c);
 }
 
 extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
@@ -728,6 +860,18 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         if (v != 1 && v != 2 && v != 4) return fail(c, LBMBT_EINVAL, "sites per thread must be 1, 2 or 4");
         c->spt = (int)v;
         break;
+    case LBMBT_OPT_KERNEL:
+        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "kernel must be 0 (auto), 1 (register) or 2 (bulk copy)");
+        c->kernel_opt = (int)v;
+        break;
+    case LBMBT_OPT_STAGES:
+        if (v < 2 || v > 6) return fail(c, LBMBT_EINVAL, "stages must be 2..6");
+        c->tma_stages = (int)v;
+        break;
+    case LBMBT_OPT_TMA_SHAPE:
+        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "bulk-copy shape must be 0, 1 or 2");
+        c->tma_variant = (int)v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -742,6 +886,10 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_AUTOTUNE: *v = c->autotune; break;
     case LBMBT_OPT_BLOCK: *v = c->block; break;
     case LBMBT_OPT_SPT: *v = c->spt; break;
+    case LBMBT_OPT_KERNEL: *v = c->kernel_opt; break;
+    case LBMBT_OPT_STAGES: *v = c->tma_stages; break;
+    case LBMBT_OPT_TMA_SHAPE: *v = c->tma_variant; break;
+    case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     return LBMBT_OK;
@@ -814,7 +962,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
             }
     }
     c->k_cur = K;
-    CU(c, launch_reduce(c->d_partial, c->d_tile_start, n, c->d_Z, nullptr, 0, c->d_ctl, c->stream));
+    CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), n, c->d_Z, nullptr, 0, c->d_ctl, c->stream));
     c->launches++;
     std::vector<double2> Z(n);
     CU(c, cudaMemcpyAsync(Z.data(), c->d_Z, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
@@ -838,15 +986,16 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     }
     CU(c, cudaMemcpyAsync(c->d_desc, rd.data(), sizeof(MemberDesc) * n, cudaMemcpyHostToDevice, c->stream));
     CU(c, cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * NGACC * c->n_tiles, c->stream));
-    std::vector<double> F(K + 1);
-    F[0] = 0.0;
-    for (long long k = 0; k < K; ++k) F[k + 1] = F[k] + c->f[k] * c->dt;
+    if ((rc = grow(c, &c->d_ftab, &c->cap_ftab, sizeof(float2) * 6 * (size_t)(K + 1) * n))) return rc;
+    CU(c, launch_factor_table(c->d_desc, n, c->d_F, K, c->d_ftab, c->stream));
+    c->launches++;
     AdjointArgs aa;
     aa.members = c->d_desc;
     aa.tile_start = c->d_tile_start;
     aa.n_members = n;
     aa.lam_init = c->d_laminit;
     aa.gacc = c->d_gacc;
+    aa.ftab = c->d_ftab;
     int parity = 1;
     for (long long seg = n_ck - 1; seg >= 0; --seg) {
         const long long k0 = seg * ck, k1 = std::min(K, k0 + ck);
@@ -866,8 +1015,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
             aa.fwd_slot = (int)(k - 1 - k0);
             aa.lam_parity = parity;
             aa.fprev = (float)c->f[k - 1];
-            aa.Fprev = F[k - 1];
-            CU(c, launch_adjoint(aa, F[k], c->n_tiles, c->tile_block, c->tile_spt, c->stream));
+            CU(c, launch_adjoint(aa, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
             c->launches++;
             parity ^= 1;
         }

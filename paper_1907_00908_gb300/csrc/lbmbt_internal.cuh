@@ -33,7 +33,9 @@ struct MemberDesc {
     const uint8_t* mask;  // per-site membrane bits 0..5 + phase bits 6..7
     long long N;          // sites
     long long plane;      // plane stride in sites
-    long long tile0;      // first work-list tile of this member
+    long long tile0;      // first work-list tile of this member (site tiles)
+    long long unit0;      // first row-unit of this member (bulk-copy sweep)
+    int rpu;              // x-rows per unit of the bulk-copy sweep
     int nx, ny, nz;
     int bc[3];            // BcMode per axis
     double gG[3];         // gamma*G0, rad/(um ms)
@@ -42,15 +44,23 @@ struct MemberDesc {
     float omega[4];       // 1/tau_p (Eq. tau_def)
     float eps[4];         // 1 - exp(-dt/T2_p), from expm1 in FP64
     float s_share;        // 1/(1+P): crossing share of a membrane link (Eq. B5)
-    float pad_;
+    int axes;             // bit a set iff ctheta[a] != 0
+    int memb;             // the geometry has at least one membrane link
+    // exact division of site indices (< 2^28) by nx and ny: q = (n*m) >> s
+    unsigned div_m[2];
+    int div_s[2];
+    // per-axis rotation tables (FP64-built): etab[off_a + n] =
+    // (cos(ctheta_a n) - 1, sin(ctheta_a n)), offsets 0, nx, nx+ny; or nullptr
+    const float2* etab;
 };
 
-// Step control word in device memory.  The sweep reads k here; the last block
-// of every sweep launch advances it, so a captured graph of sweeps can be
-// replayed from any step.  No kernel ever waits on it.
+// Step control word in device memory.  The sweep reads k here; a one-block
+// control kernel between sweeps advances it and prepares the next step's
+// boundary factors, so a captured graph of (sweep, control) pairs replays
+// from any step.  No kernel ever waits on it.
 struct StepCtl {
     int k;              // step index the next sweep performs
-    unsigned done;      // blocks finished in the current sweep
+    unsigned done;      // unused (kept zero)
     int sig_step;       // step whose end signal is reduced (-1: none)
     int field_step;     // step whose end field is written (-1: none)
     int slot_base;      // src slot = (k - slot_base) % slot_mod
@@ -67,19 +77,34 @@ struct SweepArgs {
     const float* f;               // waveform per step
     const double* F;              // F_k = sum_{m<k} f_m dt, per step
     double2* partial;             // per-tile (sum Re M, sum Im M)
+    const float2* fac;            // [2][n_members][6] boundary factors, level k & 1
 };
 
 // ---- launchers (sweep.cu) ------------------------------------------------
 cudaError_t launch_build_mask(const int32_t* labels, const uint8_t* phase_of_label, int n_labels,
                               int nx, int ny, int nz, const int bc[3], uint8_t* mask, int* err,
                               cudaStream_t st);
-cudaError_t launch_set_ctl(StepCtl* ctl, const StepCtl& v, cudaStream_t st);
+// set != 0: write v to the control word; else advance k by one.  Then compute
+// the boundary factors of the (new) step k for every member into fac[k & 1].
+cudaError_t launch_ctl(StepCtl* ctl, const StepCtl& v, int set, const MemberDesc* members, int n_members,
+                       const double* F, float2* fac, cudaStream_t st);
+// Boundary factors of every step 0..K for every member: table[k][m][6].
+cudaError_t launch_factor_table(const MemberDesc* members, int n_members, const double* F, long long K,
+                                float2* table, cudaStream_t st);
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot,
                         cudaStream_t st);
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
-cudaError_t launch_reduce(const double2* partial, const long long* tile_start, int n_members,
+// Sums partial[tile_start[m]*per .. tile_start[m+1]*per) per member.
+cudaError_t launch_reduce(const double2* partial, const long long* tile_start, int per, int n_members,
                           double2* out, double2* series, long long series_stride,
                           const StepCtl* ctl, cudaStream_t st);
+
+// ---- bulk-copy sweep (sweep_tma.cu) --------------------------------------
+size_t tma_smem_bytes(int cap, int capx, int nst);
+int tma_partials_per_unit(int variant);
+cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int* ctas_per_sm);
+cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
+                             cudaStream_t st);
 
 // ---- adjoint (adjoint.cu) -------------------------------------------------
 // Per-tile gradient accumulators: [0..3] sum <lambda, w M - g> per phase
@@ -97,10 +122,10 @@ struct AdjointArgs {
     int lam_parity;               // nu^k is adj level lam_parity
     const double2* lam_init;      // per member Z / (N |Z|)
     float fprev;                  // f_(k-1)
-    double Fprev;                 // F_(k-1)
     double* gacc;                 // per tile NGACC doubles, accumulated
+    const float2* ftab;           // [K+1][n_members][6] boundary factors
 };
-cudaError_t launch_adjoint(const AdjointArgs& a, double Fk, long long n_tiles, int block, int spt, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
 cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int n_members, double* out,
                                cudaStream_t st);
 

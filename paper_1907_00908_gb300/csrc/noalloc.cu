@@ -34,6 +34,7 @@ constexpr size_t OFF_CTL = 0;
 constexpr size_t OFF_DESC = 256;
 constexpr size_t OFF_TS = 512;
 constexpr size_t OFF_Z = 768;
+constexpr size_t OFF_FAC = 832;                      // [2][1][6] boundary factors
 constexpr size_t OFF_F64 = 1024;
 constexpr size_t OFF_F32 = OFF_F64 + NA_MAX_STEPS * sizeof(double);
 constexpr size_t OFF_FCUM = OFF_F32 + NA_MAX_STEPS * sizeof(float);
@@ -41,6 +42,7 @@ constexpr size_t OFF_PART = (OFF_FCUM + (NA_MAX_STEPS + 1) * sizeof(double) + 25
 constexpr size_t NA_SCRATCH_BYTES = OFF_PART + NA_MAX_TILES * sizeof(double2);
 static_assert(sizeof(StepCtl) <= OFF_DESC - OFF_CTL, "control word does not fit");
 static_assert(sizeof(MemberDesc) <= OFF_TS - OFF_DESC, "descriptor does not fit");
+static_assert(OFF_FAC + 12 * sizeof(float2) <= OFF_F64, "factors do not fit");
 static_assert(NA_SCRATCH_BYTES <= (1u << 21), "scratch larger than stated");
 
 // The scratch.  Host code must not pass `na_scratch` itself to a kernel: on
@@ -52,14 +54,13 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex na_mutex;
 unsigned char* na_ptr[NA_MAX_DEVICES] = {};
 
-__global__ void na_setup_kernel(unsigned char* base, MemberDesc d, long long n_tiles, StepCtl c, int K, double dt)
+__global__ void na_setup_kernel(unsigned char* base, MemberDesc d, long long n_tiles, int K, double dt)
 {
-    // descriptor, tile prefix and control word
+    // descriptor and tile prefix
     *reinterpret_cast<MemberDesc*>(base + OFF_DESC) = d;
     long long* ts = reinterpret_cast<long long*>(base + OFF_TS);
     ts[0] = 0;
     ts[1] = n_tiles;
-    *reinterpret_cast<StepCtl*>(base + OFF_CTL) = c;
     // waveform tables from the caller's samples (copied to OFF_F64):
     // f_k as float and F_k = sum_{m<k} f_m dt in FP64, summed in order
     const double* f64 = reinterpret_cast<const double*>(base + OFF_F64);
@@ -162,6 +163,18 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     }
     const double cP = EPS_D * dx_um / (2.0 * dt_ms);
     d.s_share = std::isinf(kappa_um_ms) ? 1.f : (float)(kappa_um_ms / (kappa_um_ms + cP));
+    d.axes = 0;
+    for (int a = 0; a < 3; ++a)
+        if (d.ctheta[a] != 0.f) d.axes |= 1 << a;
+    d.etab = nullptr;  // no tables here: the reaction angle uses sincosf
+    d.memb = 1;        // the mask is the caller's: assume membranes may be present
+    const unsigned dv[2] = {(unsigned)nx, (unsigned)ny};
+    for (int j = 0; j < 2; ++j) {  // exact n / d for n < 2^28 (multiply-shift)
+        int l = 0;
+        while ((1ull << l) < dv[j]) ++l;
+        d.div_m[j] = (unsigned)((1ull << (28 + l)) / dv[j] + 1);
+        d.div_s[j] = 28 + l;
+    }
     const long long n_tiles = (N + NA_TILE - 1) / NA_TILE;
 
     int dev = 0;
@@ -183,7 +196,7 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     c.err = 0;
     e = cudaMemcpyAsync(base + OFF_F64, f, n_total_steps * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        na_setup_kernel<<<1, 1, 0, st>>>(base, d, n_tiles, c, (int)n_total_steps, dt_ms);
+        na_setup_kernel<<<1, 1, 0, st>>>(base, d, n_tiles, (int)n_total_steps, dt_ms);
         e = cudaGetLastError();
     }
     SweepArgs a;
@@ -194,10 +207,20 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.f = reinterpret_cast<const float*>(base + OFF_F32);
     a.F = reinterpret_cast<const double*>(base + OFF_FCUM);
     a.partial = reinterpret_cast<double2*>(base + OFF_PART);
+    float2* fac = reinterpret_cast<float2*>(base + OFF_FAC);
+    a.fac = fac;
+    MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
+    const double* Fd = reinterpret_cast<const double*>(base + OFF_FCUM);
+    // control word (done counter and step start from the values above every
+    // call) and the first step's boundary factors
+    if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 1, dd, 1, Fd, fac, st);
     if (e == cudaSuccess && init) e = launch_init(a, n_tiles, NA_BLOCK, NA_SPT, 0, st);
-    for (long long k = 0; e == cudaSuccess && k < n_steps; ++k) e = launch_sweep(a, n_tiles, NA_BLOCK, NA_SPT, st);
+    for (long long k = 0; e == cudaSuccess && k < n_steps; ++k) {
+        e = launch_sweep(a, n_tiles, NA_BLOCK, NA_SPT, st);
+        if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 0, dd, 1, Fd, fac, st);
+    }
     double2* Zd = reinterpret_cast<double2*>(base + OFF_Z);
-    if (e == cudaSuccess) e = launch_reduce(a.partial, a.tile_start, 1, Zd, nullptr, 0, a.ctl, st);
+    if (e == cudaSuccess) e = launch_reduce(a.partial, a.tile_start, 1, 1, Zd, nullptr, 0, a.ctl, st);
     double2 Z = make_double2(0.0, 0.0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&Z, Zd, sizeof Z, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

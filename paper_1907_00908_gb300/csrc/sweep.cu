@@ -13,6 +13,8 @@
 //    maps hat g(t^k) -> hat g(t^{k+1}), i.e. the paper's step order re-cut at
 //    the collision, so every site reads 7 complex values (one from each
 //    upstream neighbour) and writes 7.
+//  * ctl_kernel        : sets / advances the step word between sweeps and
+//                        computes the next step's FP64 boundary factors
 //  * reduce_kernel     : fixed-order FP64 sum of the per-tile partials.
 //
 // The work list of a launch is the concatenation of all members' tiles; a
@@ -57,6 +59,7 @@ __global__ void build_mask_kernel(const int32_t* __restrict__ labels, const uint
             if (labels[nb] != L) m |= 1u << b;
         }
         mask[s] = (uint8_t)m;
+        if (m & 0x3fu) atomicOr(err, 2);   // bit 1: the geometry has membranes
     }
 }
 
@@ -84,59 +87,48 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
 template <int SPT>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 {
-    __shared__ MemberDesc sd;
-    __shared__ float2 sfac[3][2];
-    __shared__ int s_k, s_flags, s_src, s_dst;
     __shared__ double2 s_red[32];
+    // Every thread looks up its member, step and flags itself (broadcast
+    // loads): there is no per-block prologue to wait for.
+    const int m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, blockIdx.x);
+    const MemberDesc* __restrict__ sd = a.members + m;
+    const int k = __ldcg(&a.ctl->k);
+    const int sbase = __ldcg(&a.ctl->slot_base), smod = __ldcg(&a.ctl->slot_mod);
+    const bool do_sig = __ldcg(&a.ctl->series) || k == __ldcg(&a.ctl->sig_step);
+    float2* const field = sd->field;
+    const bool do_field = k == __ldcg(&a.ctl->field_step) && field != nullptr;
+    const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + m) * 6;
 
-    if (threadIdx.x == 0) {
-        const int m = find_member(a.tile_start, a.n_members, blockIdx.x);
-        sd = a.members[m];
-        const int k = __ldcg(&a.ctl->k);
-        const int base = __ldcg(&a.ctl->slot_base), mod = __ldcg(&a.ctl->slot_mod);
-        s_k = k;
-        s_src = (k - base) % mod;
-        s_dst = (k + 1 - base) % mod;
-        int flags = 0;
-        if (__ldcg(&a.ctl->series) || k == __ldcg(&a.ctl->sig_step)) flags |= 1;
-        if (k == __ldcg(&a.ctl->field_step) && sd.field != nullptr) flags |= 2;
-        s_flags = flags;
-        boundary_factors(sd, a.F[k], sfac);
-    }
-    __syncthreads();
-
-    const int k = s_k;
-    const int flags = s_flags;
     const float fk = __ldg(a.f + k);
-    const unsigned P = (unsigned)sd.plane;
-    const float2* __restrict__ src = sd.state + (size_t)s_src * 7 * P;
-    float2* __restrict__ dst = sd.state + (size_t)s_dst * 7 * P;
-    const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
+    const unsigned P = (unsigned)sd->plane;
+    const float2* __restrict__ src = sd->state + (size_t)((k - sbase) % smod) * 7 * P;
+    float2* __restrict__ dst = sd->state + (size_t)((k + 1 - sbase) % smod) * 7 * P;
+    const uint8_t* __restrict__ mask = sd->mask;
+    const int nx = sd->nx, ny = sd->ny, nz = sd->nz;
+    const int bcx = sd->bc[0], bcy = sd->bc[1], bcz = sd->bc[2];
     const unsigned sxy = (unsigned)nx * ny;
-    const unsigned N = (unsigned)sd.N;
-    const unsigned base = (unsigned)(blockIdx.x - sd.tile0) * blockDim.x * SPT;
-    const float sh = sd.s_share;
-    double zr = 0.0, zi = 0.0;
+    const unsigned N = (unsigned)sd->N;
+    const unsigned base = (unsigned)(blockIdx.x - sd->tile0) * blockDim.x * SPT;
+    const float sh = sd->s_share;
+    float zr = 0.f, zi = 0.f;   // per-thread sums in FP32, FP64 from the warp level up
 
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
         const unsigned s = base + j * blockDim.x + threadIdx.x;
         if (s >= N) break;
-        const unsigned row = s / nx;
-        const int x = (int)(s - row * nx);
-        const int z = (int)(row / ny);
-        const int y = (int)(row - (unsigned)z * ny);
-        const unsigned mk = sd.mask[s];
+        int x, y, z;
+        coords(sd, s, nx, ny, x, y, z);
+        const unsigned mk = mask[s];
         const int ph = mk >> 6;
 
         float2 g[Q];
         g[0] = __ldg(src + s);
-        g[1] = pull<0, +1>(src, P, s, x, nx, 1u, sd.bc[0], sfac[0][0]);
-        g[2] = pull<0, -1>(src, P, s, x, nx, 1u, sd.bc[0], sfac[0][1]);
-        g[3] = pull<1, +1>(src, P, s, y, ny, (unsigned)nx, sd.bc[1], sfac[1][0]);
-        g[4] = pull<1, -1>(src, P, s, y, ny, (unsigned)nx, sd.bc[1], sfac[1][1]);
-        g[5] = pull<2, +1>(src, P, s, z, nz, sxy, sd.bc[2], sfac[2][0]);
-        g[6] = pull<2, -1>(src, P, s, z, nz, sxy, sd.bc[2], sfac[2][1]);
+        g[1] = pull<0, +1>(src, P, s, x, nx, 1u, bcx, fac);
+        g[2] = pull<0, -1>(src, P, s, x, nx, 1u, bcx, fac);
+        g[3] = pull<1, +1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
+        g[4] = pull<1, -1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
+        g[5] = pull<2, +1>(src, P, s, z, nz, sxy, bcz, fac);
+        g[6] = pull<2, -1>(src, P, s, z, nz, sxy, bcz, fac);
 
         // Half-link membrane (Eq. B5): on a membrane link the arriving
         // population is r * (own population sent towards the membrane) +
@@ -146,56 +138,35 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ib = (i & 1) ? i + 1 : i - 1;
-                if (mk & (1u << (ib - 1))) {
-                    const float2 o = __ldg(src + (size_t)ib * P + s);
-                    g[i].x = o.x + sh * (g[i].x - o.x);
-                    g[i].y = o.y + sh * (g[i].y - o.y);
-                }
+                if (mk & (1u << (ib - 1))) g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
             }
         }
 
         // Reaction (Eq. reaction_LBM): g <- g exp(-i gamma x.G0 f_k dt) (1 - eps),
-        // applied as g + g q with q = exp(i theta)(1 - eps) - 1 and
-        // cos(theta) - 1 = -2 sin^2(theta/2), so no O(1) rounding enters.
-        const float ep = sd.eps[ph];
-        float qr = -ep, qi = 0.f;
-        if (fk != 0.f) {
-            const float th = fk * (sd.ctheta[0] * (float)x + sd.ctheta[1] * (float)y + sd.ctheta[2] * (float)z);
-            float sh2, ch2;
-            sincosf(0.5f * th, &sh2, &ch2);
-            const float cm1 = -2.f * sh2 * sh2;
-            qr = cm1 - ep * (1.f + cm1);
-            qi = 2.f * sh2 * ch2 * (1.f - ep);
-        }
-        float mr = 0.f, mi = 0.f;
+        // applied as g + g q with q = exp(i theta)(1 - eps) - 1 (minus-one
+        // forms, no O(1) rounding); then M and the BGK collision
+        // (Eqs. M'summation, collision_LBM).
+        const float2 q = fk != 0.f ? reaction_q(rotation_m1(sd, fk, x, y, z), sd->eps[ph])
+                                   : make_float2(-sd->eps[ph], 0.f);
+        float mr, mi;
+        react(g, q, mr, mi);
+        collide(g, sd->omega[ph], mr, mi);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float gr = g[i].x, gi = g[i].y;
-            g[i].x = gr + (gr * qr - gi * qi);
-            g[i].y = gi + (gr * qi + gi * qr);
-            mr += g[i].x;
-            mi += g[i].y;
-        }
+        for (int i = 0; i < Q; ++i) __stcs(dst + (size_t)i * P + s, g[i]);
 
-        // BGK collision (Eq. collision_LBM) with g_eq = w_i M (Eq. g_eq).
-        const float om = sd.omega[ph];
-        __stcs(dst + s, make_float2(g[0].x + om * (W0 * mr - g[0].x), g[0].y + om * (W0 * mi - g[0].y)));
-#pragma unroll
-        for (int i = 1; i < Q; ++i)
-            __stcs(dst + (size_t)i * P + s,
-                   make_float2(g[i].x + om * (WI * mr - g[i].x), g[i].y + om * (WI * mi - g[i].y)));
-
-        if (flags & 1) { zr += mr; zi += mi; }
-        if (flags & 2) sd.field[s] = make_float2(mr, mi);
+        zr += mr;
+        zi += mi;
+        if (do_field) field[s] = make_float2(mr, mi);
     }
 
-    if (flags & 1) {
+    if (do_sig) {   // block-uniform: the only barrier of the kernel
+        double dr = zr, di = zi;
         for (int o = 16; o > 0; o >>= 1) {
-            zr += __shfl_down_sync(0xffffffffu, zr, o);
-            zi += __shfl_down_sync(0xffffffffu, zi, o);
+            dr += __shfl_down_sync(0xffffffffu, dr, o);
+            di += __shfl_down_sync(0xffffffffu, di, o);
         }
         const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        if (l == 0) s_red[w] = make_double2(zr, zi);
+        if (l == 0) s_red[w] = make_double2(dr, di);
         __syncthreads();
         if (w == 0) {
             const int nw = blockDim.x >> 5;
@@ -207,28 +178,46 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
             if (l == 0) a.partial[blockIdx.x] = v;
         }
     }
+}
 
-    // Advance the step counter once every block of this launch has finished.
-    __syncthreads();
+// Control word: set (or advance k), then the boundary factors of the new step
+// for every member, in FP64 (one block; members strided over its threads).
+__global__ void ctl_kernel(StepCtl* ctl, StepCtl v, int set, const MemberDesc* __restrict__ members,
+                           int n_members, const double* __restrict__ F, float2* __restrict__ fac)
+{
+    __shared__ int sk;
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&a.ctl->done, 1u);
-        if (prev == gridDim.x - 1) {
-            a.ctl->done = 0;
-            a.ctl->k = k + 1;
-            __threadfence();
-        }
+        if (set) *ctl = v;
+        else ctl->k = ctl->k + 1;
+        sk = ctl->k;
+    }
+    __syncthreads();
+    const int k = sk;
+    const double Fk = F[k];
+    for (int m = threadIdx.x; m < n_members; m += blockDim.x)
+        boundary_factors6(members[m], Fk, fac + ((size_t)(k & 1) * n_members + m) * 6);
+}
+
+// Boundary factors of all steps 0..K (adjoint sweep): table[k][m][6].
+__global__ void factor_table_kernel(const MemberDesc* __restrict__ members, int n_members,
+                                    const double* __restrict__ F, long long K, float2* __restrict__ table)
+{
+    const long long n = (K + 1) * n_members;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long k = t / n_members;
+        const int m = (int)(t - k * n_members);
+        boundary_factors6(members[m], F[k], table + t * 6);
     }
 }
 
 // ---------------------------------------------------------------- reduce
 __global__ void reduce_kernel(const double2* __restrict__ partial, const long long* __restrict__ tile_start,
-                              double2* __restrict__ out, double2* __restrict__ series, long long series_stride,
-                              const StepCtl* ctl)
+                              int per, double2* __restrict__ out, double2* __restrict__ series,
+                              long long series_stride, const StepCtl* ctl)
 {
     __shared__ double2 sh[256];
     const int m = blockIdx.x;
-    const long long t0 = tile_start[m], t1 = tile_start[m + 1];
+    const long long t0 = tile_start[m] * per, t1 = tile_start[m + 1] * per;
     double2 v = make_double2(0.0, 0.0);
     for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
         v.x += partial[t].x;
@@ -249,15 +238,22 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, const long lo
     }
 }
 
-// The control word is written by a kernel so its value travels as a launch
-// argument (stream-ordered, no host staging buffer to keep alive).
-__global__ void set_ctl_kernel(StepCtl* ctl, StepCtl v) { *ctl = v; }
-
 }  // namespace
 
-cudaError_t launch_set_ctl(StepCtl* ctl, const StepCtl& v, cudaStream_t st)
+cudaError_t launch_ctl(StepCtl* ctl, const StepCtl& v, int set, const MemberDesc* members, int n_members,
+                       const double* F, float2* fac, cudaStream_t st)
 {
-    set_ctl_kernel<<<1, 1, 0, st>>>(ctl, v);
+    ctl_kernel<<<1, 256, 0, st>>>(ctl, v, set, members, n_members, F, fac);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor_table(const MemberDesc* members, int n_members, const double* F, long long K,
+                                float2* table, cudaStream_t st)
+{
+    const long long n = (K + 1) * n_members;
+    long long grid = (n + 255) / 256;
+    if (grid > 152LL * 32) grid = 152LL * 32;
+    factor_table_kernel<<<(unsigned)grid, 256, 0, st>>>(members, n_members, F, K, table);
     return cudaGetLastError();
 }
 
@@ -290,10 +286,10 @@ cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int s
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const double2* partial, const long long* tile_start, int n_members, double2* out,
+cudaError_t launch_reduce(const double2* partial, const long long* tile_start, int per, int n_members, double2* out,
                           double2* series, long long series_stride, const StepCtl* ctl, cudaStream_t st)
 {
-    reduce_kernel<<<n_members, 256, 0, st>>>(partial, tile_start, out, series, series_stride, ctl);
+    reduce_kernel<<<n_members, 256, 0, st>>>(partial, tile_start, per, out, series, series_stride, ctl);
     return cudaGetLastError();
 }
 

@@ -59,14 +59,14 @@ __device__ __forceinline__ void boundary_factors(const MemberDesc& sd, double F,
 // Pull of direction I = 1 + 2*AX + (SIGN > 0 ? 0 : 1) into site s.
 // SIGN = +1: direction +e_AX, the population comes from coord - 1;
 // SIGN = -1: direction -e_AX, it comes from coord + 1.
-// Crossing the low face (+ direction at coord 0) uses fac = sfac[AX][0],
-// the high face uses sfac[AX][1]:
+// Crossing the low face (+ direction at coord 0) uses fac[2*AX], the high
+// face fac[2*AX + 1] (loaded only by threads that cross):
 //   periodic : value from the wrapped node times exp(+-i gamma L G F_k)
 //   mirror   : hat g_ibar of the node itself (G parallel to the face), or its
 //              conjugate times exp(-i psi) (G normal to the face)
 template <int AX, int SIGN>
 __device__ __forceinline__ float2 pull(const float2* __restrict__ src, unsigned P, unsigned s, int coord,
-                                       int dim, unsigned stride, int bc, float2 fac)
+                                       int dim, unsigned stride, int bc, const float2* __restrict__ fac)
 {
     constexpr int I = 1 + 2 * AX + (SIGN > 0 ? 0 : 1);
     constexpr int IB = (SIGN > 0) ? I + 1 : I - 1;
@@ -80,9 +80,110 @@ __device__ __forceinline__ float2 pull(const float2* __restrict__ src, unsigned 
     float2 v = __ldg(src + (size_t)pl * P + nb);
     if (cr && bc != BC_MIR) {
         if (bc == BC_MIR_CONJ) v.y = -v.y;
-        v = cmul(v, fac);
+        v = cmul(v, __ldg(fac + 2 * AX + (SIGN > 0 ? 0 : 1)));
     }
     return v;
+}
+
+// Exact n / d for n < 2^28 with host-computed (m, s) (Granlund-Montgomery,
+// 28-bit dividends: m = floor(2^(28+l)/d) + 1, s = 28 + l, l = ceil(log2 d)).
+__device__ __forceinline__ unsigned fdiv(unsigned n, unsigned m, int s)
+{
+    return (unsigned)(((unsigned long long)n * m) >> s);
+}
+
+// Site coordinates of linear index s.
+__device__ __forceinline__ void coords(const MemberDesc* __restrict__ d, unsigned s, int nx, int ny, int& x, int& y,
+                                       int& z)
+{
+    const unsigned row = fdiv(s, d->div_m[0], d->div_s[0]);
+    x = (int)(s - row * (unsigned)nx);
+    const unsigned zz = fdiv(row, d->div_m[1], d->div_s[1]);
+    z = (int)zz;
+    y = (int)(row - zz * (unsigned)ny);
+}
+
+// exp(i theta) - 1 for theta = fk * sum_a ctheta_a n_a, returned as
+// (cos theta - 1, sin theta).  For fk in {-1, +1} from the per-axis tables,
+// combining axes by (1+u)(1+v) - 1 = u + v + u v; otherwise sincosf.  The
+// arithmetic order is fixed with explicit roundings so every kernel that
+// calls this gets the same bits.
+__device__ __forceinline__ float2 cadd_prod(float2 u, float2 v)
+{
+    // u + v + u v
+    const float pr = __fmaf_rn(u.x, v.x, __fmul_rn(-u.y, v.y));
+    const float pi = __fmaf_rn(u.x, v.y, __fmul_rn(u.y, v.x));
+    return make_float2(__fadd_rn(__fadd_rn(u.x, v.x), pr), __fadd_rn(__fadd_rn(u.y, v.y), pi));
+}
+
+__device__ __forceinline__ float2 rotation_m1(const MemberDesc* __restrict__ d, float fk, int x, int y, int z)
+{
+    const float2* __restrict__ et = d->etab;
+    const int ax = d->axes;
+    if (et != nullptr && (fk == 1.f || fk == -1.f)) {
+        float2 q = make_float2(0.f, 0.f);
+        bool any = false;
+        if (ax & 1) { q = __ldg(et + x); any = true; }
+        if (ax & 2) { const float2 v = __ldg(et + d->nx + y); q = any ? cadd_prod(q, v) : v; any = true; }
+        if (ax & 4) { const float2 v = __ldg(et + d->nx + d->ny + z); q = any ? cadd_prod(q, v) : v; }
+        if (fk < 0.f) q.y = -q.y;
+        return q;
+    }
+    const float th = __fmul_rn(fk, __fmaf_rn(d->ctheta[2], (float)z,
+                                              __fmaf_rn(d->ctheta[1], (float)y, __fmul_rn(d->ctheta[0], (float)x))));
+    float sh2, ch2;
+    sincosf(0.5f * th, &sh2, &ch2);
+    return make_float2(__fmul_rn(-2.f, __fmul_rn(sh2, sh2)), __fmul_rn(2.f, __fmul_rn(sh2, ch2)));
+}
+
+// Reaction factor minus one, q = exp(i theta)(1 - eps) - 1, from rot = exp(i theta) - 1.
+__device__ __forceinline__ float2 reaction_q(float2 rot, float ep)
+{
+    return make_float2(__fmaf_rn(-ep, __fadd_rn(1.f, rot.x), rot.x), __fmul_rn(rot.y, __fsub_rn(1.f, ep)));
+}
+
+// Membrane link: o + s (v - o) (Eq. B5 with r = 1 - s).
+__device__ __forceinline__ float2 mix(float2 o, float2 v, float sh)
+{
+    return make_float2(__fmaf_rn(sh, __fsub_rn(v.x, o.x), o.x), __fmaf_rn(sh, __fsub_rn(v.y, o.y), o.y));
+}
+
+// Reaction g <- g + g q in place, with M = sum_i g_i (fixed order).
+__device__ __forceinline__ void react(float2 (&g)[Q], float2 q, float& mr, float& mi)
+{
+    mr = 0.f;
+    mi = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float gr = g[i].x, gi = g[i].y;
+        g[i].x = __fmaf_rn(gr, q.x, __fmaf_rn(-gi, q.y, gr));
+        g[i].y = __fmaf_rn(gi, q.x, __fmaf_rn(gr, q.y, gi));
+        mr = __fadd_rn(mr, g[i].x);
+        mi = __fadd_rn(mi, g[i].y);
+    }
+}
+
+// BGK collision hat g = g + omega (w M - g) in place.
+__device__ __forceinline__ void collide(float2 (&g)[Q], float om, float mr, float mi)
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float w = i == 0 ? W0 : WI;
+        g[i].x = __fmaf_rn(om, __fmaf_rn(w, mr, -g[i].x), g[i].x);
+        g[i].y = __fmaf_rn(om, __fmaf_rn(w, mi, -g[i].y), g[i].y);
+    }
+}
+
+// boundary_factors() into a flat [6] array: index 2*axis + (0 low, 1 high).
+__device__ __forceinline__ void boundary_factors6(const MemberDesc& sd, double F, float2* out6)
+{
+    float2 f[3][2];
+    boundary_factors(sd, F, f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out6[2 * a] = f[a][0];
+        out6[2 * a + 1] = f[a][1];
+    }
 }
 
 }  // namespace

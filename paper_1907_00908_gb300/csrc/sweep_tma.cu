@@ -1,0 +1,456 @@
+// sweep_tma.cu -- the fused time step with bulk-copy (TMA) staging.
+//
+// Same arithmetic as sweep_kernel (sweep.cu), different data movement: the
+// work unit is `rpu` consecutive x-rows of one z-plane of one member
+// (L = rpu*nx sites).  For each unit one thread issues cp.async.bulk copies of
+// the 7 source row-blocks (and the mask bytes) into a shared-memory stage;
+// completion is tracked by an mbarrier (expect_tx / complete_tx).  A
+// persistent CTA walks its units through a ring of 2-6 stages, filled by a
+// producer warp and drained by 16 consumer warps, so the next units' copies
+// are in flight while the current one is computed, without holding the data
+// in registers.  The own-site values of planes 3..6 (membrane links in y and z) are
+// prefetched into registers one unit ahead.
+//
+// Source row-blocks of a unit starting at site s0 (all 16-byte aligned when
+// nx is even; the mask copy needs nx % 16 == 0):
+//   plane 0      [s0, s0+L)
+//   plane 1 (+x) [s0-2, s0+L)      value for local l is at l+1, wrap at l+nx+1
+//   plane 2 (-x) [s0, s0+L+2)      value for local l is at l+1, wrap at l-nx+1
+//   plane 3 (+y) rows y-1 (row 0 of the grid: wrapped row, or the mirror
+//                source: own row of plane 4)
+//   plane 4 (-y) rows y+1 (last row: wrapped row, or own row of plane 3)
+//   plane 5 (+z) plane z-1 (z = 0: wrapped plane, or own rows of plane 6)
+//   plane 6 (-z) plane z+1 (last plane: wrapped, or own rows of plane 5)
+// The boundary factors (periodic phase, mirror conjugation and rewind) are
+// applied per element after the copy, exactly as in the register kernel.
+//
+// Waits are bounded: a wait that has not completed after ~2 s sets the error
+// word of the step control, the CTA waits (again bounded) for the copies it
+// still has in flight, and returns.
+#include "lbmbt_internal.cuh"
+#include "sweep_common.cuh"
+
+namespace lbmbt {
+namespace {
+
+constexpr int TMA_MAX_STAGES = 6;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// try_wait with a suspend-time hint (ns): the waiting warp sleeps until the
+// phase completes or the hint elapses instead of spinning on issue slots.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for one phase of an mbarrier; false after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+
+// Shared-memory stage (all parts 16-byte aligned): 7 pull rows of (cap + 2)
+// complex values (the sources listed above), capx spare complex values
+// (0 in use), then cap mask bytes.
+__host__ __device__ __forceinline__ size_t stage_bytes(int cap, int capx)
+{
+    return (((size_t)7 * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
+}
+__device__ __forceinline__ float2* stage_plane(unsigned char* stage, int cap, int i)
+{
+    return reinterpret_cast<float2*>(stage) + (size_t)i * (cap + 2);
+}
+__device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, int capx)
+{
+    return stage + ((size_t)7 * (cap + 2) + capx) * sizeof(float2);
+}
+
+// Where unit u lies: member, z-plane, first row, rows, first site, sites.
+struct UnitGeo {
+    int m, z, y0, rows, L;
+    unsigned s0;
+};
+
+__device__ __forceinline__ UnitGeo unit_geo(const SweepArgs& a, long long u)
+{
+    UnitGeo G;
+    G.m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, u);
+    const MemberDesc* __restrict__ d = a.members + G.m;
+    const int ny = d->ny, nx = d->nx, rpu = d->rpu;
+    const int lu = (int)(u - d->unit0);
+    const int upz = (ny + rpu - 1) / rpu;
+    G.z = lu / upz;
+    G.y0 = (lu - G.z * upz) * rpu;
+    G.rows = min(rpu, ny - G.y0);
+    G.L = G.rows * nx;
+    G.s0 = (unsigned)G.z * ((unsigned)nx * ny) + (unsigned)G.y0 * nx;
+    return G;
+}
+
+// Thread 0: copies of unit u into `stage`, completion on `bar`.
+__device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, int smod, unsigned char* stage, int cap,
+                           int capx, uint64_t* bar, UnitGeo* info)
+{
+    const UnitGeo G = unit_geo(a, u);
+    *info = G;   // published to the consumers by the mbarrier (release/acquire)
+    const int m = G.m, z = G.z, y0 = G.y0, rows = G.rows;
+    const MemberDesc& d = a.members[m];
+    const long long nx = d.nx, sxy = (long long)d.nx * d.ny;
+    const long long L = rows * nx;
+    const long long s0 = (long long)z * sxy + (long long)y0 * nx;
+    const size_t P = (size_t)d.plane;
+    const float2* src = d.state + (size_t)((k - sbase) % smod) * 7 * P;
+    auto pl = [&](int i) { return src + (size_t)i * P; };
+    const uint32_t rowb = (uint32_t)(nx * sizeof(float2));
+    const uint32_t Lb = (uint32_t)(L * sizeof(float2));
+    const uint32_t total = 5 * Lb + 2 * (Lb + 16) + (uint32_t)L;
+    mbar_arrive_expect_tx(bar, total);
+    // rest, +x, -x
+    bulk_g2s(stage_plane(stage, cap, 0), pl(0) + s0, Lb, bar);
+    bulk_g2s(stage_plane(stage, cap, 1), pl(1) + s0 - 2, Lb + 16, bar);
+    bulk_g2s(stage_plane(stage, cap, 2), pl(2) + s0, Lb + 16, bar);
+    // +y: rows y0-1 .. y0+rows-2
+    {
+        float2* dst = stage_plane(stage, cap, 3);
+        if (y0 >= 1) {
+            bulk_g2s(dst, pl(3) + s0 - nx, Lb, bar);
+        } else {
+            const float2* face = d.bc[1] == BC_PER ? pl(3) + (long long)z * sxy + (long long)(d.ny - 1) * nx
+                                                    : pl(4) + s0;  // mirror: own row 0 of plane 4
+            bulk_g2s(dst, face, rowb, bar);
+            if (rows > 1) bulk_g2s(dst + nx, pl(3) + s0, Lb - rowb, bar);
+        }
+    }
+    // -y: rows y0+1 .. y0+rows
+    {
+        float2* dst = stage_plane(stage, cap, 4);
+        if (y0 + rows <= d.ny - 1) {
+            bulk_g2s(dst, pl(4) + s0 + nx, Lb, bar);
+        } else {
+            if (rows > 1) bulk_g2s(dst, pl(4) + s0 + nx, Lb - rowb, bar);
+            const long long last = s0 + (long long)(rows - 1) * nx;  // row ny-1
+            const float2* face = d.bc[1] == BC_PER ? pl(4) + (long long)z * sxy : pl(3) + last;
+            bulk_g2s(dst + (rows - 1) * nx, face, rowb, bar);
+        }
+    }
+    // +z, -z
+    {
+        const float2* srcz;
+        if (z >= 1) srcz = pl(5) + s0 - sxy;
+        else srcz = d.bc[2] == BC_PER ? pl(5) + s0 + (long long)(d.nz - 1) * sxy : pl(6) + s0;
+        bulk_g2s(stage_plane(stage, cap, 5), srcz, Lb, bar);
+        if (z <= d.nz - 2) srcz = pl(6) + s0 + sxy;
+        else srcz = d.bc[2] == BC_PER ? pl(6) + (long long)y0 * nx : pl(5) + s0;
+        bulk_g2s(stage_plane(stage, cap, 6), srcz, Lb, bar);
+    }
+    bulk_g2s(stage_mask(stage, cap, capx), d.mask + s0, (uint32_t)L, bar);
+}
+
+__device__ __forceinline__ float2 face_fix(float2 v, int bc, float2 f)
+{
+    if (bc == BC_MIR) return v;
+    if (bc == BC_MIR_CONJ) v.y = -v.y;
+    return cmul(v, f);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised persistent sweep: warp TMA_CONSUMERS/32 is the producer
+// (issues the bulk copies of every unit of this CTA into a ring of nst
+// stages), the other warps consume.  Stage st has a "full" mbarrier (one
+// arrival with the byte count, completed by the copies) and an "empty"
+// mbarrier (one arrival per consumer warp when it is done with the stage).
+// No block-wide barrier is used after set-up: every wait is an mbarrier wait
+// with a time limit, so a failed wait ends each warp on its own.
+template <int TMA_CONSUMERS, int TMA_SPT>
+__global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
+    sweep_tma_kernel(const SweepArgs a, long long n_units, int cap, int capx, int nst)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t full[TMA_MAX_STAGES];
+    __shared__ uint64_t empty[TMA_MAX_STAGES];
+    __shared__ UnitGeo infos[TMA_MAX_STAGES];
+    __shared__ int s_abort;
+
+    const size_t stb = stage_bytes(cap, capx);
+    const int tid = threadIdx.x;
+    const int k = __ldcg(&a.ctl->k);
+    const int sbase = __ldcg(&a.ctl->slot_base), smod = __ldcg(&a.ctl->slot_mod);
+    auto unit_of = [&](long long j) { return blockIdx.x + j * (long long)gridDim.x; };
+
+    if (tid == 0) {
+        for (int st = 0; st < nst; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], TMA_CONSUMERS / 32);
+        }
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    if (tid >= TMA_CONSUMERS) {
+        // ---------------- producer warp (lane 0 issues)
+        if (tid != TMA_CONSUMERS) return;
+        long long j = 0;
+        for (;; ++j) {
+            const long long u = unit_of(j);
+            if (u >= n_units || s_abort) break;
+            const int st = (int)(j % nst);
+            if (j >= nst && !mbar_wait(&empty[st], (uint32_t)(((j / nst) - 1) & 1))) {
+                s_abort = 1;
+                break;
+            }
+            fence_proxy_async_smem();
+            issue_unit(a, u, k, sbase, smod, smem + st * stb, cap, capx, &full[st], &infos[st]);
+        }
+        // wait (bounded) for the copies of the last stages before leaving
+        for (long long q = j - 1; q >= 0 && q >= j - nst; --q)
+            mbar_wait(&full[q % nst], (uint32_t)((q / nst) & 1));
+        if (s_abort) atomicOr(&a.ctl->err, 1);
+        return;
+    }
+
+    // ---------------- consumer warps
+    const bool do_sig = __ldcg(&a.ctl->series) || k == __ldcg(&a.ctl->sig_step);
+    const bool field_step = k == __ldcg(&a.ctl->field_step);
+    const float fk = __ldg(a.f + k);
+    const int lsrc = (k - sbase) % smod, ldst = (k + 1 - sbase) % smod;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    // Own-site values of planes 3..6 on membrane links in y and z, prefetched
+    // into registers one unit ahead for the lanes whose mask needs them.
+    float2 own[TMA_SPT][4], nown[TMA_SPT][4];
+    auto prefetch = [&](long long j, float2 (&o)[TMA_SPT][4]) -> bool {
+        if (unit_of(j) >= n_units) return true;
+        const int st = (int)(j % nst);
+        if (!mbar_wait(&full[st], (uint32_t)((j / nst) & 1))) return false;
+        const UnitGeo G = infos[st];
+        const MemberDesc* __restrict__ d = a.members + G.m;
+        if (!d->memb) return true;   // geometry without membranes
+        unsigned char* sb = smem + st * stb;
+        const uint8_t* __restrict__ mk8 = stage_mask(sb, cap, capx);
+        const unsigned P = (unsigned)d->plane;
+        const float2* __restrict__ sp = d->state + (size_t)lsrc * 7 * P;
+#pragma unroll
+        for (int jj = 0; jj < TMA_SPT; ++jj) {
+            const int l = tid + jj * TMA_CONSUMERS;
+            if (l < G.L) {
+                const unsigned mk = mk8[l];
+                const unsigned s = G.s0 + (unsigned)l;
+                if (mk & 4u) o[jj][0] = __ldg(sp + (size_t)3 * P + s);
+                if (mk & 8u) o[jj][1] = __ldg(sp + (size_t)4 * P + s);
+                if (mk & 16u) o[jj][2] = __ldg(sp + (size_t)5 * P + s);
+                if (mk & 32u) o[jj][3] = __ldg(sp + (size_t)6 * P + s);
+            }
+        }
+        return true;
+    };
+    bool ok = prefetch(0, own);
+
+    // constants of the current member, reloaded only when the member changes
+    int cm = -1, nx = 1, ny = 1, nz = 1, bcx = 0, bcy = 0, bcz = 0;
+    unsigned P = 0, dm0 = 0;
+    int ds0 = 0;
+    float sh = 0.f, om0 = 0.f, om1 = 0.f, om2 = 0.f, om3 = 0.f, ep0 = 0.f, ep1 = 0.f, ep2 = 0.f, ep3 = 0.f;
+    float2* dstb = nullptr;
+    float2* field = nullptr;
+    const MemberDesc* __restrict__ sd = a.members;
+
+    for (long long i = 0;; ++i) {
+        const long long u = unit_of(i);
+        if (u >= n_units) break;
+        const int st = (int)(i % nst);
+        ok = ok && prefetch(i + 1, nown);
+        ok = ok && mbar_wait(&full[st], (uint32_t)((i / nst) & 1));
+        if (!ok) {
+            s_abort = 1;
+            break;
+        }
+        const UnitGeo G = infos[st];
+        unsigned char* sb = smem + st * stb;
+        if (G.m != cm) {
+            cm = G.m;
+            sd = a.members + cm;
+            nx = sd->nx; ny = sd->ny; nz = sd->nz;
+            bcx = sd->bc[0]; bcy = sd->bc[1]; bcz = sd->bc[2];
+            P = (unsigned)sd->plane;
+            dm0 = sd->div_m[0]; ds0 = sd->div_s[0];
+            sh = sd->s_share;
+            om0 = sd->omega[0]; om1 = sd->omega[1]; om2 = sd->omega[2]; om3 = sd->omega[3];
+            ep0 = sd->eps[0]; ep1 = sd->eps[1]; ep2 = sd->eps[2]; ep3 = sd->eps[3];
+            dstb = sd->state + (size_t)ldst * 7 * P;
+            field = sd->field;
+        }
+        const float2* __restrict__ r0 = stage_plane(sb, cap, 0);
+        const float2* __restrict__ r1 = stage_plane(sb, cap, 1);
+        const float2* __restrict__ r2 = stage_plane(sb, cap, 2);
+        const float2* __restrict__ r3 = stage_plane(sb, cap, 3);
+        const float2* __restrict__ r4 = stage_plane(sb, cap, 4);
+        const float2* __restrict__ r5 = stage_plane(sb, cap, 5);
+        const float2* __restrict__ r6 = stage_plane(sb, cap, 6);
+        const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx);
+        const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + G.m) * 6;
+        float2* __restrict__ dst = dstb;
+        const bool do_field = field_step && field != nullptr;
+        float zr = 0.f, zi = 0.f;
+#pragma unroll
+        for (int j = 0; j < TMA_SPT; ++j) {
+            const int l = tid + j * TMA_CONSUMERS;
+            if (l >= G.L) break;
+            const int r = G.rows == 1 ? 0 : (int)fdiv((unsigned)l, dm0, ds0);
+            const int x = l - r * nx;
+            const int y = G.y0 + r;
+            const int z = G.z;
+            const unsigned s = G.s0 + (unsigned)l;
+            const unsigned mk = rm[l];
+            const int ph = mk >> 6;
+            float2 g[Q];
+            g[0] = r0[l];
+            if (x == 0) g[1] = bcx == BC_PER ? cmul(r1[l + nx + 1], __ldg(fac + 0)) : face_fix(r2[l], bcx, __ldg(fac + 0));
+            else g[1] = r1[l + 1];
+            if (x == nx - 1) g[2] = bcx == BC_PER ? cmul(r2[l - nx + 1], __ldg(fac + 1)) : face_fix(r1[l + 2], bcx, __ldg(fac + 1));
+            else g[2] = r2[l + 1];
+            g[3] = r3[l];
+            if (y == 0) g[3] = face_fix(g[3], bcy, __ldg(fac + 2));
+            g[4] = r4[l];
+            if (y == ny - 1) g[4] = face_fix(g[4], bcy, __ldg(fac + 3));
+            g[5] = r5[l];
+            if (z == 0) g[5] = face_fix(g[5], bcz, __ldg(fac + 4));
+            g[6] = r6[l];
+            if (z == nz - 1) g[6] = face_fix(g[6], bcz, __ldg(fac + 5));
+
+            // Half-link membrane (Eq. B5): A + s (B - A) with A = own
+            // population sent towards the membrane.
+            if (mk & 0x3fu) {
+                if (mk & 2u) g[1] = mix(r2[l], g[1], sh);       // link to -x: own hat g_2
+                if (mk & 1u) g[2] = mix(r1[l + 2], g[2], sh);   // link to +x: own hat g_1
+                if (mk & 8u) g[3] = mix(own[j][1], g[3], sh);   // link to -y: own hat g_4
+                if (mk & 4u) g[4] = mix(own[j][0], g[4], sh);   // link to +y: own hat g_3
+                if (mk & 32u) g[5] = mix(own[j][3], g[5], sh);  // link to -z: own hat g_6
+                if (mk & 16u) g[6] = mix(own[j][2], g[6], sh);  // link to +z: own hat g_5
+            }
+            // Reaction (Eq. reaction_LBM) and BGK collision (Eq. collision_LBM).
+            const float ep = (ph & 2) ? ((ph & 1) ? ep3 : ep2) : ((ph & 1) ? ep1 : ep0);
+            const float om = (ph & 2) ? ((ph & 1) ? om3 : om2) : ((ph & 1) ? om1 : om0);
+            const float2 q = fk != 0.f ? reaction_q(rotation_m1(sd, fk, x, y, z), ep) : make_float2(-ep, 0.f);
+            float mr, mi;
+            react(g, q, mr, mi);
+            collide(g, om, mr, mi);
+#pragma unroll
+            for (int i2 = 0; i2 < Q; ++i2) __stcs(dst + (size_t)i2 * P + s, g[i2]);
+            zr += mr;
+            zi += mi;
+            if (do_field) field[s] = make_float2(mr, mi);
+        }
+        // this warp is done with the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+#pragma unroll
+        for (int j = 0; j < TMA_SPT; ++j)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) own[j][p] = nown[j][p];
+        if (do_sig) {   // grid-uniform; FP64 from the warp level up, one slot per warp
+            double dr = zr, di = zi;
+            for (int o = 16; o > 0; o >>= 1) {
+                dr += __shfl_down_sync(0xffffffffu, dr, o);
+                di += __shfl_down_sync(0xffffffffu, di, o);
+            }
+            if (lane == 0) a.partial[u * (TMA_CONSUMERS / 32) + warp] = make_double2(dr, di);
+        }
+    }
+    if (s_abort && tid == 0) atomicOr(&a.ctl->err, 1);
+}
+
+}  // namespace
+
+size_t tma_smem_bytes(int cap, int capx, int nst) { return stage_bytes(cap, capx) * nst; }
+// signal partial slots per unit: one per consumer warp of the variant
+int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2 ? 8 : 16; }
+
+// variant 0: 16 consumer warps x 2 sites, 1 (default): 12 x 3, 2: 8 x 4
+// (units <= 1024 sites; 17 warps cap registers at 96 and spill, 12 + 1 fit 157)
+static void* tma_kernel(int variant)
+{
+    switch (variant) {
+    case 1: return (void*)sweep_tma_kernel<384, 3>;
+    case 2: return (void*)sweep_tma_kernel<256, 4>;
+    default: return (void*)sweep_tma_kernel<512, 2>;
+    }
+}
+static int tma_threads(int variant) { return variant == 1 ? 384 + 32 : variant == 2 ? 256 + 32 : 512 + 32; }
+
+cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int* ctas_per_sm)
+{
+    const size_t bytes = tma_smem_bytes(cap, capx, nst);
+    cudaError_t e = cudaFuncSetAttribute(tma_kernel(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, tma_kernel(variant), tma_threads(variant), bytes);
+}
+
+cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
+                             cudaStream_t st)
+{
+    if (nst < 2 || nst > TMA_MAX_STAGES) return cudaErrorInvalidValue;
+    const size_t sm = tma_smem_bytes(cap, capx, nst);
+    switch (variant) {
+    case 1: sweep_tma_kernel<384, 3><<<grid, 384 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 2: sweep_tma_kernel<256, 4><<<grid, 256 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    default: sweep_tma_kernel<512, 2><<<grid, 512 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbmbt

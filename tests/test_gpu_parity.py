@@ -231,13 +231,17 @@ def test_graph_and_launch_shapes_do_not_change_results(lb):
     gG, f = oracle.pgse(2000.0, 1.0, 3.0, dt, (1, 1, 0))
     s = _solver(lb, geom, (0, 0, 0), D, T2, kap, dt, f, gG)
     base = s.run()["S"]
-    for graph, block, spt in [(0, 256, 2), (1, 128, 1), (1, 512, 1), (1, 256, 4), (0, 64, 4)]:
+    for graph, block, spt, kern in [(0, 256, 2, 1), (1, 128, 1, 1), (1, 512, 1, 1), (1, 256, 4, 1), (0, 64, 4, 1),
+                                    (1, 256, 2, 2), (0, 256, 2, 2)]:
         s.set_option(lb.OPT_GRAPH, graph)
         s.set_option(lb.OPT_BLOCK, block)
         s.set_option(lb.OPT_SPT, spt)
-        assert s.run()["S"] == pytest.approx(base, rel=1e-12)
+        s.set_option(lb.OPT_KERNEL, kern)
+        # the fields are bit-identical across shapes and kernels; the signal's
+        # per-thread FP32 partial sums group sites differently, ~1e-9 relative
+        assert s.run()["S"] == pytest.approx(base, rel=1e-7)
     s.set_option(lb.OPT_AUTOTUNE, 1)
-    assert s.run()["S"] == pytest.approx(base, rel=1e-12)
+    assert s.run()["S"] == pytest.approx(base, rel=1e-7)
     s.close()
 
 
@@ -270,7 +274,7 @@ def test_batch_matches_plain_runs(lb):
         o = _oracle(geom, (0, 0, 0), D, T2, kap, dt, f, gG)
         assert abs(rb["S"][i] - o["S"]) <= S_TOL * o["S"], i
         with _solver(lb, geom, (0, 0, 0), D, T2, kap, dt, f, gG) as sp:
-            assert sp.run()["S"] == pytest.approx(rb["S"][i], rel=1e-12)
+            assert sp.run()["S"] == pytest.approx(rb["S"][i], rel=1e-7)
 
 
 # -------------------------------------------------------------- errors
@@ -300,4 +304,76 @@ def test_error_codes(lb):
     assert math.isfinite(s.run()["S"])
     with pytest.raises(lb.LbmbtError):
         s.set_option(lb.OPT_SPT, 3)
+    s.close()
+
+
+# --------------------------------------------- bulk-copy (TMA) sweep
+TMA_CASES = [
+    ((8, 20, 16), (1, 1, 1), (1, 0, 0)),      # one 20-row unit per plane: both y faces in one unit
+    ((6, 37, 32), (1, 0, 0), (1, 0, 0)),      # 16-row units, ragged last unit, periodic y
+    ((5, 9, 48), (0, 1, 1), (0, 0, 1)),       # mirror y/z, G normal to z
+    ((3, 4, 512), (1, 0, 0), (0, 0.6, 0.8)),  # one row per unit, oblique G parallel to the x mirror
+    ((1, 1, 64), (0, 0, 0), (1, 1, 1)),       # single row, every axis wraps onto itself
+    ((2, 1, 16), (0, 1, 0), (1, 0, 0)),       # ny = 1 with a mirror on y
+]
+
+
+@pytest.mark.parametrize("case", range(len(TMA_CASES)))
+def test_bulk_copy_sweep_parity(lb, case):
+    """The bulk-copy sweep equals the register sweep bit for bit on the field
+    and both match the oracle, on grids whose row units cover faces, ragged
+    units, degenerate axes and membranes on most links."""
+    shape, bc, d = TMA_CASES[case]
+    rng = np.random.default_rng(100 + case)
+    lab = rng.integers(0, 3, size=shape).astype(np.int32)
+    geom = synth.Geometry(lab, np.array([0, 1, 2], np.uint8), 0.5)
+    dt = 0.02
+    D, T2, kap = [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.04
+    gG, f = oracle.pgse(1500.0, 1.0, 2.0, dt, d)
+    out = {}
+    for kern, tshape in ((1, 0), (2, 0), (2, 1), (2, 2)):
+        s = _solver(lb, geom, bc, D, T2, kap, dt, f, gG)
+        s.set_option(lb.OPT_KERNEL, kern)
+        s.set_option(lb.OPT_TMA_SHAPE, tshape)
+        r, fld = _gpu_field(s, geom.n_sites)
+        assert s.get_option(lb.OPT_KERNEL_USED) == kern
+        s.close()
+        out[(kern, tshape)] = (r, fld)
+    for key in out:
+        assert np.array_equal(out[(1, 0)][1], out[key][1]), key
+    o = _oracle(geom, bc, D, T2, kap, dt, f, gG, want_field=True)
+    for kern in out:
+        assert abs(out[kern][0]["S"] - o["S"]) <= S_TOL * o["S"]
+        assert _field_err(out[kern][1].reshape(shape), o["field"]) < FIELD_TOL
+
+
+def test_bulk_copy_sweep_rejects_ineligible_grid(lb):
+    geom = synth.uniform((4, 4, 24), 1.0)
+    s = _solver(lb, geom, (0, 0, 0), [2.0], [INF], INF, 0.05, np.zeros(4), [0, 0, 0])
+    s.set_option(lb.OPT_KERNEL, 2)
+    with pytest.raises(lb.LbmbtError):
+        s.run()
+    s.set_option(lb.OPT_KERNEL, 0)
+    s.run()
+    assert s.get_option(lb.OPT_KERNEL_USED) == 1
+    s.close()
+
+
+def test_signal_partials_do_not_leak_between_runs(lb):
+    """Runs with different kernels and launch shapes in one context reuse the
+    per-tile signal buffer: every shape must reduce only its own slots."""
+    geom = synth.cylinders(32, 0.5, seed=4)
+    dt = 0.025
+    D, T2, kap = [2.0, 1.0], [80.0, 50.0], 0.02
+    gG, f = oracle.pgse(2000.0, 1.0, 3.0, dt, (1, 1, 0))
+    o = _oracle(geom, (0, 0, 0), D, T2, kap, dt, f, gG)
+    s = _solver(lb, geom, (0, 0, 0), D, T2, kap, dt, f, gG)
+    for kern, shape, block, spt in [(1, 0, 64, 1), (2, 0, 256, 2), (2, 1, 256, 2), (2, 2, 256, 2), (1, 0, 512, 4),
+                                    (2, 1, 128, 1)]:
+        s.set_option(lb.OPT_KERNEL, kern)
+        s.set_option(lb.OPT_TMA_SHAPE, shape)
+        s.set_option(lb.OPT_BLOCK, block)
+        s.set_option(lb.OPT_SPT, spt)
+        r = s.run()
+        assert abs(r["S"] - o["S"]) <= S_TOL * o["S"], (kern, shape, block, spt)
     s.close()
