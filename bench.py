@@ -197,6 +197,138 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched (c3)
+C2_D, C2_T2, C2_KAPPA = [2.0, 1.0], [80.0, 50.0], 0.02   # phase 0 extracellular, 1 intracellular
+C2_DT, C2_DELTA, C2_BIG_DELTA = 0.00625, 10.0, 30.0
+
+
+def batch_workload(seed=7):
+    """64 directions x 8 b-values on one 128^3 cylinder pack (dx 0.5 um) plus
+    16 sphere packs of uneven edges (multiples of 16 in 48..160, radii
+    U(2, 6) um, fraction 0.5, kappa U(0, 0.05) um/ms), one member each."""
+    from paper_1907_00908_gb300 import lbmbt, synth
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cyl = synth.cylinders(128, 0.5, seed=1)
+    dirs = synth.directions_on_sphere(64, seed=seed)
+    bvals = np.linspace(0.0, 3000.0, 8)
+    members = []
+    for d in dirs:
+        for b in bvals:
+            gG, _ = lbmbt.pgse(float(b), C2_DELTA, C2_BIG_DELTA, C2_DT, d)
+            members.append((gG, 0, C2_KAPPA))
+    sizes = rng.choice(np.arange(48, 161, 16), size=16)
+    packs = []
+    for j, n in enumerate(sizes):
+        g = synth.spheres(int(n), 0.5, rmin=2.0, rmax=6.0, fraction=0.5, seed=100 + j)
+        packs.append(g)
+        gG, _ = lbmbt.pgse(float(bvals[j % 8]), C2_DELTA, C2_BIG_DELTA, C2_DT, dirs[j])
+        members.append((gG, 1 + j, float(rng.uniform(0.0, 0.05))))
+    _, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, C2_DT, (1, 0, 0))
+    return cyl, packs, members, f
+
+
+def run_batch(args):
+    import torch
+    from paper_1907_00908_gb300 import lbmbt
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    cyl, packs, members, f = batch_workload()
+    s = lbmbt.Solver(0, stream)
+    s.set_geometry(cyl.labels, cyl.phase_of_label, 0.5)
+    for g in packs:
+        s.add_geometry(g.labels, g.phase_of_label, 0.5)
+    s.set_phases(C2_D, C2_T2)
+    s.set_sequence(C2_DT, f, members[0][0])
+    mem = lbmbt.Solver.members([m[0] for m in members], [m[1] for m in members], [m[2] for m in members])
+    sites = [cyl.n_sites] * 512 + [g.n_sites for g in packs]
+    total_sites = float(sum(sites))
+
+    def timed(solver, mems, steps, warm):
+        solver.prepare(mems)
+        solver.advance(warm)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        solver.advance(steps, want_signal=True, n_members=len(mems))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    with Clocks(0) as clk:
+        ms_batch = timed(s, mem, args.steps, args.warmup)
+    kernel = s.get_option(lbmbt.OPT_KERNEL_USED)
+    one = lbmbt.Solver.members([members[5][0]], 0, C2_KAPPA)
+    ms_plain = timed(s, one, args.steps, args.warmup)
+    s.close()
+    peak, peak_kind = peaks()
+    v = total_sites / (ms_batch * 1e-3) / 1e6
+    vp = cyl.n_sites / (ms_plain * 1e-3) / 1e6
+    line = {"metric": "MLUPS (batched sweep, FP32, 528 members)", "value": v, "unit": "MLUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_c3_128cyl_64dirx8b_plus_16_packs", "members": len(members),
+                       "sites_per_step": total_sites, "pack_edges": [int(g.shape[0]) for g in packs],
+                       "kernel": "bulk-copy" if kernel == 2 else "register"},
+            "plain_single_direction": {"value": vp, "unit": "MLUPS", "ms_per_step": ms_plain,
+                                       "workload": "128^3 cylinders, 1 member"},
+            "batched_over_plain": v / vp,
+            "roofline": {"bound": "hbm", "achieved": v * 1e6 * BYTES_PER_SITE / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": v * 1e6 * BYTES_PER_SITE / 1e9 / peak, "peak_source": peak_kind},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- adjoint (c4)
+def run_adjoint(args):
+    import torch
+    from paper_1907_00908_gb300 import lbmbt, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    geom = synth.spheres(96, 0.5, rmin=2.0, rmax=6.0, fraction=0.5, seed=4)
+    dirs = synth.directions_on_sphere(30, seed=11)
+    gGs = []
+    for b in (1000.0, 2500.0):
+        for d in dirs:
+            gGs.append(lbmbt.pgse(b, C2_DELTA, C2_BIG_DELTA, C2_DT, d)[0])
+    _, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, C2_DT, (1, 0, 0))
+    K = args.steps
+    f = f[:K]
+    s = lbmbt.Solver(0, stream)
+    s.set_geometry(geom.labels, geom.phase_of_label, 0.5)
+    s.set_phases(C2_D, C2_T2)
+    s.set_sequence(C2_DT, f, gGs[0])
+    mem = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
+    s.grad_batch(lbmbt.Solver.members(gGs[:2], 0, C2_KAPPA), checkpoint_every=64)  # warm-up
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = s.grad_batch(mem, checkpoint_every=64)
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = s.run_batch(mem)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    s.close()
+    work = geom.n_sites * len(gGs) * K
+    line = {"metric": "MLUPS-equivalent (gradient of S wrt D, T2, kappa; forward + checkpointed adjoint)",
+            "value": work / t_grad / 1e6, "unit": "MLUPS", "n_gpus": 1, "steps": K, "warmup": 1,
+            "ms_per_step": 1e3 * t_grad / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint_c4_96pack_30dirx2b", "members": len(gGs), "checkpoint_every": 64,
+                       "sites": geom.n_sites, "steps_of_schedule": K},
+            "plain_forward": {"value": work / t_fwd / 1e6, "unit": "MLUPS", "seconds": t_fwd},
+            "gradient_over_forward_time": t_grad / t_fwd,
+            "sample_gradient_member0": {"S": float(g["S"][0]), "dS_dD": g["dD"][0].tolist(),
+                                        "dS_dT2": g["dT2"][0].tolist(), "dS_dkappa": float(g["dkappa"][0])},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -208,9 +340,16 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
+    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint"],
+                    help="tissue512 (default): the 512^3 tissue batch of 3 directions; batch: 528 members on "
+                         "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     import torch
     import torch.distributed as dist
@@ -256,12 +395,10 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
     launches = s.launch_count() - l0
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    from paper_1907_00908_gb300 import shard
+    ms = shard.max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms = float(t.item())
     value = n_sites * nm * args.steps * world / (ms * 1e-3) / 1e6
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE * n_sites * nm / per_launch_s / 1e9
@@ -283,11 +420,7 @@ def main():
         s2.prepare(members)
         sig2 = s2.advance(args.steps, want_signal=True, n_members=nm)
         torch.cuda.synchronize()
-        te = time.perf_counter() - h0
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+        te = shard.max_over_ranks(time.perf_counter() - h0, dist if world > 1 else None, dev)
         s2.close()
         h2d = n_sites * 4 + geom.phase_of_label.size + K_total * (4 + 8) + nm * 200
         d2h = nm * 16

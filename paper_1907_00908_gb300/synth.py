@@ -88,35 +88,46 @@ def _relax_periodic(centers, radii, box, gap, max_iter=4000, rng=None):
     """Place discs/spheres without overlap in a periodic box.
 
     Radii are grown from 60 % to full size in steps; after each growth step
-    overlapping pairs are pushed apart along their centre line (minimum
-    image) until none overlap.  Returns the centres and the iterations used.
+    overlapping pairs (found with a periodic KD-tree) are pushed apart along
+    their centre line (minimum image) until none overlap.  Returns the
+    centres and the iterations used.
     """
-    c = centers.copy()
+    from scipy.spatial import cKDTree
+
+    c = np.array(centers, dtype=np.float64) % box
     dim = c.shape[1]
+    boxv = np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,)).copy()
     total = 0
     for scale in np.linspace(0.6, 1.0, 9):
         rad = radii * scale
+        reach = 2.0 * float(rad.max()) + gap
         for it in range(max_iter):
-            d = c[:, None, :] - c[None, :, :]
-            d -= box * np.round(d / box)
-            dist = np.sqrt((d * d).sum(-1))
-            need = rad[:, None] + rad[None, :] + gap
-            np.fill_diagonal(dist, np.inf)
-            if (dist >= need).all():
+            tree = cKDTree(c, boxsize=boxv)
+            pairs = tree.query_pairs(reach, output_type="ndarray")
+            if len(pairs) == 0:
                 break
+            i, j = pairs[:, 0], pairs[:, 1]
+            d = c[i] - c[j]
+            d -= boxv * np.round(d / boxv)
+            dist = np.sqrt((d * d).sum(-1))
+            need = rad[i] + rad[j] + gap
+            bad = dist < need
+            if not bad.any():
+                break
+            i, j, d, dist, need = i[bad], j[bad], d[bad], dist[bad], need[bad]
             ov = need + 1e-6 - dist  # push slightly past contact
-            ov[ov < 0] = 0.0
+            safe = np.where(dist > 1e-12, dist, 1.0)
+            u = d / safe[:, None]
+            coinc = dist <= 1e-12
+            if coinc.any():
+                rnd = (rng or np.random.default_rng(0)).normal(size=(int(coinc.sum()), dim))
+                u[coinc] = rnd / np.linalg.norm(rnd, axis=1, keepdims=True)
+            wi = rad[j] ** dim / (rad[i] ** dim + rad[j] ** dim)
+            push = 0.55 * ov[:, None] * u
+            np.add.at(c, i, push * wi[:, None])
+            np.add.at(c, j, -push * (1.0 - wi)[:, None])
+            c %= boxv
             total += 1
-            dist_safe = np.where(dist > 1e-12, dist, 1.0)
-            u = d / dist_safe[..., None]
-            coinc = dist < 1e-12
-            if coinc.any() and rng is not None:
-                rnd = rng.normal(size=u.shape)
-                rnd /= np.linalg.norm(rnd, axis=-1, keepdims=True)
-                u = np.where(coinc[..., None], rnd, u)
-            w = rad[None, :] ** dim / (rad[:, None] ** dim + rad[None, :] ** dim)
-            c += 0.55 * ((ov * w)[..., None] * u).sum(1)
-            c %= box
         else:
             raise RuntimeError("packing relaxation did not converge; lower the target fraction")
     return c, total
