@@ -377,3 +377,45 @@ def test_signal_partials_do_not_leak_between_runs(lb):
         r = s.run()
         assert abs(r["S"] - o["S"]) <= S_TOL * o["S"], (kern, shape, block, spt)
     s.close()
+
+
+# --------------------------------------------- full size (benchmark workload)
+def test_full_size_tissue_sampled_parity(lb):
+    """The benchmark workload at full size (512^3 tissue, mirror faces, three
+    directions, default launch configuration = bulk-copy sweep): the field
+    after 8 steps at sampled interior, face, edge and corner sites equals the
+    oracle (crop method, cropcheck.py, pinned against full oracle runs), and
+    the batched signal equals the per-direction runs."""
+    import bench
+    import cropcheck
+    geom = bench.geometry(512)
+    seqs = bench.sequences()
+    k = 8
+    rng = np.random.default_rng(5)
+    sites = [tuple(int(v) for v in rng.integers(20, 490, size=3)) for _ in range(6)]
+    sites += [(0, 0, 0), (0, 250, 17), (300, 0, 0), (77, 1, 400), (5, 480, 0), (0, 3, 255)]
+    idx = torch.tensor([(z * 512 + y) * 512 + x for (z, y, x) in sites], device="cuda")
+    S_plain = []
+    for gG, f in seqs:
+        s = lb.Solver(0)
+        s.set_geometry(geom.labels, geom.phase_of_label, bench.DX, (1, 1, 1))
+        s.set_phases(bench.D, bench.T2)
+        s.set_permeability(bench.KAPPA)
+        s.set_sequence(bench.DT, f[:k], gG)
+        fld = torch.zeros(geom.n_sites, dtype=torch.complex64, device="cuda")
+        r = s.run(field=fld)
+        assert s.get_option(lb.OPT_KERNEL_USED) == 2
+        s.close()
+        got = fld[idx].cpu().numpy()
+        del fld
+        ref = cropcheck.sample_values(geom.labels, geom.phase_of_label, (1, 1, 1), bench.DX, bench.D, bench.T2,
+                                      bench.KAPPA, bench.DT, f, gG, sites, k)
+        assert np.abs(got - ref).max() <= FIELD_TOL * np.abs(ref).max()
+        S_plain.append(r["S"])
+    s = lb.Solver(0)
+    s.set_geometry(geom.labels, geom.phase_of_label, bench.DX, (1, 1, 1))
+    s.set_phases(bench.D, bench.T2)
+    s.set_sequence(bench.DT, seqs[0][1][:k], seqs[0][0])
+    rb = s.run_batch(lb.Solver.members([g for g, _ in seqs], 0, bench.KAPPA))
+    s.close()
+    np.testing.assert_allclose(rb["S"], S_plain, rtol=1e-7)

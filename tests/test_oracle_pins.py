@@ -305,3 +305,20 @@ def test_oracle_mask_matches_numpy_definition():
                 diff[tuple(idx)] = False
             exp |= diff.astype(np.uint16) << i
         assert np.array_equal(m, exp.astype(np.uint8))
+
+
+# ------------------------------------------------------ sampled checking
+@pytest.mark.parametrize("gdir,bc", [((1, 0, 0), (1, 1, 1)), ((0, 0, 1), (1, 1, 1)), ((0.6, 0.8, 0.0), (0, 0, 0))])
+def test_crop_sampling_reproduces_full_run(gdir, bc):
+    """The crop method used for full-size GPU checks (cropcheck.py) gives
+    the full run's values at interior, face and corner sites."""
+    import cropcheck
+    geom = synth.crop(synth.voronoi_tissue(64, 0.5, cell_diam=6.0, vessel_radius=2.0, seed=21), 36)
+    dt, k = 0.025, 6
+    gG, f = oracle.pgse(1500.0, 1.0, 2.0, dt, gdir)
+    D, T2, kap = [1.0, 2.5, 3.0], [50.0, 80.0, 80.0], 0.03
+    full = oracle.run(geom.labels, geom.dx, geom.phase_of_label, bc, D, T2, kap, dt, f[:k], gG, want_field=True)
+    sites = [(18, 17, 16), (0, 0, 0), (0, 20, 11), (12, 0, 25), (20, 19, 0), (2, 28, 3)]
+    vals = cropcheck.sample_values(geom.labels, geom.phase_of_label, bc, geom.dx, D, T2, kap, dt, f, gG, sites, k)
+    ref = np.array([full["field"][s] for s in sites])
+    np.testing.assert_allclose(vals, ref, rtol=0, atol=1e-13)
