@@ -337,6 +337,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
@@ -372,6 +373,8 @@ def main():
     nm = len(seqs)
 
     s = lbmbt.Solver(local, stream)
+    if not args.no_autotune:
+        s.set_option(lbmbt.OPT_AUTOTUNE, 1)
     if args.block:
         s.set_option(lbmbt.OPT_BLOCK, args.block)
     if args.spt:
@@ -395,6 +398,10 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
     launches = s.launch_count() - l0
+    shape = {"kernel": "bulk-copy" if s.get_option(lbmbt.OPT_KERNEL_USED) == 2 else "register",
+             "tma_shape": s.get_option(lbmbt.OPT_TMA_SHAPE), "stages": s.get_option(lbmbt.OPT_STAGES),
+             "block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT),
+             "autotuned": not args.no_autotune}
     from paper_1907_00908_gb300 import shard
     ms = shard.max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
     if world > 1:
@@ -443,7 +450,7 @@ def main():
             "config": {"workload": WORKLOAD, "grid": [args.n] * 3, "dx_um": DX, "dt_ms": DT, "members": nm,
                        "bc": "mirror", "phases": 3, "kappa_um_ms": KAPPA, "b_s_mm2": B,
                        "l2": "state of 15 GB per direction, far larger than L2; no flush needed",
-                       "sites_per_step": n_sites * nm, "geometry_gen_s": round(t_geo, 1)},
+                       "sites_per_step": n_sites * nm, "geometry_gen_s": round(t_geo, 1), "launch": shape},
             "signal_after_timed_steps": [float(x) for x in sig[:, 2]],
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

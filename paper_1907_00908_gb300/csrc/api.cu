@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -75,6 +76,9 @@ struct lbmbt_ctx {
     int tma_capx = 0;
     int tma_stages = 3;
     int tma_variant = 1;
+    int tuned_kernel = 0;         // 0: untuned, 1 register, 2 bulk copy (auto follows it)
+    struct Tuned { int kernel, block, spt, variant, stages; };
+    std::map<std::string, Tuned> tune_cache;
     int tma_grid = 0;
     int sm_count = 0;
     int tile_block = 0, tile_spt = 0;
@@ -440,7 +444,8 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     const long long tile = (long long)block * spt;
     c->tile_start.assign(c->n_members + 1, 0);
     c->unit_start.assign(c->n_members + 1, 0);
-    const bool tma = (c->kernel_opt == 0 || c->kernel_opt == 2) && tma_eligible(c);
+    const bool want = c->kernel_opt == 2 || (c->kernel_opt == 0 && c->tuned_kernel != 1);
+    const bool tma = want && tma_eligible(c);
     if (c->kernel_opt == 2 && !tma)
         return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member", TMA_MAX_CAP);
     int cap = 16, capx = 0;
@@ -553,36 +558,71 @@ static int issue_step(lbmbt_ctx* c)
     return LBMBT_OK;
 }
 
+// Times a few steps of every launch shape that fits -- register sweep block x
+// sites per thread, bulk-copy sweep consumer shape x stages -- and keeps the
+// fastest for this problem shape (cached per shape for the context's life).
 static int autotune(lbmbt_ctx* c)
 {
-    static const int cand[][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 2}, {256, 2}, {512, 2}, {128, 4}, {256, 4}};
-    cudaEvent_t e0, e1;
-    CU(c, cudaEventCreate(&e0));
-    CU(c, cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bb = c->block, bs = c->spt;
-    const bool saved_series = c->series_mode;
-    c->series_mode = false;
-    for (auto& cd : cand) {
-        int rc = build_worklist(c, cd[0], cd[1]);
-        if (rc) return rc;
-        rc = init_state(c);
-        if (!rc) rc = write_ctl(c, -1, -1);
-        if (rc) return rc;
-        issue_step(c);
-        CU(c, cudaEventRecord(e0, c->stream));
-        for (int r = 0; r < 4; ++r) issue_step(c);
-        CU(c, cudaEventRecord(e1, c->stream));
-        CU(c, cudaEventSynchronize(e1));
-        float ms = 0;
-        CU(c, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; bb = cd[0]; bs = cd[1]; }
+    std::string key = std::to_string(c->n_members);
+    for (auto& d : c->descs) key += "/" + std::to_string(d.nx) + "x" + std::to_string(d.ny) + "x" + std::to_string(d.nz);
+    auto it = c->tune_cache.find(key);
+    if (it == c->tune_cache.end()) {
+        struct Cand { int kernel, block, spt, variant, stages; };
+        std::vector<Cand> cand;
+        if (c->kernel_opt != 2)
+            for (auto bs : {std::make_pair(128, 1), std::make_pair(256, 1), std::make_pair(512, 1),
+                            std::make_pair(128, 2), std::make_pair(256, 2), std::make_pair(512, 2),
+                            std::make_pair(128, 4), std::make_pair(256, 4)})
+                cand.push_back({1, bs.first, bs.second, c->tma_variant, c->tma_stages});
+        if (c->kernel_opt != 1 && tma_eligible(c))
+            for (int v = 0; v < 3; ++v)
+                for (int st = 2; st <= 4; ++st) cand.push_back({2, c->block, c->spt, v, st});
+        const int saved_opt = c->kernel_opt, saved_block = c->block, saved_spt = c->spt;
+        const int saved_var = c->tma_variant, saved_st = c->tma_stages;
+        const bool saved_series = c->series_mode;
+        c->series_mode = false;
+        cudaEvent_t e0, e1;
+        CU(c, cudaEventCreate(&e0));
+        CU(c, cudaEventCreate(&e1));
+        float best = 1e30f;
+        Cand win = {0, saved_block, saved_spt, saved_var, saved_st};
+        for (const Cand& cd : cand) {
+            c->kernel_opt = cd.kernel;
+            c->tma_variant = cd.variant;
+            c->tma_stages = cd.stages;
+            if (build_worklist(c, cd.block, cd.spt) != LBMBT_OK) {  // e.g. stages do not fit
+                c->err.clear();
+                cudaGetLastError();
+                continue;
+            }
+            int rc = init_state(c);
+            if (!rc) rc = write_ctl(c, -1, -1);
+            if (!rc) rc = issue_step(c);
+            if (rc) break;
+            CU(c, cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < 4 && !rc; ++r) rc = issue_step(c);
+            CU(c, cudaEventRecord(e1, c->stream));
+            CU(c, cudaEventSynchronize(e1));
+            float ms = 0;
+            CU(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (!rc && ms < best) { best = ms; win = cd; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->kernel_opt = saved_opt;
+        c->block = saved_block;
+        c->spt = saved_spt;
+        c->tma_variant = saved_var;
+        c->tma_stages = saved_st;
+        c->series_mode = saved_series;
+        it = c->tune_cache.emplace(key, lbmbt_ctx::Tuned{win.kernel, win.block, win.spt, win.variant, win.stages}).first;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    c->series_mode = saved_series;
-    c->block = bb;
-    c->spt = bs;
+    const lbmbt_ctx::Tuned& t = it->second;
+    c->tuned_kernel = t.kernel;
+    c->block = t.block;
+    c->spt = t.spt;
+    c->tma_variant = t.variant;
+    c->tma_stages = t.stages;
     return LBMBT_OK;
 }
 
@@ -851,7 +891,10 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
     if (!c) return LBMBT_EINVAL;
     switch (opt) {
     case LBMBT_OPT_GRAPH: c->use_graph = v != 0; break;
-    case LBMBT_OPT_AUTOTUNE: c->autotune = v != 0; break;
+    case LBMBT_OPT_AUTOTUNE:
+        c->autotune = v != 0;
+        if (!c->autotune) c->tuned_kernel = 0;
+        break;
     case LBMBT_OPT_BLOCK:
         if (v < 64 || v > 512 || (v & 31)) return fail(c, LBMBT_EINVAL, "block must be a multiple of 32 in 64..512");
         c->block = (int)v;
