@@ -299,6 +299,7 @@ def run_adjoint(args):
     s.set_geometry(geom.labels, geom.phase_of_label, 0.5)
     s.set_phases(C2_D, C2_T2)
     s.set_sequence(C2_DT, f, gGs[0])
+    s.set_option(lbmbt.OPT_ADJOINT_SHAPE, args.adj_shape)
     mem = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
     s.grad_batch(lbmbt.Solver.members(gGs[:2], 0, C2_KAPPA), checkpoint_every=64)  # warm-up
     with Clocks(0) as clk:
@@ -338,6 +339,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
+    ap.add_argument("--adj-shape", type=int, default=1, help="bulk-copy adjoint consumer shape (0 or 1)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")

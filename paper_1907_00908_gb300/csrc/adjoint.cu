@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
     }
 }
 
-__global__ void reduce_grad_kernel(const double* __restrict__ gacc, const long long* __restrict__ tile_start,
+__global__ void reduce_grad_kernel(const double* __restrict__ gacc, const long long* __restrict__ tile_start, int per,
                                    double* __restrict__ out)
 {
     __shared__ double sh[NGACC][128];
@@ -235,7 +235,7 @@ __global__ void reduce_grad_kernel(const double* __restrict__ gacc, const long l
     double v[NGACC];
 #pragma unroll
     for (int j = 0; j < NGACC; ++j) v[j] = 0.0;
-    for (long long t = tile_start[m] + threadIdx.x; t < tile_start[m + 1]; t += blockDim.x)
+    for (long long t = tile_start[m] * per + threadIdx.x; t < tile_start[m + 1] * per; t += blockDim.x)
 #pragma unroll
         for (int j = 0; j < NGACC; ++j) v[j] += gacc[t * NGACC + j];
 #pragma unroll
@@ -264,10 +264,10 @@ cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int n_members, double* out,
+cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int per, int n_members, double* out,
                                cudaStream_t st)
 {
-    reduce_grad_kernel<<<n_members, 128, 0, st>>>(gacc, tile_start, out);
+    reduce_grad_kernel<<<n_members, 128, 0, st>>>(gacc, tile_start, per, out);
     return cudaGetLastError();
 }
 

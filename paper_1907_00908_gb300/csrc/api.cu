@@ -71,6 +71,14 @@ struct lbmbt_ctx {
     long long n_units = 0;
     long long* d_unit_start = nullptr;
     size_t cap_us = 0;
+    std::vector<long long> adj_unit_start;
+    long long n_adj_units = 0;
+    long long* d_adj_unit_start = nullptr;
+    size_t cap_aus = 0;
+    bool adj_tma_ok = false;
+    int adj_cap = 0;
+    int adjoint_opt = 0;          // 0 auto, 1 register adjoint, 2 bulk-copy adjoint
+    int adj_shape = 1;            // bulk-copy adjoint consumer shape (16 warps x 1 site)
     bool use_tma = false;
     int tma_cap = 0;
     int tma_capx = 0;
@@ -233,6 +241,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
     cudaFree(c->d_fac); cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab);
+    cudaFree(c->d_adj_unit_start);
     cudaFree(c->d_ck); cudaFree(c->d_seg); cudaFree(c->d_gacc); cudaFree(c->d_gout); cudaFree(c->d_laminit);
     if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
     delete c;
@@ -444,6 +453,9 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     const long long tile = (long long)block * spt;
     c->tile_start.assign(c->n_members + 1, 0);
     c->unit_start.assign(c->n_members + 1, 0);
+    c->adj_unit_start.assign(c->n_members + 1, 0);
+    int adj_cap = 16;
+    bool adj_ok = true;
     const bool want = c->kernel_opt == 2 || (c->kernel_opt == 0 && c->tuned_kernel != 1);
     const bool tma = want && tma_eligible(c);
     if (c->kernel_opt == 2 && !tma)
@@ -456,11 +468,19 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
         d.rpu = std::max(1, std::min(d.ny, TMA_TARGET_SITES / std::max(1, d.nx)));
         d.unit0 = c->unit_start[m];
         c->unit_start[m + 1] = c->unit_start[m] + (long long)d.nz * ((d.ny + d.rpu - 1) / d.rpu);
+        d.rpu_adj = std::max(1, std::min(d.ny, adj_tma_max_sites() / std::max(1, d.nx)));
+        d.unit0_adj = c->adj_unit_start[m];
+        c->adj_unit_start[m + 1] = c->adj_unit_start[m] + (long long)d.nz * ((d.ny + d.rpu_adj - 1) / d.rpu_adj);
+        adj_cap = std::max(adj_cap, d.rpu_adj * d.nx);
+        if (d.nx > adj_tma_max_sites()) adj_ok = false;
         cap = std::max(cap, d.rpu * d.nx);
         (void)capx;   // the x rotation table is read through L1, not staged
     }
     c->n_tiles = c->tile_start[c->n_members];
     c->n_units = c->unit_start[c->n_members];
+    c->n_adj_units = c->adj_unit_start[c->n_members];
+    c->adj_tma_ok = adj_ok && tma_eligible(c);
+    c->adj_cap = (adj_cap + 15) / 16 * 16;
     if (c->n_tiles > 0x7fffffffLL) return fail(c, LBMBT_EINVAL, "work list too long");
     c->use_tma = tma;
     if (tma) {
@@ -476,6 +496,7 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     int rc = grow(c, &c->d_desc, &c->cap_desc, sizeof(MemberDesc) * c->n_members);
     if (!rc) rc = grow(c, &c->d_tile_start, &c->cap_ts, sizeof(long long) * (c->n_members + 1));
     if (!rc) rc = grow(c, &c->d_unit_start, &c->cap_us, sizeof(long long) * (c->n_members + 1));
+    if (!rc) rc = grow(c, &c->d_adj_unit_start, &c->cap_aus, sizeof(long long) * (c->n_members + 1));
     if (!rc) rc = grow(c, &c->d_partial, &c->cap_partial, sizeof(double2) * n_part);
     if (!rc) rc = grow(c, &c->d_fac, &c->cap_fac, sizeof(float2) * 12 * c->n_members);
     if (rc) return rc;
@@ -484,6 +505,8 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     CU(c, cudaMemcpyAsync(c->d_tile_start, c->tile_start.data(), sizeof(long long) * (c->n_members + 1),
                           cudaMemcpyHostToDevice, c->stream));
     CU(c, cudaMemcpyAsync(c->d_unit_start, c->unit_start.data(), sizeof(long long) * (c->n_members + 1),
+                          cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->d_adj_unit_start, c->adj_unit_start.data(), sizeof(long long) * (c->n_members + 1),
                           cudaMemcpyHostToDevice, c->stream));
     c->tile_block = block;
     c->tile_spt = spt;
@@ -915,6 +938,14 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "bulk-copy shape must be 0, 1 or 2");
         c->tma_variant = (int)v;
         break;
+    case LBMBT_OPT_ADJOINT_KERNEL:
+        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "adjoint kernel must be 0 (auto), 1 or 2");
+        c->adjoint_opt = (int)v;
+        break;
+    case LBMBT_OPT_ADJOINT_SHAPE:
+        if (v < 0 || v > 1) return fail(c, LBMBT_EINVAL, "adjoint shape must be 0 or 1");
+        c->adj_shape = (int)v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -932,6 +963,8 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_KERNEL: *v = c->kernel_opt; break;
     case LBMBT_OPT_STAGES: *v = c->tma_stages; break;
     case LBMBT_OPT_TMA_SHAPE: *v = c->tma_variant; break;
+    case LBMBT_OPT_ADJOINT_KERNEL: *v = c->adjoint_opt; break;
+    case LBMBT_OPT_ADJOINT_SHAPE: *v = c->adj_shape; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
@@ -969,7 +1002,11 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     for (auto& d : c->descs) lvl_total += (size_t)7 * d.plane;
     rc = grow(c, &c->d_ck, &c->cap_ck, lvl_total * n_ck * sizeof(float2));
     if (!rc) rc = grow(c, &c->d_seg, &c->cap_seg, lvl_total * (ck + 1) * sizeof(float2));
-    if (!rc) rc = grow(c, &c->d_gacc, &c->cap_gacc, sizeof(double) * NGACC * c->n_tiles);
+    const bool adj_tma = c->adjoint_opt == 2 || (c->adjoint_opt == 0 && c->adj_tma_ok);
+    if (c->adjoint_opt == 2 && !c->adj_tma_ok)
+        return fail(c, LBMBT_EINVAL, "bulk-copy adjoint needs nx %% 16 == 0 and nx <= %d", adj_tma_max_sites());
+    const long long n_gslots = adj_tma ? c->n_adj_units * adj_tma_slots_per_unit() : c->n_tiles;
+    if (!rc) rc = grow(c, &c->d_gacc, &c->cap_gacc, sizeof(double) * NGACC * n_gslots);
     if (!rc) rc = grow(c, &c->d_gout, &c->cap_gout, sizeof(double) * NGACC * n);
     if (!rc) rc = grow(c, &c->d_laminit, &c->cap_laminit, sizeof(double2) * n);
     if (rc) return rc;
@@ -1028,7 +1065,16 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
         rd[m].state = segb[m];
     }
     CU(c, cudaMemcpyAsync(c->d_desc, rd.data(), sizeof(MemberDesc) * n, cudaMemcpyHostToDevice, c->stream));
-    CU(c, cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * NGACC * c->n_tiles, c->stream));
+    CU(c, cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * NGACC * n_gslots, c->stream));
+    int adj_grid = 0;
+    const int adj_stages = 3;
+    if (adj_tma) {
+        int per_sm = 0;
+        CU(c, adj_tma_prepare(c->adj_cap, adj_stages, c->adj_shape, &per_sm));
+        if (per_sm < 1) return fail(c, LBMBT_EINVAL, "bulk-copy adjoint does not fit on an SM");
+        if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+        adj_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_adj_units);
+    }
     if ((rc = grow(c, &c->d_ftab, &c->cap_ftab, sizeof(float2) * 6 * (size_t)(K + 1) * n))) return rc;
     CU(c, launch_factor_table(c->d_desc, n, c->d_F, K, c->d_ftab, c->stream));
     c->launches++;
@@ -1039,6 +1085,8 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     aa.lam_init = c->d_laminit;
     aa.gacc = c->d_gacc;
     aa.ftab = c->d_ftab;
+    aa.unit_start = c->d_adj_unit_start;
+    aa.ctl_err = &c->d_ctl->err;
     int parity = 1;
     for (long long seg = n_ck - 1; seg >= 0; --seg) {
         const long long k0 = seg * ck, k1 = std::min(K, k0 + ck);
@@ -1058,16 +1106,20 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
             aa.fwd_slot = (int)(k - 1 - k0);
             aa.lam_parity = parity;
             aa.fprev = (float)c->f[k - 1];
-            CU(c, launch_adjoint(aa, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
+            if (adj_tma)
+                CU(c, launch_adjoint_tma(aa, c->n_adj_units, c->adj_cap, adj_stages, c->adj_shape, adj_grid, c->stream));
+            else CU(c, launch_adjoint(aa, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
             c->launches++;
             parity ^= 1;
         }
     }
-    CU(c, launch_reduce_grad(c->d_gacc, c->d_tile_start, n, c->d_gout, c->stream));
+    if (adj_tma) CU(c, launch_reduce_grad(c->d_gacc, c->d_adj_unit_start, adj_tma_slots_per_unit(), n, c->d_gout,
+                                          c->stream));
+    else CU(c, launch_reduce_grad(c->d_gacc, c->d_tile_start, 1, n, c->d_gout, c->stream));
     c->launches++;
     std::vector<double> G((size_t)NGACC * n);
     CU(c, cudaMemcpyAsync(G.data(), c->d_gout, sizeof(double) * G.size(), cudaMemcpyDeviceToHost, c->stream));
-    if ((rc = sync(c))) return rc;
+    if ((rc = check_device_error(c))) return rc;
     c->prepared = false;  // descriptors now describe the reverse pass
     // chain rule to the physical parameters
     for (int m = 0; m < n; ++m) {

@@ -36,6 +36,8 @@ struct MemberDesc {
     long long tile0;      // first work-list tile of this member (site tiles)
     long long unit0;      // first row-unit of this member (bulk-copy sweep)
     int rpu;              // x-rows per unit of the bulk-copy sweep
+    int rpu_adj;          // x-rows per unit of the bulk-copy adjoint sweep
+    long long unit0_adj;  // first row-unit of this member (bulk-copy adjoint)
     int nx, ny, nz;
     int bc[3];            // BcMode per axis
     double gG[3];         // gamma*G0, rad/(um ms)
@@ -124,9 +126,18 @@ struct AdjointArgs {
     float fprev;                  // f_(k-1)
     double* gacc;                 // per tile NGACC doubles, accumulated
     const float2* ftab;           // [K+1][n_members][6] boundary factors
+    const long long* unit_start;  // bulk-copy adjoint: row-unit prefix
+    int* ctl_err;                 // error word of the step control
 };
 cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
-cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int n_members, double* out,
+// Sums gacc slots [tile_start[m]*per, tile_start[m+1]*per) per member.
+cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int per, int n_members, double* out,
+                               cudaStream_t st);
+// bulk-copy adjoint (adjoint_tma.cu)
+int adj_tma_slots_per_unit();
+int adj_tma_max_sites();
+cudaError_t adj_tma_prepare(int cap, int nst, int shape, int* ctas_per_sm);
+cudaError_t launch_adjoint_tma(const AdjointArgs& a, long long n_units, int cap, int nst, int shape, int grid,
                                cudaStream_t st);
 
 }  // namespace lbmbt

@@ -29,75 +29,12 @@
 // still has in flight, and returns.
 #include "lbmbt_internal.cuh"
 #include "sweep_common.cuh"
+#include "tma_common.cuh"
 
 namespace lbmbt {
 namespace {
 
 constexpr int TMA_MAX_STAGES = 6;
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// try_wait with a suspend-time hint (ns): the waiting warp sleeps until the
-// phase completes or the hint elapses instead of spinning on issue slots.
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for one phase of an mbarrier; false after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > WAIT_NS) return false;
-    return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 
 // Shared-memory stage (all parts 16-byte aligned): 7 pull rows of (cap + 2)
 // complex values (the sources listed above), capx spare complex values
@@ -115,33 +52,11 @@ __device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, in
     return stage + ((size_t)7 * (cap + 2) + capx) * sizeof(float2);
 }
 
-// Where unit u lies: member, z-plane, first row, rows, first site, sites.
-struct UnitGeo {
-    int m, z, y0, rows, L;
-    unsigned s0;
-};
-
-__device__ __forceinline__ UnitGeo unit_geo(const SweepArgs& a, long long u)
-{
-    UnitGeo G;
-    G.m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, u);
-    const MemberDesc* __restrict__ d = a.members + G.m;
-    const int ny = d->ny, nx = d->nx, rpu = d->rpu;
-    const int lu = (int)(u - d->unit0);
-    const int upz = (ny + rpu - 1) / rpu;
-    G.z = lu / upz;
-    G.y0 = (lu - G.z * upz) * rpu;
-    G.rows = min(rpu, ny - G.y0);
-    G.L = G.rows * nx;
-    G.s0 = (unsigned)G.z * ((unsigned)nx * ny) + (unsigned)G.y0 * nx;
-    return G;
-}
-
 // Thread 0: copies of unit u into `stage`, completion on `bar`.
 __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, int smod, unsigned char* stage, int cap,
                            int capx, uint64_t* bar, UnitGeo* info)
 {
-    const UnitGeo G = unit_geo(a, u);
+    const UnitGeo G = unit_geo(a.members, a.tile_start, a.n_members, u);
     *info = G;   // published to the consumers by the mbarrier (release/acquire)
     const int m = G.m, z = G.z, y0 = G.y0, rows = G.rows;
     const MemberDesc& d = a.members[m];
@@ -196,17 +111,6 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
     bulk_g2s(stage_mask(stage, cap, capx), d.mask + s0, (uint32_t)L, bar);
 }
 
-__device__ __forceinline__ float2 face_fix(float2 v, int bc, float2 f)
-{
-    if (bc == BC_MIR) return v;
-    if (bc == BC_MIR_CONJ) v.y = -v.y;
-    return cmul(v, f);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Warp-specialised persistent sweep: warp TMA_CONSUMERS/32 is the producer
 // (issues the bulk copies of every unit of this CTA into a ring of nst

@@ -23,6 +23,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5:
 BC_PERIODIC = 0
 BC_MIRROR = 1
 OPT_GRAPH, OPT_AUTOTUNE, OPT_BLOCK, OPT_SPT, OPT_KERNEL, OPT_KERNEL_USED, OPT_STAGES, OPT_TMA_SHAPE = 1, 2, 3, 4, 5, 6, 7, 8
+OPT_ADJOINT_KERNEL, OPT_ADJOINT_SHAPE = 9, 10
 
 # every entry point declared in include/lbmbt.h
 EXPORTS = [

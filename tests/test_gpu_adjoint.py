@@ -64,6 +64,13 @@ CASES = {
     "spheres_oblique": dict(geom=lambda: synth.spheres(20, 1.0, rmin=2.0, rmax=3.5, fraction=0.45, seed=4),
                             bc=(0, 0, 0), D=[2.0, 1.0], T2=[80.0, 50.0], kap=0.02, dt=0.05, b=2500.0,
                             delta=2.0, Delta=5.0, d=(0.3, -0.5, 0.8)),
+    "cylinders32_bulk": dict(geom=lambda: synth.cylinders(32, 1.0, fraction=0.5, seed=6), bc=(0, 0, 0),
+                             D=[2.0, 1.0], T2=[80.0, 50.0], kap=0.05, dt=0.05, b=1500.0,
+                             delta=2.0, Delta=5.0, d=(0.6, -0.48, 0.64)),
+    "voronoi32_mirror_bulk": dict(geom=lambda: synth.crop(synth.voronoi_tissue(48, 0.5, cell_diam=6.0,
+                                                                               vessel_radius=1.5, seed=8), 32),
+                                  bc=(1, 1, 1), D=[1.0, 2.5, 3.0], T2=[50.0, 80.0, 80.0], kap=0.01, dt=0.025,
+                                  b=1000.0, delta=1.0, Delta=3.0, d=(0, 0, 1)),
     "voronoi_mirror": dict(geom=lambda: synth.crop(synth.voronoi_tissue(40, 0.5, cell_diam=6.0, vessel_radius=1.5,
                                                                         seed=2), 22),
                            bc=(1, 1, 1), D=[1.0, 2.5, 3.0], T2=[50.0, 80.0, 80.0], kap=0.01, dt=0.025,
@@ -159,3 +166,24 @@ def test_autograd_function(lb):
     np.testing.assert_allclose(D.grad.numpy(), 2.0 * g["dD"], rtol=1e-12)
     np.testing.assert_allclose(T2.grad.numpy(), 2.0 * g["dT2"], rtol=1e-12)
     assert float(kap.grad) == pytest.approx(2.0 * g["dkappa"], rel=1e-12)
+
+
+@pytest.mark.parametrize("name", ["cylinders32_bulk", "voronoi32_mirror_bulk"])
+def test_bulk_copy_adjoint_matches_register_adjoint(lb, name):
+    """The bulk-copy adjoint sweep and the register adjoint sweep give the
+    same gradients (they differ only in the grouping of FP32 partial sums)."""
+    c = CASES[name]
+    geom = c["geom"]()
+    gG, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
+    s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gG)
+    out = {}
+    for kern, shape in ((1, 0), (2, 0), (2, 1)):
+        s.set_option(lb.OPT_ADJOINT_KERNEL, kern)
+        s.set_option(lb.OPT_ADJOINT_SHAPE, shape)
+        out[(kern, shape)] = s.grad(checkpoint_every=16)
+    s.close()
+    a = _logvec(out[(1, 0)], c["D"], c["T2"], c["kap"])
+    for key in ((2, 0), (2, 1)):
+        b = _logvec(out[key], c["D"], c["T2"], c["kap"])
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max(), key
+        assert out[(1, 0)]["S"] == out[key]["S"]
