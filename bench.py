@@ -292,6 +292,7 @@ def run_adjoint(args):
     for b in (1000.0, 2500.0):
         for d in dirs:
             gGs.append(lbmbt.pgse(b, C2_DELTA, C2_BIG_DELTA, C2_DT, d)[0])
+    gGs = gGs[:args.members]
     _, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, C2_DT, (1, 0, 0))
     K = args.steps
     f = f[:K]
@@ -340,6 +341,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--adj-shape", type=int, default=1, help="bulk-copy adjoint consumer shape (0 or 1)")
+    ap.add_argument("--members", type=int, default=60, help="adjoint workload: number of members (<= 60)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
