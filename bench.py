@@ -72,7 +72,7 @@ def peaks():
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep_tma.cu", "sweep_common.cuh", "lbmbt_internal.cuh"):
+    for f in ("sweep_tma.cu", "sweep_common.cuh", "tma_common.cuh", "lbmbt_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -181,7 +181,8 @@ enum {
     LBMBT_OPT_KERNEL_USED = 6, /* read-only: 1 or 2 for the prepared run, else 0 */
     LBMBT_OPT_STAGES = 7,    /* shared-memory stages of the bulk-copy sweep, 2..6 */
     LBMBT_OPT_TMA_SHAPE = 8, /* bulk-copy consumers x sites per thread per unit:
-                                0 = 512 x 2, 1 = 384 x 3 (default), 2 = 256 x 4 */
+                                0 = 512 x 2, 1 = 384 x 3, 2 = 256 x 4,
+                                3 = 352 x 3 (default)                         */
     LBMBT_OPT_ADJOINT_KERNEL = 9, /* 0 (default) auto, 1 register adjoint sweep,
                                 2 bulk-copy adjoint sweep (nx % 16 == 0, nx <= 512) */
     LBMBT_OPT_ADJOINT_SHAPE = 10 /* bulk-copy adjoint consumers x sites per thread:

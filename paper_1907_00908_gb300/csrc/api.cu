@@ -83,7 +83,7 @@ struct lbmbt_ctx {
     int tma_cap = 0;
     int tma_capx = 0;
     int tma_stages = 3;
-    int tma_variant = 1;
+    int tma_variant = 3;
     int tuned_kernel = 0;         // 0: untuned, 1 register, 2 bulk copy (auto follows it)
     struct Tuned { int kernel, block, spt, variant, stages; };
     std::map<std::string, Tuned> tune_cache;
@@ -598,7 +598,7 @@ static int autotune(lbmbt_ctx* c)
                             std::make_pair(128, 4), std::make_pair(256, 4)})
                 cand.push_back({1, bs.first, bs.second, c->tma_variant, c->tma_stages});
         if (c->kernel_opt != 1 && tma_eligible(c))
-            for (int v = 0; v < 3; ++v)
+            for (int v = 0; v < 4; ++v)
                 for (int st = 2; st <= 4; ++st) cand.push_back({2, c->block, c->spt, v, st});
         const int saved_opt = c->kernel_opt, saved_block = c->block, saved_spt = c->spt;
         const int saved_var = c->tma_variant, saved_st = c->tma_stages;
@@ -935,7 +935,7 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         c->tma_stages = (int)v;
         break;
     case LBMBT_OPT_TMA_SHAPE:
-        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "bulk-copy shape must be 0, 1 or 2");
+        if (v < 0 || v > 3) return fail(c, LBMBT_EINVAL, "bulk-copy shape must be 0, 1, 2 or 3");
         c->tma_variant = (int)v;
         break;
     case LBMBT_OPT_ADJOINT_KERNEL:

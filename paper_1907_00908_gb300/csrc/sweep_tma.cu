@@ -6,10 +6,14 @@
 // the 7 source row-blocks (and the mask bytes) into a shared-memory stage;
 // completion is tracked by an mbarrier (expect_tx / complete_tx).  A
 // persistent CTA walks its units through a ring of 2-6 stages, filled by a
-// producer warp and drained by 16 consumer warps, so the next units' copies
-// are in flight while the current one is computed, without holding the data
-// in registers.  The own-site values of planes 3..6 (membrane links in y and z) are
-// prefetched into registers one unit ahead.
+// producer warp and drained by 8 to 16 consumer warps, so the next units'
+// copies are in flight while the current one is computed, without holding the
+// data in registers.  A consumer first gathers the pulled populations of all
+// its sites (phase 1, after which the stage is released), then reacts,
+// collides and stores them with no branch between sites (phase 2), so the
+// arithmetic of several sites interleaves.  The own-site values of planes
+// 3..6 (membrane links in y and z) are prefetched into registers one unit
+// ahead.
 //
 // Source row-blocks of a unit starting at site s0 (all 16-byte aligned when
 // nx is even; the mask copy needs nx % 16 == 0):
@@ -249,59 +253,99 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + G.m) * 6;
         float2* __restrict__ dst = dstb;
         const bool do_field = field_step && field != nullptr;
-        float zr = 0.f, zi = 0.f;
+        const int z = G.z;
+
+        // Phase 1, every site of this thread: pulls with the face transforms
+        // and the half-link membrane rule.  Lanes past the unit's end work on
+        // site 0 of the stage and store nothing.
+        float2 g[TMA_SPT][Q];
+        unsigned mks[TMA_SPT];
+        int xs[TMA_SPT], ys[TMA_SPT];
 #pragma unroll
         for (int j = 0; j < TMA_SPT; ++j) {
-            const int l = tid + j * TMA_CONSUMERS;
-            if (l >= G.L) break;
+            const int l0 = tid + j * TMA_CONSUMERS;
+            const bool valid = l0 < G.L;
+            const int l = valid ? l0 : 0;
             const int r = G.rows == 1 ? 0 : (int)fdiv((unsigned)l, dm0, ds0);
             const int x = l - r * nx;
             const int y = G.y0 + r;
-            const int z = G.z;
-            const unsigned s = G.s0 + (unsigned)l;
-            const unsigned mk = rm[l];
-            const int ph = mk >> 6;
-            float2 g[Q];
-            g[0] = r0[l];
-            if (x == 0) g[1] = bcx == BC_PER ? cmul(r1[l + nx + 1], __ldg(fac + 0)) : face_fix(r2[l], bcx, __ldg(fac + 0));
-            else g[1] = r1[l + 1];
-            if (x == nx - 1) g[2] = bcx == BC_PER ? cmul(r2[l - nx + 1], __ldg(fac + 1)) : face_fix(r1[l + 2], bcx, __ldg(fac + 1));
-            else g[2] = r2[l + 1];
-            g[3] = r3[l];
-            if (y == 0) g[3] = face_fix(g[3], bcy, __ldg(fac + 2));
-            g[4] = r4[l];
-            if (y == ny - 1) g[4] = face_fix(g[4], bcy, __ldg(fac + 3));
-            g[5] = r5[l];
-            if (z == 0) g[5] = face_fix(g[5], bcz, __ldg(fac + 4));
-            g[6] = r6[l];
-            if (z == nz - 1) g[6] = face_fix(g[6], bcz, __ldg(fac + 5));
+            const unsigned mk = valid ? (unsigned)rm[l] : 0u;
+            g[j][0] = r0[l];
+            if (x == 0) g[j][1] = bcx == BC_PER ? cmul(r1[l + nx + 1], __ldg(fac + 0)) : face_fix(r2[l], bcx, __ldg(fac + 0));
+            else g[j][1] = r1[l + 1];
+            if (x == nx - 1) g[j][2] = bcx == BC_PER ? cmul(r2[l - nx + 1], __ldg(fac + 1)) : face_fix(r1[l + 2], bcx, __ldg(fac + 1));
+            else g[j][2] = r2[l + 1];
+            g[j][3] = r3[l];
+            if (y == 0) g[j][3] = face_fix(g[j][3], bcy, __ldg(fac + 2));
+            g[j][4] = r4[l];
+            if (y == ny - 1) g[j][4] = face_fix(g[j][4], bcy, __ldg(fac + 3));
+            g[j][5] = r5[l];
+            if (z == 0) g[j][5] = face_fix(g[j][5], bcz, __ldg(fac + 4));
+            g[j][6] = r6[l];
+            if (z == nz - 1) g[j][6] = face_fix(g[j][6], bcz, __ldg(fac + 5));
 
             // Half-link membrane (Eq. B5): A + s (B - A) with A = own
             // population sent towards the membrane.
             if (mk & 0x3fu) {
-                if (mk & 2u) g[1] = mix(r2[l], g[1], sh);       // link to -x: own hat g_2
-                if (mk & 1u) g[2] = mix(r1[l + 2], g[2], sh);   // link to +x: own hat g_1
-                if (mk & 8u) g[3] = mix(own[j][1], g[3], sh);   // link to -y: own hat g_4
-                if (mk & 4u) g[4] = mix(own[j][0], g[4], sh);   // link to +y: own hat g_3
-                if (mk & 32u) g[5] = mix(own[j][3], g[5], sh);  // link to -z: own hat g_6
-                if (mk & 16u) g[6] = mix(own[j][2], g[6], sh);  // link to +z: own hat g_5
+                if (mk & 2u) g[j][1] = mix(r2[l], g[j][1], sh);          // link to -x: own hat g_2
+                if (mk & 1u) g[j][2] = mix(r1[l + 2], g[j][2], sh);      // link to +x: own hat g_1
+                if (mk & 8u) g[j][3] = mix(own[j][1], g[j][3], sh);      // link to -y: own hat g_4
+                if (mk & 4u) g[j][4] = mix(own[j][0], g[j][4], sh);      // link to +y: own hat g_3
+                if (mk & 32u) g[j][5] = mix(own[j][3], g[j][5], sh);     // link to -z: own hat g_6
+                if (mk & 16u) g[j][6] = mix(own[j][2], g[j][6], sh);     // link to +z: own hat g_5
             }
-            // Reaction (Eq. reaction_LBM) and BGK collision (Eq. collision_LBM).
-            const float ep = (ph & 2) ? ((ph & 1) ? ep3 : ep2) : ((ph & 1) ? ep1 : ep0);
-            const float om = (ph & 2) ? ((ph & 1) ? om3 : om2) : ((ph & 1) ? om1 : om0);
-            const float2 q = fk != 0.f ? reaction_q(rotation_m1(sd, fk, x, y, z), ep) : make_float2(-ep, 0.f);
-            float mr, mi;
-            react(g, q, mr, mi);
-            collide(g, om, mr, mi);
-#pragma unroll
-            for (int i2 = 0; i2 < Q; ++i2) __stcs(dst + (size_t)i2 * P + s, g[i2]);
-            zr += mr;
-            zi += mi;
-            if (do_field) field[s] = make_float2(mr, mi);
+            mks[j] = mk;
+            xs[j] = x;
+            ys[j] = y;
         }
         // this warp is done with the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
+
+        // Phase 2: reaction (Eq. reaction_LBM), BGK collision
+        // (Eq. collision_LBM) and the stores, with no branch between sites.
+        // rot(j) gives exp(i theta) - 1 of site j; the three forms below are
+        // chosen once per unit and give the same bits as rotation_m1.
+        float zr = 0.f, zi = 0.f;
+        auto phase2 = [&](auto rot) {
+#pragma unroll
+            for (int j = 0; j < TMA_SPT; ++j) {
+                const int l = tid + j * TMA_CONSUMERS;
+                const bool valid = l < G.L;
+                const int ph = mks[j] >> 6;
+                const float ep = (ph & 2) ? ((ph & 1) ? ep3 : ep2) : ((ph & 1) ? ep1 : ep0);
+                const float om = (ph & 2) ? ((ph & 1) ? om3 : om2) : ((ph & 1) ? om1 : om0);
+                const float2 q = reaction_q(rot(j), ep);
+                float mr, mi;
+                react(g[j], q, mr, mi);
+                collide(g[j], om, mr, mi);
+                const unsigned s = G.s0 + (unsigned)l;
+                if (valid) {
+#pragma unroll
+                    for (int i2 = 0; i2 < Q; ++i2) __stcs(dst + (size_t)i2 * P + s, g[j][i2]);
+                    zr += mr;
+                    zi += mi;
+                    if (do_field) field[s] = make_float2(mr, mi);
+                }
+            }
+        };
+        const int ax = sd->axes;
+        const float2* __restrict__ et = sd->etab;
+        if (fk == 0.f) {
+            phase2([&](int) { return make_float2(0.f, 0.f); });
+        } else if (et != nullptr && (fk == 1.f || fk == -1.f) && (ax == 1 || ax == 2 || ax == 4)) {
+            // one gradient axis: a single table entry per site
+            const float2* __restrict__ base = et + (ax == 1 ? 0 : ax == 2 ? nx : nx + ny + z);
+            const int cx = ax == 1, cy = ax == 2;
+            const bool neg = fk < 0.f;
+            phase2([&](int j) {
+                float2 v = __ldg(base + xs[j] * cx + ys[j] * cy);
+                if (neg) v.y = -v.y;
+                return v;
+            });
+        } else {
+            phase2([&](int j) { return rotation_m1(sd, fk, xs[j], ys[j], z); });
+        }
 #pragma unroll
         for (int j = 0; j < TMA_SPT; ++j)
 #pragma unroll
@@ -322,19 +366,26 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 
 size_t tma_smem_bytes(int cap, int capx, int nst) { return stage_bytes(cap, capx) * nst; }
 // signal partial slots per unit: one per consumer warp of the variant
-int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2 ? 8 : 16; }
+int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2 ? 8 : variant == 3 ? 11 : 16; }
 
-// variant 0: 16 consumer warps x 2 sites, 1 (default): 12 x 3, 2: 8 x 4
-// (units <= 1024 sites; 17 warps cap registers at 96 and spill, 12 + 1 fit 157)
+// variant 0: 16 consumer warps x 2 sites, 1: 12 x 3, 2: 8 x 4, 3 (default):
+// 11 x 3 (units <= 1024 sites).  The register file is split over the SM's 4
+// sub-partitions: with the producer warp, 9 to 12 warps per CTA allow 168
+// registers a thread, 13 to 16 warps 128 and 17 warps 96; the two-phase
+// consumer needs about 150.
 static void* tma_kernel(int variant)
 {
     switch (variant) {
     case 1: return (void*)sweep_tma_kernel<384, 3>;
     case 2: return (void*)sweep_tma_kernel<256, 4>;
+    case 3: return (void*)sweep_tma_kernel<352, 3>;
     default: return (void*)sweep_tma_kernel<512, 2>;
     }
 }
-static int tma_threads(int variant) { return variant == 1 ? 384 + 32 : variant == 2 ? 256 + 32 : 512 + 32; }
+static int tma_threads(int variant)
+{
+    return variant == 1 ? 384 + 32 : variant == 2 ? 256 + 32 : variant == 3 ? 352 + 32 : 512 + 32;
+}
 
 cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int* ctas_per_sm)
 {
@@ -352,6 +403,7 @@ cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int
     switch (variant) {
     case 1: sweep_tma_kernel<384, 3><<<grid, 384 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
     case 2: sweep_tma_kernel<256, 4><<<grid, 256 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 3: sweep_tma_kernel<352, 3><<<grid, 352 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
     default: sweep_tma_kernel<512, 2><<<grid, 512 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
     }
     return cudaGetLastError();

@@ -331,7 +331,7 @@ def test_bulk_copy_sweep_parity(lb, case):
     D, T2, kap = [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.04
     gG, f = oracle.pgse(1500.0, 1.0, 2.0, dt, d)
     out = {}
-    for kern, tshape in ((1, 0), (2, 0), (2, 1), (2, 2)):
+    for kern, tshape in ((1, 0), (2, 0), (2, 1), (2, 2), (2, 3)):
         s = _solver(lb, geom, bc, D, T2, kap, dt, f, gG)
         s.set_option(lb.OPT_KERNEL, kern)
         s.set_option(lb.OPT_TMA_SHAPE, tshape)
@@ -369,7 +369,7 @@ def test_signal_partials_do_not_leak_between_runs(lb):
     o = _oracle(geom, (0, 0, 0), D, T2, kap, dt, f, gG)
     s = _solver(lb, geom, (0, 0, 0), D, T2, kap, dt, f, gG)
     for kern, shape, block, spt in [(1, 0, 64, 1), (2, 0, 256, 2), (2, 1, 256, 2), (2, 2, 256, 2), (1, 0, 512, 4),
-                                    (2, 1, 128, 1)]:
+                                    (2, 3, 256, 2), (2, 1, 128, 1)]:
         s.set_option(lb.OPT_KERNEL, kern)
         s.set_option(lb.OPT_TMA_SHAPE, shape)
         s.set_option(lb.OPT_BLOCK, block)
