@@ -345,14 +345,14 @@ static void* adj_kernel(int shape)
 {
     return shape == 1 ? (void*)adjoint_tma_kernel<512, 1> : (void*)adjoint_tma_kernel<256, 2>;
 }
+static int adj_threads(int shape) { return shape == 1 ? 544 : 288; }
 
 cudaError_t adj_tma_prepare(int cap, int nst, int shape, int* ctas_per_sm)
 {
     const size_t bytes = adj_stage_bytes(cap) * nst;
     cudaError_t e = cudaFuncSetAttribute(adj_kernel(shape), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, adj_kernel(shape), shape == 1 ? 544 : 288,
-                                                         bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, adj_kernel(shape), adj_threads(shape), bytes);
 }
 
 cudaError_t launch_adjoint_tma(const AdjointArgs& a, long long n_units, int cap, int nst, int shape, int grid,

@@ -304,8 +304,9 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 
         // Phase 2: reaction (Eq. reaction_LBM), BGK collision
         // (Eq. collision_LBM) and the stores, with no branch between sites.
-        // rot(j) gives exp(i theta) - 1 of site j; the three forms below are
-        // chosen once per unit and give the same bits as rotation_m1.
+        // rot(j) gives exp(i theta) - 1 of site j; the forms below are chosen
+        // once per unit and give the values of rotation_m1 (up to the sign of
+        // a zero).
         float zr = 0.f, zi = 0.f;
         auto phase2 = [&](auto rot) {
 #pragma unroll
@@ -340,6 +341,16 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             const bool neg = fk < 0.f;
             phase2([&](int j) {
                 float2 v = __ldg(base + xs[j] * cx + ys[j] * cy);
+                if (neg) v.y = -v.y;
+                return v;
+            });
+        } else if (et != nullptr && (fk == 1.f || fk == -1.f)) {
+            // general direction: x and y entries per site, the z entry once
+            // per unit (a disabled axis has an all-zero table)
+            const float2 ez = __ldg(et + nx + ny + z);
+            const bool neg = fk < 0.f;
+            phase2([&](int j) {
+                float2 v = cadd_prod(cadd_prod(__ldg(et + xs[j]), __ldg(et + nx + ys[j])), ez);
                 if (neg) v.y = -v.y;
                 return v;
             });
