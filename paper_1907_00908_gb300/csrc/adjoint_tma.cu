@@ -174,6 +174,18 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
         const float2* __restrict__ facP = a.ftab + ((size_t)(a.k - 1) * a.n_members + G.m) * 6;
         const float2* __restrict__ facK = a.ftab + ((size_t)a.k * a.n_members + G.m) * 6;
         const float sh = sd->s_share;
+        const float ep0 = sd->eps[0], ep1 = sd->eps[1], ep2 = sd->eps[2], ep3 = sd->eps[3];
+        const float om0 = sd->omega[0], om1 = sd->omega[1], om2 = sd->omega[2], om3 = sd->omega[3];
+        // reaction rotation form of this unit (values as rotation_m1): 0 none
+        // (f = 0), 1 one table entry (G on one axis), 2 x and y entries per
+        // site and the z entry per unit, 3 general
+        const float2* __restrict__ et = sd->etab;
+        const int ax = sd->axes;
+        const bool tab = et != nullptr && (fk == 1.f || fk == -1.f);
+        const int rmode = fk == 0.f ? 0 : !tab ? 3 : (ax == 1 || ax == 2 || ax == 4) ? 1 : 2;
+        const float2* __restrict__ rbase = et + (ax == 1 ? 0 : ax == 2 ? nx : nx + ny + G.z);
+        const int rcx = ax == 1, rcy = ax == 2;
+        const float2 ez = rmode == 2 ? __ldg(et + nx + ny + G.z) : make_float2(0.f, 0.f);
         float2 sL = make_float2(0.f, 0.f);
         if (a.first) {
             const double2 Ld = a.lam_init[G.m];
@@ -243,9 +255,20 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
                 if (mk & 32u) gp[5] = mix(own[5], gp[5], sh);
                 if (mk & 16u) gp[6] = mix(own[6], gp[6], sh);
             }
-            const float ep = sd->eps[ph];
-            const float2 rot = fk != 0.f ? rotation_m1(sd, fk, x, y, z) : make_float2(0.f, 0.f);
-            const float2 q = fk != 0.f ? reaction_q(rot, ep) : make_float2(-ep, 0.f);
+            const float ep = (ph & 2) ? ((ph & 1) ? ep3 : ep2) : ((ph & 1) ? ep1 : ep0);
+            float2 rot;
+            if (rmode == 0) {
+                rot = make_float2(0.f, 0.f);
+            } else if (rmode == 1) {
+                rot = __ldg(rbase + x * rcx + y * rcy);
+                if (fk < 0.f) rot.y = -rot.y;
+            } else if (rmode == 2) {
+                rot = cadd_prod(cadd_prod(__ldg(et + x), __ldg(et + nx + y)), ez);
+                if (fk < 0.f) rot.y = -rot.y;
+            } else {
+                rot = rotation_m1(sd, fk, x, y, z);
+            }
+            const float2 q = reaction_q(rot, ep);
             float2 gg[Q];
 #pragma unroll
             for (int i2 = 0; i2 < Q; ++i2) gg[i2] = gp[i2];
@@ -292,7 +315,7 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
                 lwr += w * lam[i2].x;
                 lwi += w * lam[i2].y;
             }
-            const float om = sd->omega[ph];
+            const float om = (ph & 2) ? ((ph & 1) ? om3 : om2) : ((ph & 1) ? om1 : om0);
             const float er = 1.f + rot.x, ei = rot.y;
             float dEp = 0.f;
 #pragma unroll
