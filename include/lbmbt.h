@@ -94,6 +94,52 @@ int lbmbt_add_geometry(lbmbt_ctx* ctx, int nx, int ny, int nz, double dx_um,
                        const int32_t* labels, int labels_on_device, int n_labels,
                        const uint8_t* phase_of_label, const int bc[3], int* index_out);
 
+/*
+ * Slab of a larger grid (the paper's strip decomposition, Sec. 2.5, cut along
+ * z here): the context's only geometry becomes planes z0 .. z0+nz-1 of a grid
+ * of nz_global planes, so a grid can be split over several contexts (one per
+ * GPU, or several on one GPU) that exchange one plane of one population per
+ * face and time step.  labels_ext: int32 [nz + 2][ny][nx], host or device:
+ * the plane below the slab, the slab's nz planes, the plane above (labels of
+ * the neighbouring slabs, so the face links get their membrane bits; at a
+ * global periodic face the wrapped plane).  lo_kind / hi_kind say what lies
+ * across the low / high z face:
+ *   LBMBT_FACE_OWN        the global face, a mirror (bc[2] = LBMBT_BC_MIRROR);
+ *   LBMBT_FACE_HALO       another slab;
+ *   LBMBT_FACE_HALO_WRAP  another slab across the periodic global face (the
+ *                         halo value takes the wrap factor exp(+-i gamma
+ *                         L_z G_z F_k) of Sec. 2.4.3, L_z = nz_global dx).
+ * A face is OWN or wraps iff the slab touches the global face.  Node
+ * coordinates (reaction phase, mirror and wrap factors) are global.  nx must
+ * be even.  A slab is stepped with lbmbt_prepare and lbmbt_advance(ctx, 1,
+ * ...); between steps the caller moves each member's faces to its
+ * neighbours' halos (lbmbt_slab_faces -> lbmbt_slab_set_halos).  The halos
+ * start at the initial state (M = 1).  lbmbt_run, lbmbt_run_batch and
+ * lbmbt_advance with more than one step return ESTATE / EINVAL on a slab;
+ * the adjoint returns EUNSUPPORTED.  The signal of a slab is its part of Z:
+ * the caller sums Z over the slabs.
+ */
+enum { LBMBT_FACE_OWN = 0, LBMBT_FACE_HALO = 1, LBMBT_FACE_HALO_WRAP = 2 };
+int lbmbt_set_geometry_slab(lbmbt_ctx* ctx, int nx, int ny, int nz, double dx_um,
+                            const int32_t* labels_ext, int labels_on_device, int n_labels,
+                            const uint8_t* phase_of_label, const int bc[3], int z0, int nz_global,
+                            int lo_kind, int hi_kind);
+
+/* Faces of member `member` of a prepared slab run at the current step, before
+ * the next lbmbt_advance: lo_out receives hat g_6 (the population moving to
+ * -z) of the slab's first plane, for the slab below; hi_out hat g_5 (moving
+ * to +z) of its last plane, for the slab above.  Each is nx*ny complex64
+ * values [ny][nx], host or device memory (NULL: skip).  The copies are issued
+ * on the context's stream and the call returns without waiting for them. */
+int lbmbt_slab_faces(lbmbt_ctx* ctx, int member, void* lo_out, void* hi_out);
+
+/* Halo planes of member `member` for the next lbmbt_advance: lo_in = hat g_5
+ * of the plane below the slab (the lower neighbour's hi_out), hi_in = hat g_6
+ * of the plane above (the upper neighbour's lo_out); nx*ny complex64 each,
+ * host or device (NULL: leave unchanged, e.g. at an OWN face).  Issued on the
+ * context's stream; the call returns without waiting. */
+int lbmbt_slab_set_halos(lbmbt_ctx* ctx, int member, const void* lo_in, const void* hi_in);
+
 /* Copy the per-node mask byte of geometry `index` (encoding above) to host
  * memory mask_out[nz*ny*nx]. */
 int lbmbt_get_mask(lbmbt_ctx* ctx, int index, uint8_t* mask_out);
@@ -202,6 +248,12 @@ int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);
  */
 int lbmbt_prepare(lbmbt_ctx* ctx, int n_members, const lbmbt_member* members);
 int lbmbt_advance(lbmbt_ctx* ctx, int64_t n_steps, int want_signal, double* signal_out);
+
+/* Field output of the next lbmbt_prepare: device complex64 [N] receiving
+ * M(x, t_end) of the (single) member when lbmbt_advance performs the last
+ * step of the sequence; NULL (default) for none.  The buffer must stay valid
+ * until that step; lbmbt_prepare with more than one member then fails. */
+int lbmbt_set_field(lbmbt_ctx* ctx, void* field_dev);
 
 /* Number of kernel launches the library issued on ctx since creation. */
 int lbmbt_launch_count(lbmbt_ctx* ctx, int64_t* count_out);

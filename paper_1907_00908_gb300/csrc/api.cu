@@ -31,6 +31,10 @@ struct Geom {
     int max_phase = 0;
     int has_membranes = 0;
     uint8_t* d_mask = nullptr;
+    // slab of a larger grid (z planes z0 .. z0+nz-1 of nzg); face kinds
+    // LBMBT_FACE_OWN / _HALO / _HALO_WRAP of the low and high z face
+    int slab = 0, z0 = 0, nzg = 0;
+    int zkind[2] = {0, 0};
 };
 
 constexpr int GRAPH_CHUNK = 16;
@@ -101,6 +105,9 @@ struct lbmbt_ctx {
     size_t cap_ftab = 0;
     float2* d_etab = nullptr;     // per-member rotation tables
     size_t cap_etab = 0;
+    float2* d_halo = nullptr;     // slab halo planes, [member][2][nx*ny]
+    size_t cap_halo = 0;
+    std::vector<size_t> halo_off; // per member offset into d_halo (elements)
     double2* d_Z = nullptr;
     size_t cap_Z = 0;
     double2* d_series = nullptr;
@@ -114,6 +121,7 @@ struct lbmbt_ctx {
     bool prepared = false;
     bool series_mode = false;
     void* field_dev = nullptr;
+    void* field_req = nullptr;    // lbmbt_set_field: field buffer for the next lbmbt_prepare
     cudaGraphExec_t graph = nullptr;
     int graph_series = -1;
     // adjoint buffers
@@ -142,12 +150,13 @@ static void div_magic(unsigned d, unsigned* m, int* s)
 }
 
 // Per-axis rotation table of one member: (cos(c n) - 1, sin(c n)), c = -gG_a dx dt.
-static void rotation_table(const double gG[3], double dx, double dt, const int dims[3], std::vector<float2>& out)
+static void rotation_table(const double gG[3], double dx, double dt, const int dims[3], int z0,
+                           std::vector<float2>& out)
 {
     for (int a = 0; a < 3; ++a) {
         const double c = -gG[a] * dx * dt;
         for (int n = 0; n < dims[a]; ++n) {
-            const double t = c * n;
+            const double t = c * (n + (a == 2 ? z0 : 0));
             const double h = std::sin(0.5 * t);
             out.push_back(make_float2((float)(-2.0 * h * h), (float)std::sin(t)));
         }
@@ -241,7 +250,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
     cudaFree(c->d_fac); cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab);
-    cudaFree(c->d_adj_unit_start);
+    cudaFree(c->d_adj_unit_start); cudaFree(c->d_halo);
     cudaFree(c->d_ck); cudaFree(c->d_seg); cudaFree(c->d_gacc); cudaFree(c->d_gout); cudaFree(c->d_laminit);
     if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
     delete c;
@@ -339,6 +348,92 @@ extern "C" int lbmbt_add_geometry(lbmbt_ctx* c, int nx, int ny, int nz, double d
     invalidate_run(c);
     c->geoms.push_back(g);
     if (index_out) *index_out = (int)c->geoms.size() - 1;
+    return LBMBT_OK;
+}
+
+// Slab of a grid cut along z (the strips of Sec. 2.5): labels_ext holds
+// nz + 2 planes, the plane below the slab, the slab's nz planes, the plane
+// above.  The mask is built over the extended block (z wrapped, which only
+// the ghost planes see) and its nz interior planes are kept, so the links of
+// the face planes compare with the neighbouring slab's labels.  A face of
+// kind OWN is the global mirror face: its ghost plane is replaced by a copy
+// of the face plane first, so the face links carry no membrane bit.
+extern "C" int lbmbt_set_geometry_slab(lbmbt_ctx* c, int nx, int ny, int nz, double dx, const int32_t* labels_ext,
+                                       int on_dev, int n_labels, const uint8_t* pol, const int bc[3], int z0,
+                                       int nz_global, int lo_kind, int hi_kind)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!labels_ext || !bc) return fail(c, LBMBT_EINVAL, "labels/bc missing");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(c, LBMBT_EINVAL, "grid sizes must be >= 1");
+    if (z0 < 0 || nz_global < 1 || z0 + nz > nz_global)
+        return fail(c, LBMBT_EINVAL, "slab planes [%d, %d) outside the grid of %d planes", z0, z0 + nz, nz_global);
+    const int kinds[2] = {lo_kind, hi_kind};
+    for (int h = 0; h < 2; ++h) {
+        const int k = kinds[h];
+        if (k != LBMBT_FACE_OWN && k != LBMBT_FACE_HALO && k != LBMBT_FACE_HALO_WRAP)
+            return fail(c, LBMBT_EINVAL, "face kind %d invalid", k);
+        if (k == LBMBT_FACE_OWN && bc[2] != LBMBT_BC_MIRROR)
+            return fail(c, LBMBT_EINVAL, "a slab face of its own must be a global mirror face (a periodic whole "
+                                         "grid is a plain geometry)");
+        if (k == LBMBT_FACE_HALO_WRAP && bc[2] != LBMBT_BC_PERIODIC)
+            return fail(c, LBMBT_EINVAL, "a wrapping halo face needs a periodic z axis");
+    }
+    if (bc[2] == LBMBT_BC_MIRROR &&
+        ((lo_kind == LBMBT_FACE_OWN) != (z0 == 0) || (hi_kind == LBMBT_FACE_OWN) != (z0 + nz == nz_global)))
+        return fail(c, LBMBT_EINVAL, "a face is the global mirror face iff the slab touches it");
+    if ((lo_kind == LBMBT_FACE_HALO_WRAP) != (z0 == 0 && bc[2] == LBMBT_BC_PERIODIC) ||
+        (hi_kind == LBMBT_FACE_HALO_WRAP) != (z0 + nz == nz_global && bc[2] == LBMBT_BC_PERIODIC))
+        return fail(c, LBMBT_EINVAL, "the faces on the periodic global face must wrap, the others must not");
+    if (nx % 2) return fail(c, LBMBT_EINVAL, "a slab needs an even nx");
+    const long long sxy = (long long)nx * ny;
+    const long long Next = sxy * (nz + 2);
+    if (Next > (1LL << 28)) return fail(c, LBMBT_EINVAL, "slab of %lld sites (with ghost planes) exceeds 2^28", Next);
+    int rc = set_device(c);
+    if (rc) return rc;
+    int32_t* d_lab = nullptr;
+    if (cudaMalloc(&d_lab, Next * sizeof(int32_t)) != cudaSuccess) return fail(c, LBMBT_ENOMEM, "label buffer");
+    auto kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(d_lab, labels_ext, Next * sizeof(int32_t), kind, c->stream);
+    if (e == cudaSuccess && lo_kind == LBMBT_FACE_OWN)
+        e = cudaMemcpyAsync(d_lab, d_lab + sxy, sxy * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && hi_kind == LBMBT_FACE_OWN)
+        e = cudaMemcpyAsync(d_lab + (nz + 1) * sxy, d_lab + nz * sxy, sxy * sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(d_lab);
+        return fail(c, LBMBT_ECUDA, "label upload: %s", cudaGetErrorString(e));
+    }
+    const int bce[3] = {bc[0], bc[1], LBMBT_BC_PERIODIC};
+    Geom ext;
+    rc = make_geom(c, nx, ny, nz + 2, dx, d_lab, 1, n_labels, pol, bce, &ext);
+    cudaFree(d_lab);
+    if (rc) return rc;
+    uint8_t* d_mask = nullptr;
+    if (cudaMalloc(&d_mask, sxy * nz) != cudaSuccess) {
+        cudaFree(ext.d_mask);
+        return fail(c, LBMBT_ENOMEM, "mask buffer");
+    }
+    e = cudaMemcpyAsync(d_mask, ext.d_mask + sxy, sxy * nz, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(ext.d_mask);
+    if (e != cudaSuccess) {
+        cudaFree(d_mask);
+        return fail(c, LBMBT_ECUDA, "mask copy: %s", cudaGetErrorString(e));
+    }
+    Geom g = ext;
+    g.nz = nz;
+    g.N = sxy * nz;
+    for (int a = 0; a < 3; ++a) g.bc[a] = bc[a];
+    g.d_mask = d_mask;
+    g.slab = 1;
+    g.z0 = z0;
+    g.nzg = nz_global;
+    g.zkind[0] = lo_kind;
+    g.zkind[1] = hi_kind;
+    invalidate_run(c);
+    for (auto& o : c->geoms) cudaFree(o.d_mask);
+    c->geoms.clear();
+    c->geoms.push_back(g);
     return LBMBT_OK;
 }
 
@@ -677,6 +772,8 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         d.N = g.N;
         d.plane = (g.N + 63) / 64 * 64;
         d.nx = g.nx; d.ny = g.ny; d.nz = g.nz;
+        d.z0 = g.slab ? g.z0 : 0;
+        d.nzg = g.slab ? g.nzg : g.nz;
         d.dx = g.dx;
         for (int a = 0; a < 3; ++a) {
             d.gG[a] = mm.gamma_G0[a];
@@ -692,6 +789,10 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
                 d.bc[a] = BC_MIR_CONJ;
             }
         }
+        for (int h = 0; h < 2; ++h)
+            d.zbc[h] = (!g.slab || g.zkind[h] == LBMBT_FACE_OWN) ? d.bc[2]
+                       : g.zkind[h] == LBMBT_FACE_HALO          ? BC_HALO
+                                                                : BC_HALO_PER;
         for (int p = 0; p < 4; ++p) {
             const double tau = 0.5 + c->dt * c->D[p] / (EPS_D * g.dx * g.dx);   // Eq. tau_def
             if (p < c->n_phases && !(tau > 0.5))
@@ -727,6 +828,25 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         off += (size_t)c->n_slots * 7 * d.plane * sizeof(float2);
     }
     if (field_dev) c->descs[0].field = (float2*)field_dev;
+    {   // slab halo planes: two of nx*ny complex values per slab member
+        c->halo_off.assign(n_members, 0);
+        size_t hn = 0;
+        for (int m = 0; m < n_members; ++m)
+            if (c->geoms[mem[m].geometry].slab) {
+                c->halo_off[m] = hn;
+                hn += 2 * (size_t)c->descs[m].nx * c->descs[m].ny;   // nx even: planes stay 16-byte aligned
+            }
+        if (hn) {
+            rc = grow(c, &c->d_halo, &c->cap_halo, hn * sizeof(float2));
+            if (rc) return rc;
+            for (int m = 0; m < n_members; ++m)
+                if (c->geoms[mem[m].geometry].slab) {
+                    const size_t sxy = (size_t)c->descs[m].nx * c->descs[m].ny;
+                    c->descs[m].halo[0] = c->d_halo + c->halo_off[m];
+                    c->descs[m].halo[1] = c->d_halo + c->halo_off[m] + sxy;
+                }
+        }
+    }
     {   // rotation tables
         std::vector<float2> et;
         std::vector<size_t> off(n_members);
@@ -734,7 +854,7 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
             off[m] = et.size();
             const MemberDesc& d = c->descs[m];
             const int dims[3] = {d.nx, d.ny, d.nz};
-            rotation_table(d.gG, d.dx, c->dt, dims, et);
+            rotation_table(d.gG, d.dx, c->dt, dims, d.z0, et);
             if (et.size() & 1) et.push_back(make_float2(0.f, 0.f));  // 16-byte aligned tables
         }
         rc = grow(c, &c->d_etab, &c->cap_etab, et.size() * sizeof(float2));
@@ -781,6 +901,13 @@ static int capture_graph(lbmbt_ctx* c)
     return LBMBT_OK;
 }
 
+static bool any_slab(const lbmbt_ctx* c)
+{
+    for (auto& g : c->geoms)
+        if (g.slab) return true;
+    return false;
+}
+
 // Advance n steps; the signal (and field) of the last step is produced when asked.
 static int advance(lbmbt_ctx* c, long long n, bool want_signal)
 {
@@ -789,6 +916,8 @@ static int advance(lbmbt_ctx* c, long long n, bool want_signal)
         return fail(c, LBMBT_EINVAL, "advance past the end of the sequence (%lld + %lld > %lld)", c->k_cur, n,
                     c->n_steps);
     if (n == 0) return LBMBT_OK;
+    if (n > 1 && any_slab(c))
+        return fail(c, LBMBT_EINVAL, "a slab advances one step at a time, with a halo exchange between steps");
     const long long last = c->k_cur + n - 1;
     int rc = write_ctl(c, want_signal ? (int)last : -1, (c->field_dev && last == c->n_steps - 1) ? (int)last : -1);
     if (rc) return rc;
@@ -869,6 +998,7 @@ extern "C" int lbmbt_run(lbmbt_ctx* c, double* signal_out, void* field_out_dev, 
 {
     if (!c) return LBMBT_EINVAL;
     if (!signal_out) return fail(c, LBMBT_EINVAL, "signal_out is NULL");
+    if (any_slab(c)) return fail(c, LBMBT_ESTATE, "a slab runs with lbmbt_prepare and lbmbt_advance(1) per step");
     lbmbt_member m = plain_member(c);
     int rc = prepare(c, 1, &m, series_out != nullptr, field_out_dev);
     if (!rc) rc = advance(c, c->n_steps, true);
@@ -881,6 +1011,7 @@ extern "C" int lbmbt_run_batch(lbmbt_ctx* c, int n_members, const lbmbt_member* 
 {
     if (!c) return LBMBT_EINVAL;
     if (!members || !signal_out) return fail(c, LBMBT_EINVAL, "members / signal_out is NULL");
+    if (any_slab(c)) return fail(c, LBMBT_ESTATE, "a slab runs with lbmbt_prepare and lbmbt_advance(1) per step");
     int rc = prepare(c, n_members, members, series_out != nullptr, nullptr);
     if (!rc) rc = advance(c, c->n_steps, true);
     if (!rc) rc = fetch_signal(c, signal_out, series_out);
@@ -892,12 +1023,19 @@ extern "C" int lbmbt_prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* me
     if (!c) return LBMBT_EINVAL;
     if (n_members == 0) {
         lbmbt_member m = plain_member(c);
-        int rc = prepare(c, 1, &m, false, nullptr);
+        int rc = prepare(c, 1, &m, false, c->field_req);
         return rc ? rc : sync(c);
     }
     if (!members) return fail(c, LBMBT_EINVAL, "members is NULL");
-    int rc = prepare(c, n_members, members, false, nullptr);
+    int rc = prepare(c, n_members, members, false, c->field_req);
     return rc ? rc : sync(c);
+}
+
+extern "C" int lbmbt_set_field(lbmbt_ctx* c, void* field_dev)
+{
+    if (!c) return LBMBT_EINVAL;
+    c->field_req = field_dev;
+    return LBMBT_OK;
 }
 
 extern "C" int lbmbt_advance(lbmbt_ctx* c, int64_t n_steps, int want_signal, double* signal_out)
@@ -907,6 +1045,46 @@ extern "C" int lbmbt_advance(lbmbt_ctx* c, int64_t n_steps, int want_signal, dou
     if (rc) return rc;
     if (want_signal && signal_out) return fetch_signal(c, signal_out, nullptr);
     return check_device_error(c);
+}
+
+// Slab faces of member m at the current step (before the next sweep): the
+// population leaving through each z face, hat g_6 of plane 0 (for the slab
+// below) and hat g_5 of plane nz-1 (for the slab above).
+extern "C" int lbmbt_slab_faces(lbmbt_ctx* c, int member, void* lo_out, void* hi_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!c->prepared) return fail(c, LBMBT_ESTATE, "no prepared run");
+    if (member < 0 || member >= c->n_members) return fail(c, LBMBT_EINVAL, "member %d out of range", member);
+    const MemberDesc& d = c->descs[member];
+    if (!d.halo[0]) return fail(c, LBMBT_ESTATE, "member %d is not on a slab", member);
+    int rc = set_device(c);
+    if (rc) return rc;
+    const size_t sxy = (size_t)d.nx * d.ny, P = (size_t)d.plane;
+    const float2* lvl = d.state + (size_t)(c->k_cur % 2) * 7 * P;
+    if (lo_out) CU(c, cudaMemcpyAsync(lo_out, lvl + 6 * P, sxy * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (hi_out)
+        CU(c, cudaMemcpyAsync(hi_out, lvl + 5 * P + (size_t)(d.nz - 1) * sxy, sxy * sizeof(float2), cudaMemcpyDefault,
+                              c->stream));
+    return LBMBT_OK;
+}
+
+// Halo planes of member m for the next sweep: lo_in = hat g_5 of the plane
+// below the slab, hi_in = hat g_6 of the plane above (the neighbours' faces).
+extern "C" int lbmbt_slab_set_halos(lbmbt_ctx* c, int member, const void* lo_in, const void* hi_in)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!c->prepared) return fail(c, LBMBT_ESTATE, "no prepared run");
+    if (member < 0 || member >= c->n_members) return fail(c, LBMBT_EINVAL, "member %d out of range", member);
+    const MemberDesc& d = c->descs[member];
+    if (!d.halo[0]) return fail(c, LBMBT_ESTATE, "member %d is not on a slab", member);
+    int rc = set_device(c);
+    if (rc) return rc;
+    const size_t sxy = (size_t)d.nx * d.ny;
+    if (lo_in)
+        CU(c, cudaMemcpyAsync(const_cast<float2*>(d.halo[0]), lo_in, sxy * sizeof(float2), cudaMemcpyDefault, c->stream));
+    if (hi_in)
+        CU(c, cudaMemcpyAsync(const_cast<float2*>(d.halo[1]), hi_in, sxy * sizeof(float2), cudaMemcpyDefault, c->stream));
+    return LBMBT_OK;
 }
 
 extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
@@ -1152,6 +1330,7 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
         return fail(c, LBMBT_EINVAL, "NULL argument");
     if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
     if (c->geoms.empty() || c->n_phases == 0 || c->n_steps == 0) return fail(c, LBMBT_ESTATE, "set-up incomplete");
+    if (any_slab(c)) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not run on slabs");
     const int ck = checkpoint_every > 0 ? checkpoint_every : 64;
     int rc = set_device(c);
     if (rc) return rc;

@@ -23,7 +23,11 @@ constexpr double EPS_D = 0.25;
 enum BcMode : int {
     BC_PER = 0,       // modified periodic (Sec. 2.4.3): wrap with exp(+-i phi)
     BC_MIR = 1,       // mirror, G parallel to the face: hat g_i(x_m) = hat g_ibar(x_n)
-    BC_MIR_CONJ = 2   // mirror, G normal to the face: conjugate + rewind (Sec. 2.4.4)
+    BC_MIR_CONJ = 2,  // mirror, G normal to the face: conjugate + rewind (Sec. 2.4.4)
+    // z faces of a slab cut out of a larger grid (the strips of Sec. 2.5):
+    BC_HALO = 3,      // the neighbouring slab: value from the halo plane
+    BC_HALO_PER = 4   // the neighbouring slab across the periodic global face:
+                      // halo value times the wrap factor exp(+-i phi)
 };
 
 struct MemberDesc {
@@ -52,8 +56,15 @@ struct MemberDesc {
     unsigned div_m[2];
     int div_s[2];
     // per-axis rotation tables (FP64-built): etab[off_a + n] =
-    // (cos(ctheta_a n) - 1, sin(ctheta_a n)), offsets 0, nx, nx+ny; or nullptr
+    // (cos(ctheta_a n_a) - 1, sin(ctheta_a n_a)), offsets 0, nx, nx+ny, with
+    // n_z = z0 + n (global plane index); or nullptr
     const float2* etab;
+    // z extent within the whole grid: the member covers planes z0 .. z0+nz-1
+    // of nzg (z0 = 0, nzg = nz unless the geometry is a slab)
+    int z0, nzg;
+    int zbc[2];           // BcMode of the low and high z face (bc[2] unless a slab)
+    const float2* halo[2];  // slab halo planes (nx*ny complex64): hat g_5 of the
+                          // plane below, hat g_6 of the plane above; or nullptr
 };
 
 // Step control word in device memory.  The sweep reads k here; a one-block

@@ -166,6 +166,8 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     d.axes = 0;
     for (int a = 0; a < 3; ++a)
         if (d.ctheta[a] != 0.f) d.axes |= 1 << a;
+    d.nzg = nz;        // the whole grid (z0 = 0, no halo planes)
+    d.zbc[0] = d.zbc[1] = d.bc[2];
     d.etab = nullptr;  // no tables here: the reaction angle uses sincosf
     d.memb = 1;        // the mask is the caller's: assume membranes may be present
     const unsigned dv[2] = {(unsigned)nx, (unsigned)ny};

@@ -80,6 +80,10 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
             out[s] = make_float2(W0, 0.f);
 #pragma unroll
             for (int i = 1; i < Q; ++i) out[(size_t)i * P + s] = make_float2(WI, 0.f);
+            // slab halo planes start at the neighbours' initial values
+            if (s < (unsigned)(d.nx * d.ny))
+                for (int h = 0; h < 2; ++h)
+                    if (d.halo[h]) const_cast<float2*>(d.halo[h])[s] = make_float2(WI, 0.f);
         }
     }
 }
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
     float2* __restrict__ dst = sd->state + (size_t)((k + 1 - sbase) % smod) * 7 * P;
     const uint8_t* __restrict__ mask = sd->mask;
     const int nx = sd->nx, ny = sd->ny, nz = sd->nz;
-    const int bcx = sd->bc[0], bcy = sd->bc[1], bcz = sd->bc[2];
+    const int bcx = sd->bc[0], bcy = sd->bc[1], bcz0 = sd->zbc[0], bcz1 = sd->zbc[1];
     const unsigned sxy = (unsigned)nx * ny;
     const unsigned N = (unsigned)sd->N;
     const unsigned base = (unsigned)(blockIdx.x - sd->tile0) * blockDim.x * SPT;
@@ -127,8 +131,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
         g[2] = pull<0, -1>(src, P, s, x, nx, 1u, bcx, fac);
         g[3] = pull<1, +1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
         g[4] = pull<1, -1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
-        g[5] = pull<2, +1>(src, P, s, z, nz, sxy, bcz, fac);
-        g[6] = pull<2, -1>(src, P, s, z, nz, sxy, bcz, fac);
+        g[5] = pull<2, +1>(src, P, s, z, nz, sxy, bcz0, fac, &sd->halo[0]);
+        g[6] = pull<2, -1>(src, P, s, z, nz, sxy, bcz1, fac, &sd->halo[1]);
 
         // Half-link membrane (Eq. B5): on a membrane link the arriving
         // population is r * (own population sent towards the membrane) +

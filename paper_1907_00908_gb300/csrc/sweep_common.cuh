@@ -30,23 +30,32 @@ __device__ __forceinline__ int find_member(const long long* __restrict__ ts, int
 //     conj(hat g_ibar(x_n) exp(i psi)) with psi = gamma G_a (x_n + x_m) F_k
 //     (origin x_o = 0), i.e. conj(hat g_ibar) * exp(-i psi): psi = -dx at the
 //     low face, (2N-1) dx at the high face.
+// For z, N is the whole grid's nzg and each face has its own mode (a slab
+// face towards another slab takes the periodic factor only across the
+// global face, BC_HALO_PER).
 // fac[a][0] is the low-face factor, fac[a][1] the high-face factor.
 __device__ __forceinline__ void boundary_factors(const MemberDesc& sd, double F, float2 fac[3][2])
 {
-    const int dims[3] = {sd.nx, sd.ny, sd.nz};
+    const int dims[3] = {sd.nx, sd.ny, sd.nzg};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         float2 lo = make_float2(1.f, 0.f), hi = lo;
         const double g = sd.gG[ax] * sd.dx * F;
         if (g != 0.0) {
+            const int bl = ax == 2 ? sd.zbc[0] : sd.bc[ax];
+            const int bh = ax == 2 ? sd.zbc[1] : sd.bc[ax];
             double sn, cs;
-            if (sd.bc[ax] == BC_PER) {
+            if (bl == BC_PER || bl == BC_HALO_PER) {
                 sincos(g * dims[ax], &sn, &cs);
                 lo = make_float2((float)cs, (float)sn);
-                hi = make_float2((float)cs, (float)-sn);
-            } else if (sd.bc[ax] == BC_MIR_CONJ) {
+            } else if (bl == BC_MIR_CONJ) {
                 sincos(g, &sn, &cs);
                 lo = make_float2((float)cs, (float)sn);
+            }
+            if (bh == BC_PER || bh == BC_HALO_PER) {
+                sincos(g * dims[ax], &sn, &cs);
+                hi = make_float2((float)cs, (float)-sn);
+            } else if (bh == BC_MIR_CONJ) {
                 sincos(g * (2.0 * dims[ax] - 1.0), &sn, &cs);
                 hi = make_float2((float)cs, (float)-sn);
             }
@@ -64,21 +73,29 @@ __device__ __forceinline__ void boundary_factors(const MemberDesc& sd, double F,
 //   periodic : value from the wrapped node times exp(+-i gamma L G F_k)
 //   mirror   : hat g_ibar of the node itself (G parallel to the face), or its
 //              conjugate times exp(-i psi) (G normal to the face)
+//   slab face: the halo plane's value at (x, y) (times the wrap factor
+//              across the periodic global face)
 template <int AX, int SIGN>
 __device__ __forceinline__ float2 pull(const float2* __restrict__ src, unsigned P, unsigned s, int coord,
-                                       int dim, unsigned stride, int bc, const float2* __restrict__ fac)
+                                       int dim, unsigned stride, int bc, const float2* __restrict__ fac,
+                                       const float2* const* halo = nullptr)
 {
     constexpr int I = 1 + 2 * AX + (SIGN > 0 ? 0 : 1);
     constexpr int IB = (SIGN > 0) ? I + 1 : I - 1;
     const bool cr = (SIGN > 0) ? (coord == 0) : (coord == dim - 1);
     unsigned nb = (SIGN > 0) ? s - stride : s + stride;
     int pl = I;
-    if (cr) {
-        if (bc == BC_PER) nb = (SIGN > 0) ? s + (unsigned)(dim - 1) * stride : s - (unsigned)(dim - 1) * stride;
-        else { nb = s; pl = IB; }
+    float2 v;
+    if (cr && (bc == BC_HALO || bc == BC_HALO_PER)) {
+        v = __ldg(*halo + ((SIGN > 0) ? s : s - (unsigned)(dim - 1) * stride));   // pointer read only here
+    } else {
+        if (cr) {
+            if (bc == BC_PER) nb = (SIGN > 0) ? s + (unsigned)(dim - 1) * stride : s - (unsigned)(dim - 1) * stride;
+            else { nb = s; pl = IB; }
+        }
+        v = __ldg(src + (size_t)pl * P + nb);
     }
-    float2 v = __ldg(src + (size_t)pl * P + nb);
-    if (cr && bc != BC_MIR) {
+    if (cr && bc != BC_MIR && bc != BC_HALO) {
         if (bc == BC_MIR_CONJ) v.y = -v.y;
         v = cmul(v, __ldg(fac + 2 * AX + (SIGN > 0 ? 0 : 1)));
     }
@@ -129,7 +146,7 @@ __device__ __forceinline__ float2 rotation_m1(const MemberDesc* __restrict__ d, 
         if (fk < 0.f) q.y = -q.y;
         return q;
     }
-    const float th = __fmul_rn(fk, __fmaf_rn(d->ctheta[2], (float)z,
+    const float th = __fmul_rn(fk, __fmaf_rn(d->ctheta[2], (float)(z + d->z0),
                                               __fmaf_rn(d->ctheta[1], (float)y, __fmul_rn(d->ctheta[0], (float)x))));
     float sh2, ch2;
     sincosf(0.5f * th, &sh2, &ch2);

@@ -102,14 +102,17 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
             bulk_g2s(dst + (rows - 1) * nx, face, rowb, bar);
         }
     }
-    // +z, -z
+    // +z, -z (a slab face towards another slab: the halo plane's rows)
     {
         const float2* srcz;
+        const int b0 = d.zbc[0], b1 = d.zbc[1];
         if (z >= 1) srcz = pl(5) + s0 - sxy;
-        else srcz = d.bc[2] == BC_PER ? pl(5) + s0 + (long long)(d.nz - 1) * sxy : pl(6) + s0;
+        else if (b0 == BC_HALO || b0 == BC_HALO_PER) srcz = d.halo[0] + (long long)y0 * nx;
+        else srcz = b0 == BC_PER ? pl(5) + s0 + (long long)(d.nz - 1) * sxy : pl(6) + s0;
         bulk_g2s(stage_plane(stage, cap, 5), srcz, Lb, bar);
         if (z <= d.nz - 2) srcz = pl(6) + s0 + sxy;
-        else srcz = d.bc[2] == BC_PER ? pl(6) + (long long)y0 * nx : pl(5) + s0;
+        else if (b1 == BC_HALO || b1 == BC_HALO_PER) srcz = d.halo[1] + (long long)y0 * nx;
+        else srcz = b1 == BC_PER ? pl(6) + (long long)y0 * nx : pl(5) + s0;
         bulk_g2s(stage_plane(stage, cap, 6), srcz, Lb, bar);
     }
     bulk_g2s(stage_mask(stage, cap, capx), d.mask + s0, (uint32_t)L, bar);
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     bool ok = prefetch(0, own);
 
     // constants of the current member, reloaded only when the member changes
-    int cm = -1, nx = 1, ny = 1, nz = 1, bcx = 0, bcy = 0, bcz = 0;
+    int cm = -1, nx = 1, ny = 1, nz = 1, bcx = 0, bcy = 0, bcz0 = 0, bcz1 = 0;
     unsigned P = 0, dm0 = 0;
     int ds0 = 0;
     float sh = 0.f, om0 = 0.f, om1 = 0.f, om2 = 0.f, om3 = 0.f, ep0 = 0.f, ep1 = 0.f, ep2 = 0.f, ep3 = 0.f;
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             cm = G.m;
             sd = a.members + cm;
             nx = sd->nx; ny = sd->ny; nz = sd->nz;
-            bcx = sd->bc[0]; bcy = sd->bc[1]; bcz = sd->bc[2];
+            bcx = sd->bc[0]; bcy = sd->bc[1]; bcz0 = sd->zbc[0]; bcz1 = sd->zbc[1];
             P = (unsigned)sd->plane;
             dm0 = sd->div_m[0]; ds0 = sd->div_s[0];
             sh = sd->s_share;
@@ -280,9 +283,9 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             g[j][4] = r4[l];
             if (y == ny - 1) g[j][4] = face_fix(g[j][4], bcy, __ldg(fac + 3));
             g[j][5] = r5[l];
-            if (z == 0) g[j][5] = face_fix(g[j][5], bcz, __ldg(fac + 4));
+            if (z == 0) g[j][5] = face_fix(g[j][5], bcz0, __ldg(fac + 4));
             g[j][6] = r6[l];
-            if (z == nz - 1) g[j][6] = face_fix(g[j][6], bcz, __ldg(fac + 5));
+            if (z == nz - 1) g[j][6] = face_fix(g[j][6], bcz1, __ldg(fac + 5));
 
             // Half-link membrane (Eq. B5): A + s (B - A) with A = own
             // population sent towards the membrane.

@@ -100,9 +100,10 @@ __device__ __forceinline__ UnitGeo unit_geo(const MemberDesc* __restrict__ membe
     return G;
 }
 
+// Boundary transform of a value pulled across a face (see pull()).
 __device__ __forceinline__ float2 face_fix(float2 v, int bc, float2 f)
 {
-    if (bc == BC_MIR) return v;
+    if (bc == BC_MIR || bc == BC_HALO) return v;
     if (bc == BC_MIR_CONJ) v.y = -v.y;
     return cmul(v, f);
 }

@@ -22,6 +22,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSTABLE", -5:
           -6: "EDEVICE", -7: "ESTATE"}
 BC_PERIODIC = 0
 BC_MIRROR = 1
+FACE_OWN, FACE_HALO, FACE_HALO_WRAP = 0, 1, 2
 OPT_GRAPH, OPT_AUTOTUNE, OPT_BLOCK, OPT_SPT, OPT_KERNEL, OPT_KERNEL_USED, OPT_STAGES, OPT_TMA_SHAPE = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_ADJOINT_KERNEL, OPT_ADJOINT_SHAPE = 9, 10
 
@@ -31,7 +32,8 @@ EXPORTS = [
     "lbmbt_add_geometry", "lbmbt_get_mask", "lbmbt_set_phases", "lbmbt_set_permeability",
     "lbmbt_set_sequence", "lbmbt_pgse", "lbmbt_run", "lbmbt_run_batch", "lbmbt_grad",
     "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
-    "lbmbt_launch_count", "lbmbt_sweep_noalloc",
+    "lbmbt_launch_count", "lbmbt_sweep_noalloc", "lbmbt_set_geometry_slab", "lbmbt_slab_faces",
+    "lbmbt_slab_set_halos", "lbmbt_set_field",
 ]
 
 
@@ -78,6 +80,10 @@ def lib():
                 "lbmbt_prepare": [P, I, P],
                 "lbmbt_advance": [P, I64, I, P],
                 "lbmbt_launch_count": [P, ctypes.POINTER(I64)],
+                "lbmbt_set_geometry_slab": [P, I, I, I, D, P, I, I, P, P, I, I, I, I],
+                "lbmbt_slab_faces": [P, I, P, P],
+                "lbmbt_slab_set_halos": [P, I, P, P],
+                "lbmbt_set_field": [P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -211,6 +217,30 @@ class Solver:
         self.shape = (nz, ny, nx)
         return 0
 
+    def set_geometry_slab(self, labels_ext, phase_of_label, dx, bc, z0, nz_global, lo_kind, hi_kind):
+        """``lbmbt_set_geometry_slab``: labels_ext int32 [nz + 2, ny, nx] (ghost
+        plane below, the slab's planes, ghost plane above), numpy or torch CUDA."""
+        on_dev = hasattr(labels_ext, "is_cuda") and labels_ext.is_cuda
+        if not on_dev:
+            labels_ext = np.ascontiguousarray(labels_ext, np.int32)
+        nz2, ny, nx = labels_ext.shape
+        pol = np.ascontiguousarray(phase_of_label, np.uint8)
+        bcv = np.ascontiguousarray(bc, np.int32)
+        self._chk(self.L.lbmbt_set_geometry_slab(self.h, nx, ny, nz2 - 2, float(dx), _p(labels_ext), int(on_dev),
+                                                 int(pol.size), _p(pol), _p(bcv), int(z0), int(nz_global),
+                                                 int(lo_kind), int(hi_kind)), "set_geometry_slab")
+        self.n_sites = [nx * ny * (nz2 - 2)]
+        self.shape = (nz2 - 2, ny, nx)
+        return 0
+
+    def slab_faces(self, member, lo_out, hi_out):
+        """Copy the faces leaving the slab (complex64 [ny, nx] tensors or None)."""
+        self._chk(self.L.lbmbt_slab_faces(self.h, int(member), _p(lo_out), _p(hi_out)), "slab_faces")
+
+    def slab_set_halos(self, member, lo_in, hi_in):
+        """Set the halo planes read by the next step (complex64 [ny, nx] or None)."""
+        self._chk(self.L.lbmbt_slab_set_halos(self.h, int(member), _p(lo_in), _p(hi_in)), "slab_set_halos")
+
     def add_geometry(self, labels, phase_of_label, dx, bc=(0, 0, 0)):
         return self.set_geometry(labels, phase_of_label, dx, bc, add=True)
 
@@ -301,6 +331,11 @@ class Solver:
                 "dD": dD.reshape(n, -1), "dT2": dT2.reshape(n, -1), "dkappa": dk}
 
     # --- timing hooks -------------------------------------------------------
+    def set_field(self, field):
+        """Field buffer (torch complex64 CUDA [N] or None) for the next prepare()."""
+        self._field_keep = field
+        self._chk(self.L.lbmbt_set_field(self.h, _p(field)), "set_field")
+
     def prepare(self, members=None):
         if members is None:
             self._chk(self.L.lbmbt_prepare(self.h, 0, None), "prepare")
