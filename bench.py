@@ -331,6 +331,68 @@ def run_adjoint(args):
     return 0
 
 
+# ---------------------------------------------------------------- slabs (strips)
+def run_slab(args):
+    """The 512^3 tissue batch cut into z slabs on one GPU (one context per
+    slab, faces exchanged before every step), against the same grid in one
+    piece, both timed with CUDA events over the same steps."""
+    import torch
+    from paper_1907_00908_gb300 import lbmbt, slab
+    torch.cuda.set_device(0)
+    geom = geometry(args.n)
+    seqs = sequences()
+    nm = len(seqs)
+    members = lbmbt.Solver.members([g for g, _ in seqs], 0, KAPPA)
+    stream = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(stream):
+        # whole grid, stepped one launch at a time like the slabs
+        s = lbmbt.Solver(0, stream)
+        s.set_geometry(geom.labels, geom.phase_of_label, DX, (1, 1, 1))
+        s.set_phases(D, T2)
+        s.set_sequence(DT, seqs[0][1], seqs[0][0])
+        s.prepare(members)
+        for _ in range(args.warmup):
+            s.advance(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.steps):
+            sig_whole = s.advance(1, want_signal=(k == args.steps - 1), n_members=nm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["whole"] = e0.elapsed_time(e1) / args.steps
+        s.close()
+        g = slab.SlabGroup(geom.labels, geom.phase_of_label, DX, (1, 1, 1), args.slabs, D, T2, DT, seqs[0][1],
+                           members, stream)
+        for _ in range(args.warmup):
+            g.step()
+        with Clocks(0) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for k in range(args.steps):
+                Z = g.step(want_signal=(k == args.steps - 1))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out["slabs"] = e0.elapsed_time(e1) / args.steps
+        g.close()
+    Zw = sig_whole[:, 0] + 1j * sig_whole[:, 1]
+    v = geom.n_sites * nm / (out["slabs"] * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["slabs"], "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"tissue512_voronoi_mirror_3dir_{args.slabs}slabs", "grid": [args.n] * 3,
+                       "slabs": slab.split(args.n, args.slabs), "exchange": "one plane of one population per "
+                       "face, member and step, device copies on one stream"},
+            "whole_grid_one_step_per_call": {"value": geom.n_sites * nm / (out["whole"] * 1e-3) / 1e6,
+                                             "unit": "MLUPS", "ms_per_step": out["whole"]},
+            "slab_over_whole_time": out["slabs"] / out["whole"],
+            "signal_rel_diff_vs_whole": float(np.max(np.abs(Z - Zw) / np.abs(Zw))),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,9 +407,11 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
-    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint"],
+    ap.add_argument("--slabs", type=int, default=4, help="slab workload: number of z slabs")
+    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint", "slab"],
                     help="tissue512 (default): the 512^3 tissue batch of 3 directions; batch: 528 members on "
-                         "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack")
+                         "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack; slab: the "
+                         "tissue batch cut into --slabs z slabs with a face exchange per step")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -355,6 +419,8 @@ def main():
         return run_batch(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "slab":
+        return run_slab(args)
 
     import torch
     import torch.distributed as dist
