@@ -60,6 +60,14 @@ def _load():
                 ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int,
                 P, P, P, P]
             lib.lbm_oracle_run.restype = ctypes.c_int
+            lib.lbm_oracle_run_links.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                P, ctypes.c_int, P, P, ctypes.c_int, P, P,
+                ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P,
+                P, P, P, P]
+            lib.lbm_oracle_run_links.restype = ctypes.c_int
+            lib.lbm_oracle_link_coefficients.argtypes = [ctypes.c_double] * 4 + [P, P]
+            lib.lbm_oracle_link_coefficients.restype = None
             lib.lbm_oracle_mask.argtypes = [
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P]
             lib.lbm_oracle_mask.restype = ctypes.c_int
@@ -111,6 +119,13 @@ def params(D, dt, dx, kappa):
     return float(out[0]), float(out[1]), float(out[2])
 
 
+def link_coefficients(delta_m, kappa, dt, dx):
+    """(A[3], B[3]) of the theta = 0 membrane rule, Eqs. B4a-B4c."""
+    A, B = np.zeros(3), np.zeros(3)
+    _load().lbm_oracle_link_coefficients(float(delta_m), float(kappa), float(dt), float(dx), _ptr(A), _ptr(B))
+    return A, B
+
+
 def mask(labels, phase_of_label, bc):
     """Bit-packed membrane/phase byte per site (see ``lbm_oracle_mask``)."""
     labels = np.ascontiguousarray(labels, dtype=np.int32)
@@ -125,7 +140,7 @@ def mask(labels, phase_of_label, bc):
 
 
 def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
-        want_field=False, want_series=False, want_state=False, threads=0):
+        want_field=False, want_series=False, want_state=False, threads=0, delta=None):
     """Run the scheme from M = 1 to t = len(f)*dt.
 
     ``labels``: int32 [nz, ny, nx] compartment ids; ``phase_of_label``: phase
@@ -133,7 +148,9 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     Returns a dict with ``Z`` (complex sum of M over sites at the end),
     ``S`` = |Z|/N, and optionally ``field`` (complex [nz, ny, nx]),
     ``series`` (complex [K], Z after each step) and ``state`` (complex
-    [nz, ny, nx, 7]).
+    [nz, ny, nx, 7]).  ``delta``: optional [6, nz, ny, nx] membrane positions
+    on the links (distance in dx from the node along +x, -x, +y, -y, +z, -z),
+    which selects the theta = 0 rule of Eqs. B4a-B4c.
     """
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     nz, ny, nx = labels.shape
@@ -149,10 +166,17 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     field = np.empty(2 * N) if want_field else None
     series = np.empty(2 * K) if want_series else None
     state = np.empty(2 * 7 * N) if want_state else None
-    rc = _load().lbm_oracle_run(
-        nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
-        int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
-        int(threads), _ptr(Z), _ptr(field), _ptr(series), _ptr(state))
+    if delta is None:
+        rc = _load().lbm_oracle_run(
+            nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
+            int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
+            int(threads), _ptr(Z), _ptr(field), _ptr(series), _ptr(state))
+    else:
+        dl = np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(6, N).T)
+        rc = _load().lbm_oracle_run_links(
+            nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
+            int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
+            int(threads), _ptr(dl), _ptr(Z), _ptr(field), _ptr(series), _ptr(state))
     if rc != 0:
         raise ValueError("oracle run: invalid input")
     out = {"Z": complex(Z[0], Z[1])}

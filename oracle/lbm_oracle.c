@@ -20,8 +20,10 @@
  *
  * Grid: nx*ny*nz unique nodes, x fastest; node n sits at x_n = n*dx.
  * A periodic axis of N nodes has period L = N*dx (the paper's node N, which
- * duplicates node 0, is dropped).  Buffer layers at n = -1 and n = N are held
- * explicitly in a padded copy of the post-collision state.
+ * duplicates node 0, is dropped).  Buffer layers at n = -2, -1 and n = N,
+ * N+1 are held explicitly in a padded copy of the post-collision state (the
+ * second layer serves the second-neighbour terms of the link-distance
+ * membrane rule, Eqs. B4a-B4c).
  *
  * Units: um, ms.  gG[a] = gamma*G0_a in rad/(um*ms); D in um^2/ms; T2 in ms
  * (INFINITY allowed); kappa in um/ms (0 = impermeable, INFINITY = no membrane).
@@ -60,8 +62,9 @@ static int reflect_dir(int i, int axis)
     return -1;
 }
 
-/* Padded layout: (nx+2) x (ny+2) x (nz+2) nodes, coordinate -1..N on each
+/* Padded layout: (nx+4) x (ny+4) x (nz+4) nodes, coordinate -2..N+1 on each
  * axis; Q complex populations per node. */
+enum { PAD = 2 };
 typedef struct {
     int nx, ny, nz;
     int px, py, pz;
@@ -69,7 +72,7 @@ typedef struct {
 
 static size_t pidx(const grid_t* g, int x, int y, int z)
 {
-    return ((size_t)(z + 1) * g->py + (size_t)(y + 1)) * g->px + (size_t)(x + 1);
+    return ((size_t)(z + PAD) * g->py + (size_t)(y + PAD)) * g->px + (size_t)(x + PAD);
 }
 
 static size_t sidx(const grid_t* g, int x, int y, int z)
@@ -95,6 +98,48 @@ static void membrane_shares(double kappa, double dt, double dx, double* r, doubl
     *s = 1.0 / (1.0 + P);
 }
 
+/* Coefficients of the link-distance membrane rule for a straight membrane
+ * normal to the link (theta = 0), Eqs. B4a-B4c, from the Neumann (Eq. c_n)
+ * and Dirichlet (Eq. c_d) coefficients of the node's fraction dl = Delta_m
+ * and of the far node's fraction 1 - dl:
+ *   A_j = (c_d4 c*_d4 c_nj eps_D dx + (c*_d4 c_n4 c_dj + c*_n4 c_d4 c_nj) kappa dt) / F
+ *   B_j = c_d4 c_n4 (c*_nj - c*_dj) kappa dt / F
+ *   F   = c_d4 c*_d4 eps_D dx + (c_d4 c*_n4 + c_n4 c*_d4) kappa dt.
+ * A[0..2] multiply (own population towards the membrane, the same population
+ * one node further back, own population away from it); B[0..2] multiply
+ * (population arriving from the far node, the same population one node
+ * beyond it, far node's population towards the membrane). */
+static void coef_n(double d, double c[4])
+{
+    c[0] = 1.0;
+    c[1] = -(2.0 * d - 1.0) / (2.0 * d + 1.0);
+    c[2] = (2.0 * d - 1.0) / (2.0 * d + 1.0);
+    c[3] = 2.0 / (2.0 * d + 1.0);
+}
+
+static void coef_d(double d, double c[4])
+{
+    c[0] = 2.0 * (d - 1.0);
+    c[1] = -(2.0 * d - 1.0) * (2.0 * d - 1.0) / (2.0 * d + 1.0);
+    c[2] = 2.0 * (2.0 * d - 1.0) / (2.0 * d + 1.0);
+    c[3] = (3.0 - 2.0 * d) / (2.0 * d + 1.0);
+}
+
+void lbm_oracle_link_coefficients(double dl, double kappa, double dt, double dx, double* A, double* B)
+{
+    double cn[4], cd[4], cns[4], cds[4];
+    coef_n(dl, cn);
+    coef_d(dl, cd);
+    coef_n(1.0 - dl, cns);
+    coef_d(1.0 - dl, cds);
+    const double ex = EPS_D * dx, kd = kappa * dt;
+    const double F = cd[3] * cds[3] * ex + (cd[3] * cns[3] + cn[3] * cds[3]) * kd;
+    for (int j = 0; j < 3; ++j) {
+        A[j] = (cd[3] * cds[3] * cn[j] * ex + (cds[3] * cn[3] * cd[j] + cns[3] * cd[3] * cn[j]) * kd) / F;
+        B[j] = cd[3] * cn[3] * (cns[j] - cds[j]) * kd / F;
+    }
+}
+
 /* Scalar parameters as the oracle derives them: out = {tau, r, s}. */
 void lbm_oracle_params(double D, double dt, double dx, double kappa, double* out)
 {
@@ -115,7 +160,7 @@ void lbm_oracle_params(double D, double dt, double dx, double kappa, double* out
 int lbm_oracle_mask(int nx, int ny, int nz, const int32_t* labels, int n_labels,
                     const uint8_t* phase_of_label, const int* bc, uint8_t* mask_out)
 {
-    grid_t g = {nx, ny, nz, nx + 2, ny + 2, nz + 2};
+    grid_t g = {nx, ny, nz, nx + 2 * PAD, ny + 2 * PAD, nz + 2 * PAD};
     int dims[3] = {nx, ny, nz};
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -159,12 +204,12 @@ int lbm_oracle_mask(int nx, int ny, int nz, const int32_t* labels, int n_labels,
  *   state_out[2*7*N]  : g_i(x, t^K) per site, direction-major within a site.
  * Returns 0, or -1 on invalid input.
  */
-int lbm_oracle_run(int nx, int ny, int nz, double dx,
-                   const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
-                   const int* bc, int n_phases, const double* D, const double* T2,
-                   double kappa, double dt, long n_steps, const double* f,
-                   const double* gG, int n_threads,
-                   double* Z_out, double* field_out, double* series_out, double* state_out)
+static int run_impl(int nx, int ny, int nz, double dx,
+                    const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
+                    const int* bc, int n_phases, const double* D, const double* T2,
+                    double kappa, double dt, long n_steps, const double* f,
+                    const double* gG, int n_threads, const double* delta,
+                    double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0) return -1;
     if (n_phases < 1 || n_phases > 4) return -1;
@@ -175,7 +220,7 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
 #else
     (void)n_threads;
 #endif
-    grid_t g = {nx, ny, nz, nx + 2, ny + 2, nz + 2};
+    grid_t g = {nx, ny, nz, nx + 2 * PAD, ny + 2 * PAD, nz + 2 * PAD};
     const int dims[3] = {nx, ny, nz};
     const size_t N = (size_t)nx * ny * nz;
     const size_t NP = (size_t)g.px * g.py * g.pz;
@@ -203,6 +248,9 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
     }
     double r, s;
     membrane_shares(kappa, dt, dx, &r, &s);
+    if (delta)
+        for (size_t i = 0; i < 6 * N; ++i)
+            if (!(delta[i] > 0.0 && delta[i] < 1.0)) return -1;
 
     cplx* gs = malloc(sizeof(cplx) * Q * N);     /* g_i(x, t^k)             */
     cplx* gh = malloc(sizeof(cplx) * Q * NP);    /* hat g_i with buffers    */
@@ -210,9 +258,11 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
     uint8_t* ph = malloc(N);
     if (!gs || !gh || !lab || !ph) { free(gs); free(gh); free(lab); free(ph); return -1; }
 
-    /* Labels of the buffer nodes: periodic -> the wrapped node; mirror -> the
-     * boundary node itself (Sec. 2.4.4: the buffer node's geometry equals the
-     * boundary node's), so a mirror face is never a membrane. */
+    /* Labels of the buffer nodes (layers d = 0, 1 beyond each face):
+     * periodic -> the wrapped node; mirror -> the node mirrored in the face
+     * (Sec. 2.4.4: node -1-d mirrors node d, node N+d mirrors node N-1-d), so
+     * a mirror face is never a membrane.  A layer deeper than the axis
+     * (N = 1) repeats the mirrored/wrapped index modulo N. */
     for (size_t i = 0; i < NP; ++i) lab[i] = -1;
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
@@ -222,17 +272,23 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
             }
     for (int a = 0; a < 3; ++a) {
         int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
-        for (int u = 0; u < dims[o2]; ++u)
-            for (int v = 0; v < dims[o1]; ++v) {
-                int lo[3], hi[3], slo[3], shi[3];
-                lo[a] = -1; hi[a] = dims[a];
-                lo[o1] = hi[o1] = slo[o1] = shi[o1] = v;
-                lo[o2] = hi[o2] = slo[o2] = shi[o2] = u;
-                if (bc[a] == BC_PERIODIC) { slo[a] = dims[a] - 1; shi[a] = 0; }
-                else { slo[a] = 0; shi[a] = dims[a] - 1; }
-                lab[pidx(&g, lo[0], lo[1], lo[2])] = labels[sidx(&g, slo[0], slo[1], slo[2])];
-                lab[pidx(&g, hi[0], hi[1], hi[2])] = labels[sidx(&g, shi[0], shi[1], shi[2])];
-            }
+        for (int d = 0; d < PAD; ++d)
+            for (int u = 0; u < dims[o2]; ++u)
+                for (int v = 0; v < dims[o1]; ++v) {
+                    int lo[3], hi[3], slo[3], shi[3];
+                    lo[a] = -1 - d; hi[a] = dims[a] + d;
+                    lo[o1] = hi[o1] = slo[o1] = shi[o1] = v;
+                    lo[o2] = hi[o2] = slo[o2] = shi[o2] = u;
+                    if (bc[a] == BC_PERIODIC) {
+                        slo[a] = ((dims[a] - 1 - d) % dims[a] + dims[a]) % dims[a];
+                        shi[a] = d % dims[a];
+                    } else {
+                        slo[a] = d % dims[a];
+                        shi[a] = ((dims[a] - 1 - d) % dims[a] + dims[a]) % dims[a];
+                    }
+                    lab[pidx(&g, lo[0], lo[1], lo[2])] = labels[sidx(&g, slo[0], slo[1], slo[2])];
+                    lab[pidx(&g, hi[0], hi[1], hi[2])] = labels[sidx(&g, shi[0], shi[1], shi[2])];
+                }
     }
 
     /* Initial condition M = 1 + 0i at equilibrium: g_i = omega_i M (Eq. g_eq). */
@@ -267,10 +323,16 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
              * origin x_o = 0 (where G0.x = 0). */
             double xlo = (0 + (-1)) * dx, xhi = ((dims[a] - 1) + dims[a]) * dx;
             cplx rot_lo = cexp(I * gG[a] * xlo * F), rot_hi = cexp(I * gG[a] * xhi * F);
+            for (int d = 0; d < PAD; ++d)
             for (int u = 0; u < dims[o2]; ++u)
                 for (int v = 0; v < dims[o1]; ++v) {
+                    /* layer d: node -1-d and node N+d.  Periodic: images of
+                     * nodes N-1-d and d.  Mirror: reflections of nodes d and
+                     * N-1-d, whose x_n + x_m is -dx and (2N-1) dx for every d. */
                     int lo[3], hi[3], c0[3], cN[3];
-                    lo[a] = -1; hi[a] = dims[a]; c0[a] = 0; cN[a] = dims[a] - 1;
+                    lo[a] = -1 - d; hi[a] = dims[a] + d;
+                    c0[a] = d % dims[a];
+                    cN[a] = ((dims[a] - 1 - d) % dims[a] + dims[a]) % dims[a];
                     lo[o1] = hi[o1] = c0[o1] = cN[o1] = v;
                     lo[o2] = hi[o2] = c0[o2] = cN[o2] = u;
                     size_t plo = pidx(&g, lo[0], lo[1], lo[2]), phi_ = pidx(&g, hi[0], hi[1], hi[2]);
@@ -310,10 +372,26 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
                     gbar[0] = gh[pi * Q + 0];
                     for (int i = 1; i < Q; ++i) {
                         size_t py_ = pidx(&g, x - EX[i], y - EY[i], z - EZ[i]);
-                        if (lab[py_] != Lx)
-                            gbar[i] = s * gh[py_ * Q + i] + r * gh[pi * Q + OPP[i]];
-                        else
+                        if (lab[py_] == Lx) {
                             gbar[i] = gh[py_ * Q + i];
+                            continue;
+                        }
+                        const int ib = OPP[i];   /* from x towards the membrane */
+                        /* link-distance rule (Eqs. B4a-B4c): needs the node
+                         * behind x (x + e_i) in x's compartment and the node
+                         * beyond the far node (x - 2 e_i) in the far node's;
+                         * otherwise, and for kappa = inf (no membrane), the
+                         * half-link rule of Eq. B5 */
+                        size_t pb = pidx(&g, x + EX[i], y + EY[i], z + EZ[i]);
+                        size_t pe = pidx(&g, x - 2 * EX[i], y - 2 * EY[i], z - 2 * EZ[i]);
+                        if (delta && !isinf(kappa) && lab[pb] == Lx && lab[pe] == lab[py_]) {
+                            double A[3], B[3];
+                            lbm_oracle_link_coefficients(delta[si * 6 + (ib - 1)], kappa, dt, dx, A, B);
+                            gbar[i] = A[0] * gh[pi * Q + ib] + A[1] * gh[pb * Q + ib] + A[2] * gh[pi * Q + i] +
+                                      B[0] * gh[py_ * Q + i] + B[1] * gh[pe * Q + i] + B[2] * gh[py_ * Q + ib];
+                        } else {
+                            gbar[i] = s * gh[py_ * Q + i] + r * gh[pi * Q + ib];
+                        }
                     }
                     double xdotG = (x * dx) * gG[0] + (y * dx) * gG[1] + (z * dx) * gG[2];
                     cplx fac = cexp(-I * xdotG * fk * dt) * decay[ph[si]];
@@ -346,4 +424,34 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
     if (Z_out) { Z_out[0] = creal(Z); Z_out[1] = cimag(Z); }
     free(gs); free(gh); free(lab); free(ph);
     return 0;
+}
+
+int lbm_oracle_run(int nx, int ny, int nz, double dx,
+                   const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
+                   const int* bc, int n_phases, const double* D, const double* T2,
+                   double kappa, double dt, long n_steps, const double* f,
+                   const double* gG, int n_threads,
+                   double* Z_out, double* field_out, double* series_out, double* state_out)
+{
+    return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
+                    gG, n_threads, NULL, Z_out, field_out, series_out, state_out);
+}
+
+/*
+ * The same run with membranes at given positions on their links (theta = 0,
+ * Eqs. B4a-B4c): delta[6*s + (j-1)], j = 1..6, is the distance, in units of
+ * dx, from node s to the membrane on its link to the neighbour s + e_j
+ * (0 < delta < 1; read only on membrane links).  A consistent input has
+ * delta[s][j] = 1 - delta[s + e_j][jbar].
+ */
+int lbm_oracle_run_links(int nx, int ny, int nz, double dx,
+                         const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
+                         const int* bc, int n_phases, const double* D, const double* T2,
+                         double kappa, double dt, long n_steps, const double* f,
+                         const double* gG, int n_threads, const double* delta,
+                         double* Z_out, double* field_out, double* series_out, double* state_out)
+{
+    if (!delta) return -1;
+    return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
+                    gG, n_threads, delta, Z_out, field_out, series_out, state_out);
 }

@@ -16,6 +16,11 @@ micrograph, here replaced by a Voronoi tessellation):
 * ``cylinders``  -- non-overlapping z-aligned cylinders, gamma-distributed radii
 * ``spheres``    -- non-overlapping sphere pack, uniform radii
 * ``voronoi_tissue`` -- Voronoi cells + extracellular band + vessel tubes
+* ``walls``      -- planes at arbitrary positions (membranes off the half-links)
+
+``link_distances`` gives, for the analytic geometries (walls, spheres,
+cylinders), where each membrane cuts its lattice link: the input of the
+theta = 0 membrane rule with a per-link distance (Eqs. B4a-B4c).
 """
 from __future__ import annotations
 
@@ -82,6 +87,109 @@ def planes(shape, dx, widths, axis=0, phases=None):
     else:
         pol = np.array([phases[i % len(phases)] for i in range(n_labels)], np.uint8)
     return Geometry(np.ascontiguousarray(labels, np.int32), pol, dx, {"kind": "planes", "widths": list(widths)})
+
+
+def walls(n, dx, positions, axis=0, cross=(1, 1), phases=None, periodic=True):
+    """Planes normal to ``axis`` at the given positions (um, increasing, inside
+    [0, n*dx)), not tied to the half-links.  Node k (at k*dx) gets label j =
+    the number of walls at or below it; on a periodic axis the segment after
+    the last wall continues into the first (label 0).  ``cross`` = sizes of
+    the two other axes (in z, y, x order without ``axis``)."""
+    pos = np.asarray(positions, np.float64)
+    xk = np.arange(n) * dx
+    lab1 = np.searchsorted(pos, xk, side="right").astype(np.int32)
+    n_labels = len(pos) + 1
+    if periodic and len(pos) > 0:
+        lab1 %= len(pos)
+        n_labels = len(pos)
+    if axis == 0:
+        labels = np.broadcast_to(lab1[None, None, :], (cross[0], cross[1], n))
+    elif axis == 1:
+        labels = np.broadcast_to(lab1[None, :, None], (cross[0], n, cross[1]))
+    else:
+        labels = np.broadcast_to(lab1[:, None, None], (n, cross[0], cross[1]))
+    if phases is None:
+        pol = np.zeros(n_labels, np.uint8)
+    else:
+        pol = np.array([phases[i % len(phases)] for i in range(n_labels)], np.uint8)
+    return Geometry(np.ascontiguousarray(labels, np.int32), pol, dx,
+                    {"kind": "walls", "positions": pos.tolist(), "axis": axis})
+
+
+_DIRS = ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))   # +x -x +y -y +z -z
+
+
+def link_distances(geom: Geometry, bc=(0, 0, 0)):
+    """Where membranes cut the lattice links, for the analytic geometries.
+
+    Returns float32 [6, nz, ny, nx]: entry j at node s is the distance, in
+    units of dx, from s to the membrane on its link to s + e_j (directions
+    +x, -x, +y, -y, +z, -z), 0.5 where the link carries no membrane.  Walls
+    are exact; for spheres and cylinders the link is cut where it leaves the
+    sphere (cylinder) of whichever end node lies inside one (periodic minimum
+    image).  Values are clipped to [1e-4, 1 - 1e-4].
+    """
+    lab = geom.labels
+    nz, ny, nx = lab.shape
+    dims = (nx, ny, nz)
+    dx = geom.dx
+    out = np.full((6, nz, ny, nx), 0.5, np.float32)
+    kind = geom.info.get("kind")
+    if kind not in ("walls", "spheres", "cylinders"):
+        raise ValueError(f"no sub-voxel membrane positions for a '{kind}' geometry")
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    node = [xx, yy, zz]
+    for j, e in enumerate(_DIRS):
+        a = j // 2
+        nb = lab
+        # neighbour label (periodic wrap; none across a mirror face)
+        nb = np.roll(lab, -e[a], axis=2 - a)
+        exists = np.ones(lab.shape, bool)
+        if bc[a] != 0:
+            edge = node[a] == (dims[a] - 1 if e[a] > 0 else 0)
+            exists &= ~edge
+        memb = exists & (nb != lab)
+        if not memb.any():
+            continue
+        idx = np.nonzero(memb)
+        if kind == "walls":
+            if geom.info["axis"] != a:
+                continue
+            pos = np.asarray(geom.info["positions"])
+            x0 = node[a][idx] * dx
+            L = dims[a] * dx
+            # the wall between x0 and x0 + e dx (periodic: positions repeat with L)
+            cand = np.concatenate([pos - L, pos, pos + L])
+            t = (cand[None, :] - x0[:, None]) * e[a]
+            t[(t < 0) | (t > dx)] = np.inf
+            d = t.min(axis=1) / dx
+        else:
+            cen = np.asarray(geom.info["centers"], np.float64)
+            rad = np.asarray(geom.info["radii"], np.float64)
+            box = np.array([nx, ny, nz], np.float64) * dx
+            la, lb = lab[idx], nb[idx]
+            # the body one end lies in; between two bodies the lower label's,
+            # so both ends of a link see the same membrane
+            k = np.where((la > 0) & (lb > 0), np.minimum(la, lb), np.where(la > 0, la, lb)) - 1
+            p = np.stack([node[c][idx] * dx for c in range(3)], 1)
+            ndim = 3 if kind == "spheres" else 2
+            c3 = np.zeros((len(k), 3))
+            c3[:, :ndim] = cen[k][:, :ndim]
+            dv = p - c3
+            if ndim == 2:
+                dv[:, 2] = 0.0
+            dv -= box * np.round(dv / box)
+            ev = np.array(e, np.float64)
+            if ndim == 2:
+                ev[2] = 0.0
+            bq = dv @ ev
+            cq = (dv * dv).sum(1) - rad[k] ** 2
+            disc = np.sqrt(np.maximum(bq * bq - cq, 0.0))
+            r1, r2 = -bq - disc, -bq + disc
+            t = np.where((r1 > 0) & (r1 < dx), r1, r2)
+            d = t / dx
+        out[j][idx] = np.clip(d, 1e-4, 1 - 1e-4)
+    return out
 
 
 def _relax_periodic(centers, radii, box, gap, max_iter=4000, rng=None):
@@ -170,7 +278,8 @@ def cylinders(n, dx, mean_radius=3.0, cv=0.3, fraction=0.6, seed=0, gap=None):
     pol = np.full(len(radii) + 1, PHASE_IN, np.uint8)
     pol[0] = PHASE_EX
     g = Geometry(labels, pol, dx, {"kind": "cylinders", "n_cyl": len(radii), "seed": seed,
-                                   "target_fraction": fraction, "relax_iters": iters})
+                                   "target_fraction": fraction, "relax_iters": iters,
+                                   "centers": np.asarray(centers).tolist(), "radii": radii.tolist()})
     g.info["intra_fraction"] = float((lab2 > 0).mean())
     return g
 
@@ -218,7 +327,8 @@ def spheres(n, dx, rmin=2.0, rmax=6.0, fraction=0.5, seed=0, gap=None):
     pol = np.full(len(radii) + 1, PHASE_IN, np.uint8)
     pol[0] = PHASE_EX
     g = Geometry(labels, pol, dx, {"kind": "spheres", "n_spheres": len(radii), "seed": seed,
-                                   "target_fraction": fraction, "relax_iters": iters})
+                                   "target_fraction": fraction, "relax_iters": iters,
+                                   "centers": np.asarray(centers).tolist(), "radii": radii.tolist()})
     g.info["intra_fraction"] = float((labels > 0).mean())
     return g
 

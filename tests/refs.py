@@ -198,6 +198,66 @@ def slab_signal(a, D, gG, f, dt, T2=math.inf, n_modes=80):
     return abs(v[0])
 
 
+def slab_field(a, D, gG, f, dt, xi, T2=math.inf, n_modes=120):
+    """M(xi, t_end) inside one impermeable slab [0, a] (gradient normal to it,
+    coordinate measured from the slab's centre for the reaction, so the field
+    carries the global phase of the centre when sum f != 0), at positions xi in
+    [0, a], from the same Neumann-mode propagator as ``slab_signal``."""
+    n = np.arange(n_modes)
+    lam = (n * math.pi / a) ** 2
+    xs, wq = np.polynomial.legendre.leggauss(600)
+    xs = (xs + 1) * a / 2
+    wq = wq * a / 2
+    basis = lambda x: np.array([np.full_like(x, 1 / math.sqrt(a)) if m == 0 else
+                                math.sqrt(2 / a) * np.cos(m * math.pi * x / a) for m in n])
+    phi = basis(xs)
+    X = (phi * (xs - a / 2) * wq) @ phi.T
+    v = np.zeros(n_modes, complex)
+    v[0] = math.sqrt(a)          # M = 1 projected on phi_0
+    f = np.asarray(f, float)
+    k = 0
+    while k < len(f):
+        j = k
+        while j < len(f) and f[j] == f[k]:
+            j += 1
+        Hm = -(D * np.diag(lam) + 1j * gG * f[k] * X + np.eye(n_modes) / T2)
+        v = sla.expm(Hm * (j - k) * dt) @ v
+        k = j
+    return basis(np.asarray(xi, float)).T @ v
+
+
+def exchange_field(a1, a2, D1, D2, T21, T22, kappa, t_end, xq, n_cells=2000):
+    """M at positions xq (from the left wall) at t_end for the set-up of
+    ``exchange_signal``, by linear interpolation of the cell values."""
+    n1 = max(2, int(round(n_cells * a1 / (a1 + a2))))
+    n2 = max(2, n_cells - n1)
+    h1, h2 = a1 / n1, a2 / n2
+    n = n1 + n2
+    h = np.array([h1] * n1 + [h2] * n2)
+    Dc = np.array([D1] * n1 + [D2] * n2)
+    rate = np.array([1 / T21] * n1 + [1 / T22] * n2)
+    Amat = np.zeros((n, n))
+    for j in range(n - 1):
+        if j == n1 - 1:
+            res = h1 / (2 * D1) + (1 / kappa if kappa > 0 else math.inf) + h2 / (2 * D2)
+            g = 0.0 if math.isinf(res) else 1.0 / res
+        else:
+            g = 1.0 / (h[j] / (2 * Dc[j]) + h[j + 1] / (2 * Dc[j + 1]))
+        Amat[j, j] -= g / h[j]
+        Amat[j, j + 1] += g / h[j]
+        Amat[j + 1, j + 1] -= g / h[j + 1]
+        Amat[j + 1, j] += g / h[j + 1]
+    Amat -= np.diag(rate)
+    M = sla.expm(Amat * t_end) @ np.ones(n)
+    xc = np.concatenate([(np.arange(n1) + 0.5) * h1, a1 + (np.arange(n2) + 0.5) * h2])
+    xq = np.asarray(xq, float)
+    out = np.empty(xq.shape)
+    left = xq < a1
+    out[left] = np.interp(xq[left], xc[:n1], M[:n1])
+    out[~left] = np.interp(xq[~left], xc[n1:], M[n1:])
+    return out
+
+
 # --------------------------------------------------- two-compartment exchange
 def exchange_signal(a1, a2, D1, D2, T21, T22, kappa, t_end, n_cells=400):
     """Mean M over [0, a1 + a2] at t_end, M(0) = 1, Neumann outer walls,
