@@ -331,6 +331,69 @@ def run_adjoint(args):
     return 0
 
 
+# ---------------------------------------------------------------- membrane positions
+def run_links(args):
+    """Membranes at their exact positions on the links (theta = 0 rule,
+    Eqs. B4a-B4c, register sweep) against the half-link rule on the same
+    grid: z-aligned cylinders (the c2 generator) at twice its resolution,
+    256^3 at dx 0.25 um, 3 gradient directions, PGSE b = 1000."""
+    import torch
+    from paper_1907_00908_gb300 import lbmbt, synth
+    torch.cuda.set_device(0)
+    n = min(args.n, 256)
+    t0 = time.perf_counter()
+    geom = synth.cylinders(n, 0.25, seed=1)
+    dl = synth.link_distances(geom, (0, 0, 0))
+    t_geo = time.perf_counter() - t0
+    dt = 0.0015625
+    gGs = [lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, dt, d)[0] for d in ((1, 0, 0), (0, 1, 0), (1, 1, 1))]
+    _, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, dt, (1, 0, 0))
+    members = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
+    stream = torch.cuda.current_stream()
+    n_memb_links = int((dl != 0.5).sum())
+    res = {}
+    for name, kernel, use_dl in (("links_register", 1, True), ("half_link_register", 1, False),
+                                 ("half_link_bulk_copy", 2, False)):
+        s = lbmbt.Solver(0, stream)
+        s.set_option(lbmbt.OPT_KERNEL, kernel)
+        s.set_option(lbmbt.OPT_AUTOTUNE, 1)
+        s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, (0, 0, 0))
+        if use_dl:
+            s.set_link_distances(dl)
+        s.set_phases(C2_D, C2_T2)
+        s.set_sequence(dt, f, gGs[0])
+        s.prepare(members)
+        s.advance(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(0) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sig = s.advance(args.steps, want_signal=True, n_members=len(gGs))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"MLUPS": geom.n_sites * len(gGs) / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                     "launch": {"block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT)},
+                     "S_after": (np.abs(sig[:, 0] + 1j * sig[:, 1]) / geom.n_sites).tolist(), "clocks": clk.summary()}
+        s.close()
+    peak, peak_kind = peaks()
+    v = res["links_register"]["MLUPS"]
+    # algorithmic bytes: 113 per site update + 4 per membrane link (its position)
+    bytes_site = BYTES_PER_SITE + 4.0 * n_memb_links / geom.n_sites
+    achieved = bytes_site * v * 1e6 / 1e9
+    line = {"metric": "MLUPS (fused sweep with membrane positions on the links, FP32)", "value": v, "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["links_register"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"cylinders{n}_dx0.25_links_3dir", "grid": [n] * 3, "membrane_link_fraction":
+                       n_memb_links / (6.0 * geom.n_sites), "geometry_gen_s": round(t_geo, 1)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": peak_kind, "bytes_per_site_member": bytes_site,
+                         "kernel": "sweep_kernel (register)"},
+            "compare": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- slabs (strips)
 def run_slab(args):
     """The 512^3 tissue batch cut into z slabs on one GPU (one context per
@@ -408,10 +471,11 @@ def main():
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
     ap.add_argument("--slabs", type=int, default=4, help="slab workload: number of z slabs")
-    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint", "slab"],
+    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint", "slab", "links"],
                     help="tissue512 (default): the 512^3 tissue batch of 3 directions; batch: 528 members on "
                          "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack; slab: the "
-                         "tissue batch cut into --slabs z slabs with a face exchange per step")
+                         "tissue batch cut into --slabs z slabs with a face exchange per step; links: membranes at "
+                         "their exact positions on the links (256^3 cylinders) against the half-link rule")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -421,6 +485,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "slab":
         return run_slab(args)
+    if args.workload == "links":
+        return run_links(args)
 
     import torch
     import torch.distributed as dist

@@ -140,6 +140,25 @@ int lbmbt_slab_faces(lbmbt_ctx* ctx, int member, void* lo_out, void* hi_out);
  * context's stream; the call returns without waiting. */
 int lbmbt_slab_set_halos(lbmbt_ctx* ctx, int member, const void* lo_in, const void* hi_in);
 
+/*
+ * Membrane positions on the lattice links of geometry `index`, for the
+ * membrane rule of a straight membrane normal to the link (theta = 0) at a
+ * distance Delta_m dx from the node (Sec. 2.4.2, Eqs. B4a-B4c with the
+ * coefficients of Eqs. c_n and c_d), instead of the half-link rule (Eq. B5,
+ * Delta_m = 1/2).  delta: float32 [6][nz][ny][nx], host or device memory
+ * (delta_on_device != 0 means device); entry j-1 at a node is Delta_m of its
+ * link to the neighbour across +e_j (D3Q7 order +x, -x, +y, -y, +z, -z),
+ * read only on membrane links, 0 < Delta_m < 1 (host input is checked:
+ * EINVAL), and a consistent input gives the two ends of a link Delta_m and
+ * 1 - Delta_m.  The rule uses the node behind each end (the second
+ * neighbours x_ii, x_ee of Eqs. B2a/B2b); where one of them lies in another
+ * compartment, and for kappa = INFINITY, the link keeps the half-link rule.
+ * delta = NULL removes the positions.  Runs with positions use the register
+ * sweep (LBMBT_OPT_KERNEL = 2 fails with EINVAL); the adjoint and slabs
+ * return EUNSUPPORTED.
+ */
+int lbmbt_set_link_distances(lbmbt_ctx* ctx, int index, const float* delta, int delta_on_device);
+
 /* Copy the per-node mask byte of geometry `index` (encoding above) to host
  * memory mask_out[nz*ny*nx]. */
 int lbmbt_get_mask(lbmbt_ctx* ctx, int index, uint8_t* mask_out);

@@ -35,6 +35,7 @@ struct Geom {
     // LBMBT_FACE_OWN / _HALO / _HALO_WRAP of the low and high z face
     int slab = 0, z0 = 0, nzg = 0;
     int zkind[2] = {0, 0};
+    float* d_dlt = nullptr;       // membrane positions on the links, [6][plane], or nullptr
 };
 
 constexpr int GRAPH_CHUNK = 16;
@@ -245,7 +246,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
     drop_graph(c);
-    for (auto& g : c->geoms) cudaFree(g.d_mask);
+    for (auto& g : c->geoms) { cudaFree(g.d_mask); cudaFree(g.d_dlt); }
     cudaFree(c->d_f); cudaFree(c->d_F);
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
@@ -332,7 +333,7 @@ extern "C" int lbmbt_set_geometry(lbmbt_ctx* c, int nx, int ny, int nz, double d
     int rc = make_geom(c, nx, ny, nz, dx, labels, on_dev, n_labels, pol, bc, &g);
     if (rc) return rc;
     invalidate_run(c);
-    for (auto& o : c->geoms) cudaFree(o.d_mask);
+    for (auto& o : c->geoms) { cudaFree(o.d_mask); cudaFree(o.d_dlt); }
     c->geoms.clear();
     c->geoms.push_back(g);
     return LBMBT_OK;
@@ -431,7 +432,7 @@ extern "C" int lbmbt_set_geometry_slab(lbmbt_ctx* c, int nx, int ny, int nz, dou
     g.zkind[0] = lo_kind;
     g.zkind[1] = hi_kind;
     invalidate_run(c);
-    for (auto& o : c->geoms) cudaFree(o.d_mask);
+    for (auto& o : c->geoms) { cudaFree(o.d_mask); cudaFree(o.d_dlt); }
     c->geoms.clear();
     c->geoms.push_back(g);
     return LBMBT_OK;
@@ -446,6 +447,34 @@ extern "C" int lbmbt_get_mask(lbmbt_ctx* c, int index, uint8_t* mask_out)
     if (rc) return rc;
     const Geom& g = c->geoms[index];
     CU(c, cudaMemcpyAsync(mask_out, g.d_mask, g.N, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+// Membrane positions on the links of geometry `index` (theta = 0 rule,
+// Eqs. B4a-B4c): delta [6][nz][ny][nx] float32, entry j-1 at a node is the
+// distance in dx from the node to the membrane on its link to node + e_j,
+// read on membrane links only.  NULL removes them (half-link rule, Eq. B5).
+extern "C" int lbmbt_set_link_distances(lbmbt_ctx* c, int index, const float* delta, int on_device)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (index < 0 || index >= (int)c->geoms.size()) return fail(c, LBMBT_EINVAL, "geometry %d not set", index);
+    int rc = set_device(c);
+    if (rc) return rc;
+    Geom& g = c->geoms[index];
+    invalidate_run(c);
+    cudaFree(g.d_dlt);
+    g.d_dlt = nullptr;
+    if (!delta) return LBMBT_OK;
+    if (g.slab) return fail(c, LBMBT_EUNSUPPORTED, "membrane positions on a slab are not supported");
+    if (!on_device)
+        for (long long i = 0; i < 6 * g.N; ++i)
+            if (!(delta[i] > 0.f && delta[i] < 1.f))
+                return fail(c, LBMBT_EINVAL, "membrane position %g at entry %lld outside (0, 1)", (double)delta[i], i);
+    const long long plane = (g.N + 63) / 64 * 64;
+    CU(c, cudaMalloc(&g.d_dlt, sizeof(float) * 6 * plane));
+    const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int j = 0; j < 6; ++j)
+        CU(c, cudaMemcpyAsync(g.d_dlt + j * plane, delta + j * g.N, sizeof(float) * g.N, kind, c->stream));
     return sync(c);
 }
 
@@ -539,7 +568,7 @@ static constexpr int TMA_MAX_CAP = 1024;
 static bool tma_eligible(const lbmbt_ctx* c)
 {
     for (auto& d : c->descs)
-        if (d.nx % 16 != 0 || d.nx > TMA_MAX_CAP) return false;
+        if (d.nx % 16 != 0 || d.nx > TMA_MAX_CAP || d.dlt != nullptr) return false;
     return true;
 }
 
@@ -554,7 +583,8 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     const bool want = c->kernel_opt == 2 || (c->kernel_opt == 0 && c->tuned_kernel != 1);
     const bool tma = want && tma_eligible(c);
     if (c->kernel_opt == 2 && !tma)
-        return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member", TMA_MAX_CAP);
+        return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member and no "
+                                     "membrane positions", TMA_MAX_CAP);
     int cap = 16, capx = 0;
     for (int m = 0; m < c->n_members; ++m) {
         MemberDesc& d = c->descs[m];
@@ -624,6 +654,9 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.F = c->d_F;
     a.partial = c->d_partial;
     a.fac = c->d_fac;
+    a.links = 0;
+    for (auto& d : c->descs)
+        if (d.dlt) a.links = 1;
     return a;
 }
 
@@ -807,6 +840,11 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         for (int a = 0; a < 3; ++a)
             if (d.ctheta[a] != 0.f) d.axes |= 1 << a;
         d.memb = g.has_membranes;
+        if (g.d_dlt && !std::isinf(kap)) {
+            if (g.slab) return fail(c, LBMBT_EUNSUPPORTED, "membrane positions on a slab are not supported");
+            d.dlt = g.d_dlt;
+            d.lrho = (float)(kap * c->dt / (EPS_D * g.dx));
+        }
         div_magic((unsigned)g.nx, &d.div_m[0], &d.div_s[0]);
         div_magic((unsigned)g.ny, &d.div_m[1], &d.div_s[1]);
         if ((size_t)d.plane > max_plane) max_plane = d.plane;
@@ -1331,6 +1369,8 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
     if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
     if (c->geoms.empty() || c->n_phases == 0 || c->n_steps == 0) return fail(c, LBMBT_ESTATE, "set-up incomplete");
     if (any_slab(c)) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not run on slabs");
+    for (auto& g : c->geoms)
+        if (g.d_dlt) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not take membrane positions");
     const int ck = checkpoint_every > 0 ? checkpoint_every : 64;
     int rc = set_device(c);
     if (rc) return rc;

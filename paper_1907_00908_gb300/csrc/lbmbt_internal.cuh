@@ -65,6 +65,11 @@ struct MemberDesc {
     int zbc[2];           // BcMode of the low and high z face (bc[2] unless a slab)
     const float2* halo[2];  // slab halo planes (nx*ny complex64): hat g_5 of the
                           // plane below, hat g_6 of the plane above; or nullptr
+    // membrane positions on the links (theta = 0 rule, Eqs. B4a-B4c):
+    // dlt[(j-1)*plane + s] = distance in dx from s to the membrane on its
+    // link to s + e_j; nullptr = half-link rule (Eq. B5) everywhere
+    const float* dlt;
+    float lrho;           // kappa dt / (eps_D dx): the coefficients depend on it only
 };
 
 // Step control word in device memory.  The sweep reads k here; a one-block
@@ -91,6 +96,8 @@ struct SweepArgs {
     const double* F;              // F_k = sum_{m<k} f_m dt, per step
     double2* partial;             // per-tile (sum Re M, sum Im M)
     const float2* fac;            // [2][n_members][6] boundary factors, level k & 1
+    int links;                    // a member has membrane positions (register sweep
+                                  // variant with the Eqs. B4a-B4c rule)
 };
 
 // ---- launchers (sweep.cu) ------------------------------------------------

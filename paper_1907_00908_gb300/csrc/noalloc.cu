@@ -32,10 +32,10 @@ constexpr long long NA_MAX_TILES = NA_MAX_SITES / NA_TILE;
 // byte offsets inside the scratch array
 constexpr size_t OFF_CTL = 0;
 constexpr size_t OFF_DESC = 256;
-constexpr size_t OFF_TS = 512;
-constexpr size_t OFF_Z = 768;
-constexpr size_t OFF_FAC = 832;                      // [2][1][6] boundary factors
-constexpr size_t OFF_F64 = 1024;
+constexpr size_t OFF_TS = 768;
+constexpr size_t OFF_Z = 1024;
+constexpr size_t OFF_FAC = 1088;                     // [2][1][6] boundary factors
+constexpr size_t OFF_F64 = 1280;
 constexpr size_t OFF_F32 = OFF_F64 + NA_MAX_STEPS * sizeof(double);
 constexpr size_t OFF_FCUM = OFF_F32 + NA_MAX_STEPS * sizeof(float);
 constexpr size_t OFF_PART = (OFF_FCUM + (NA_MAX_STEPS + 1) * sizeof(double) + 255) / 256 * 256;
@@ -211,6 +211,7 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.partial = reinterpret_cast<double2*>(base + OFF_PART);
     float2* fac = reinterpret_cast<float2*>(base + OFF_FAC);
     a.fac = fac;
+    a.links = 0;
     MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
     const double* Fd = reinterpret_cast<const double*>(base + OFF_FCUM);
     // control word (done counter and step start from the values above every

@@ -88,7 +88,7 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
     }
 }
 
-template <int SPT>
+template <int SPT, bool LINKS>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 {
     __shared__ double2 s_red[32];
@@ -139,10 +139,30 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
         // s * (population streaming across), written A + s (B - A).
         // Bit (ibar - 1) marks the link to the upstream neighbour of i.
         if (mk & 0x3fu) {
+            const float* __restrict__ dlt = LINKS ? sd->dlt : nullptr;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ib = (i & 1) ? i + 1 : i - 1;
-                if (mk & (1u << (ib - 1))) g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
+                if (!(mk & (1u << (ib - 1)))) continue;
+                const float2 own = __ldg(src + (size_t)ib * P + s);
+                // membrane at a given position (Eqs. B4a-B4c) where the node
+                // behind s and the node beyond y stay in their compartments
+                if (LINKS && dlt != nullptr && !(mk & (1u << (i - 1)))) {
+                    const int a = (i - 1) >> 1, e = (i & 1) ? 1 : -1;
+                    const int c = a == 0 ? x : a == 1 ? y : z;
+                    const int dim = a == 0 ? nx : a == 1 ? ny : nz;
+                    const unsigned st = a == 0 ? 1u : a == 1 ? (unsigned)nx : sxy;
+                    const int bl = a == 0 ? bcx : a == 1 ? bcy : bcz0, bh = a == 0 ? bcx : a == 1 ? bcy : bcz1;
+                    const int cy = c - e;   // the far node y = s - e_i (a periodic wrap: a membrane never
+                                            // crosses a mirror face)
+                    const unsigned sy = (unsigned)((int)s + (cy < 0 ? dim - 1 : cy >= dim ? 1 - dim : -e) * (int)st);
+                    if (!(__ldg(mask + sy) & (1u << (ib - 1)))) {
+                        g[i] = link_rule(src, P, s, i, a, c, dim, st, bl, bh, fac, __ldg(dlt + (size_t)(ib - 1) * P + s),
+                                         sd->lrho, g[i], own, __ldg(src + (size_t)i * P + s));
+                        continue;
+                    }
+                }
+                g[i] = mix(own, g[i], sh);
             }
         }
 
@@ -282,9 +302,18 @@ cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int sp
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st)
 {
     switch (spt) {
-    case 1: sweep_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
-    case 2: sweep_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
-    case 4: sweep_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
+    case 1:
+        if (a.links) sweep_kernel<1, true><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        else sweep_kernel<1, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        break;
+    case 2:
+        if (a.links) sweep_kernel<2, true><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        else sweep_kernel<2, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        break;
+    case 4:
+        if (a.links) sweep_kernel<4, true><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        else sweep_kernel<4, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

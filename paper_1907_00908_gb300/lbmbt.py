@@ -33,7 +33,7 @@ EXPORTS = [
     "lbmbt_set_sequence", "lbmbt_pgse", "lbmbt_run", "lbmbt_run_batch", "lbmbt_grad",
     "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
     "lbmbt_launch_count", "lbmbt_sweep_noalloc", "lbmbt_set_geometry_slab", "lbmbt_slab_faces",
-    "lbmbt_slab_set_halos", "lbmbt_set_field",
+    "lbmbt_slab_set_halos", "lbmbt_set_field", "lbmbt_set_link_distances",
 ]
 
 
@@ -84,6 +84,7 @@ def lib():
                 "lbmbt_slab_faces": [P, I, P, P],
                 "lbmbt_slab_set_halos": [P, I, P, P],
                 "lbmbt_set_field": [P, P],
+                "lbmbt_set_link_distances": [P, I, P, I],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -243,6 +244,17 @@ class Solver:
 
     def add_geometry(self, labels, phase_of_label, dx, bc=(0, 0, 0)):
         return self.set_geometry(labels, phase_of_label, dx, bc, add=True)
+
+    def set_link_distances(self, delta, index=0):
+        """Membrane positions on the links (float32 [6, nz, ny, nx], numpy or
+        torch CUDA), or None to return to the half-link rule."""
+        if delta is None:
+            self._chk(self.L.lbmbt_set_link_distances(self.h, int(index), None, 0), "set_link_distances")
+            return
+        on_dev = hasattr(delta, "is_cuda") and delta.is_cuda
+        if not on_dev:
+            delta = np.ascontiguousarray(delta, np.float32)
+        self._chk(self.L.lbmbt_set_link_distances(self.h, int(index), _p(delta), int(on_dev)), "set_link_distances")
 
     def get_mask(self, index=0, shape=None):
         n = self.n_sites[index]
