@@ -66,6 +66,12 @@ def _load():
                 ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P,
                 P, P, P, P]
             lib.lbm_oracle_run_links.restype = ctypes.c_int
+            lib.lbm_oracle_run_ex.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                P, ctypes.c_int, P, P, ctypes.c_int, P, P,
+                ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P, ctypes.c_int,
+                P, P, P, P]
+            lib.lbm_oracle_run_ex.restype = ctypes.c_int
             lib.lbm_oracle_link_coefficients.argtypes = [ctypes.c_double] * 4 + [P, P]
             lib.lbm_oracle_link_coefficients.restype = None
             lib.lbm_oracle_mask.argtypes = [
@@ -140,7 +146,7 @@ def mask(labels, phase_of_label, bc):
 
 
 def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
-        want_field=False, want_series=False, want_state=False, threads=0, delta=None):
+        want_field=False, want_series=False, want_state=False, threads=0, delta=None, substeps=1):
     """Run the scheme from M = 1 to t = len(f)*dt.
 
     ``labels``: int32 [nz, ny, nx] compartment ids; ``phase_of_label``: phase
@@ -150,7 +156,9 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     ``series`` (complex [K], Z after each step) and ``state`` (complex
     [nz, ny, nx, 7]).  ``delta``: optional [6, nz, ny, nx] membrane positions
     on the links (distance in dx from the node along +x, -x, +y, -y, +z, -z),
-    which selects the theta = 0 rule of Eqs. B4a-B4c.
+    which selects the theta = 0 rule of Eqs. B4a-B4c.  ``substeps`` = k > 1:
+    k reaction steps of dt/k after each diffusion step (Sec. 2.3, dt = k dt'),
+    ``f`` then sampled on the dt/k grid (len(f) = k * number of steps).
     """
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     nz, ny, nx = labels.shape
@@ -161,12 +169,20 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     T2v = np.ascontiguousarray(np.atleast_1d(T2), dtype=np.float64)
     fv = np.ascontiguousarray(f, dtype=np.float64)
     gv = np.ascontiguousarray(gG, dtype=np.float64)
-    K = fv.size
+    if fv.size % substeps:
+        raise ValueError("len(f) must be a multiple of substeps")
+    K = fv.size // substeps
     Z = np.zeros(2)
     field = np.empty(2 * N) if want_field else None
     series = np.empty(2 * K) if want_series else None
     state = np.empty(2 * 7 * N) if want_state else None
-    if delta is None:
+    if substeps != 1:
+        dl = None if delta is None else np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(6, N).T)
+        rc = _load().lbm_oracle_run_ex(
+            nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
+            int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
+            int(threads), _ptr(dl), int(substeps), _ptr(Z), _ptr(field), _ptr(series), _ptr(state))
+    elif delta is None:
         rc = _load().lbm_oracle_run(
             nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
             int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),

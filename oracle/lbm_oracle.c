@@ -208,10 +208,10 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
                     const int* bc, int n_phases, const double* D, const double* T2,
                     double kappa, double dt, long n_steps, const double* f,
-                    const double* gG, int n_threads, const double* delta,
+                    const double* gG, int n_threads, const double* delta, int substeps,
                     double* Z_out, double* field_out, double* series_out, double* state_out)
 {
-    if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0) return -1;
+    if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0 || substeps < 1) return -1;
     if (n_phases < 1 || n_phases > 4) return -1;
     for (int a = 0; a < 3; ++a)
         if (bc[a] != BC_PERIODIC && bc[a] != BC_MIRROR) return -1;
@@ -244,7 +244,7 @@ static int run_impl(int nx, int ny, int nz, double dx,
     for (int p = 0; p < n_phases; ++p) {
         if (!(D[p] > 0.0)) return -1;
         tau[p] = tau_of(D[p], dt, dx);
-        decay[p] = exp(-dt / T2[p]); /* T2 = inf -> 1 */
+        decay[p] = exp(-dt / substeps / T2[p]); /* per reaction sub-step; T2 = inf -> 1 */
     }
     double r, s;
     membrane_shares(kappa, dt, dx, &r, &s);
@@ -360,8 +360,10 @@ static int run_impl(int nx, int ny, int nz, double dx,
          *    B2b_text with the B5 coefficients): the population arriving at x
          *    in direction i is s * (what streams in) + r * (what x sent out
          *    towards the membrane, reflected). */
-        /* 4. Reaction (Eq. reaction_LBM), x_n = n dx. */
-        double fk = f[k];
+        /* 4. Reaction (Eq. reaction_LBM), x_n = n dx, as `substeps` reaction
+         *    steps of dt' = dt / substeps after the one diffusion step
+         *    (Sec. 2.3: dt = k dt'), waveform sampled at the start of each. */
+        const double dts = dt / substeps;
 #pragma omp parallel for
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
@@ -394,10 +396,13 @@ static int run_impl(int nx, int ny, int nz, double dx,
                         }
                     }
                     double xdotG = (x * dx) * gG[0] + (y * dx) * gG[1] + (z * dx) * gG[2];
-                    cplx fac = cexp(-I * xdotG * fk * dt) * decay[ph[si]];
-                    for (int i = 0; i < Q; ++i) gs[si * Q + i] = fac * gbar[i];
+                    for (int j = 0; j < substeps; ++j) {
+                        cplx fac = cexp(-I * xdotG * f[k * substeps + j] * dts) * decay[ph[si]];
+                        for (int i = 0; i < Q; ++i) gbar[i] = fac * gbar[i];
+                    }
+                    for (int i = 0; i < Q; ++i) gs[si * Q + i] = gbar[i];
                 }
-        F += fk * dt;
+        for (int j = 0; j < substeps; ++j) F += f[k * substeps + j] * dts;
 
         if (series_out) {
             cplx Z = 0;
@@ -434,7 +439,7 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
                    double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, NULL, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, NULL, 1, Z_out, field_out, series_out, state_out);
 }
 
 /*
@@ -453,5 +458,22 @@ int lbm_oracle_run_links(int nx, int ny, int nz, double dx,
 {
     if (!delta) return -1;
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, 1, Z_out, field_out, series_out, state_out);
+}
+
+/*
+ * General form: optional membrane positions (as lbm_oracle_run_links, or
+ * NULL) and `substeps` >= 1 reaction steps of dt / substeps after each
+ * diffusion step (Sec. 2.3, dt = k dt'); f then holds n_steps * substeps
+ * samples on the dt' grid.
+ */
+int lbm_oracle_run_ex(int nx, int ny, int nz, double dx,
+                      const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
+                      const int* bc, int n_phases, const double* D, const double* T2,
+                      double kappa, double dt, long n_steps, const double* f,
+                      const double* gG, int n_threads, const double* delta, int substeps,
+                      double* Z_out, double* field_out, double* series_out, double* state_out)
+{
+    return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
+                    gG, n_threads, delta, substeps, Z_out, field_out, series_out, state_out);
 }
