@@ -181,6 +181,15 @@ int lbmbt_set_permeability(lbmbt_ctx* ctx, double kappa_um_ms);
 int lbmbt_set_sequence(lbmbt_ctx* ctx, double dt_ms, int64_t n_steps, const double* f,
                        const double gamma_G0[3]);
 
+/* Sequence with reaction sub-steps (Sec. 2.3: dt = k dt', one diffusion step
+ * then k reaction steps): f_fine (host, n_steps * substeps values) samples
+ * the waveform on the dt' = dt / substeps grid.  The k reaction factors of a
+ * site commute, so the library applies one reaction per step with the mean
+ * of the step's k samples (and the same F_k); substeps = 1 is
+ * lbmbt_set_sequence.  Errors as lbmbt_set_sequence, EINVAL for substeps < 1. */
+int lbmbt_set_sequence_substeps(lbmbt_ctx* ctx, double dt_ms, int64_t n_steps, int substeps,
+                                const double* f_fine, const double gamma_G0[3]);
+
 /* PGSE helper (Sec. 2.1, Fig. 2): from b (s/mm^2), delta, Delta, dt and a
  * direction, gamma_G0_out = sqrt(b/(delta^2 (Delta - delta/3))) * unit(dir)
  * and the effective waveform sampled at t^k = k dt: +1 on [0, delta), -1 on

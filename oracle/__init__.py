@@ -69,7 +69,7 @@ def _load():
             lib.lbm_oracle_run_ex.argtypes = [
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                 P, ctypes.c_int, P, P, ctypes.c_int, P, P,
-                ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P, ctypes.c_int,
+                ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                 P, P, P, P]
             lib.lbm_oracle_run_ex.restype = ctypes.c_int
             lib.lbm_oracle_link_coefficients.argtypes = [ctypes.c_double] * 4 + [P, P]
@@ -146,7 +146,8 @@ def mask(labels, phase_of_label, bc):
 
 
 def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
-        want_field=False, want_series=False, want_state=False, threads=0, delta=None, substeps=1):
+        want_field=False, want_series=False, want_state=False, threads=0, delta=None, substeps=1,
+        lattice="D3Q7"):
     """Run the scheme from M = 1 to t = len(f)*dt.
 
     ``labels``: int32 [nz, ny, nx] compartment ids; ``phase_of_label``: phase
@@ -159,6 +160,7 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     which selects the theta = 0 rule of Eqs. B4a-B4c.  ``substeps`` = k > 1:
     k reaction steps of dt/k after each diffusion step (Sec. 2.3, dt = k dt'),
     ``f`` then sampled on the dt/k grid (len(f) = k * number of steps).
+    ``lattice`` = "D2Q5": the 2-D lattice of Sec. 2.3 (eps_D = 1/3, nz = 1).
     """
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     nz, ny, nx = labels.shape
@@ -176,12 +178,15 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     field = np.empty(2 * N) if want_field else None
     series = np.empty(2 * K) if want_series else None
     state = np.empty(2 * 7 * N) if want_state else None
-    if substeps != 1:
+    if lattice not in ("D3Q7", "D2Q5"):
+        raise ValueError("lattice must be D3Q7 or D2Q5")
+    if substeps != 1 or lattice == "D2Q5":
         dl = None if delta is None else np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(6, N).T)
         rc = _load().lbm_oracle_run_ex(
             nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
             int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
-            int(threads), _ptr(dl), int(substeps), _ptr(Z), _ptr(field), _ptr(series), _ptr(state))
+            int(threads), _ptr(dl), int(substeps), int(lattice == "D2Q5"), _ptr(Z), _ptr(field), _ptr(series),
+            _ptr(state))
     elif delta is None:
         rc = _load().lbm_oracle_run(
             nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),

@@ -47,6 +47,11 @@ static const int OPP[Q] = {0, 2, 1, 4, 3, 6, 5};
 /* D3Q7: eps_D = 1/4, omega_0 = eps_D, omega_i = eps_D / 2 (Sec. 2.3 weights) */
 static const double EPS_D = 0.25;
 static const double W[Q] = {0.25, 0.125, 0.125, 0.125, 0.125, 0.125, 0.125};
+/* D2Q5 (Sec. 2.3, Eq. omega_i): directions 0, +x, -x, +y, -y (the first five
+ * above), eps_D = 1/3, omega_0 = eps_D, omega_1..4 = eps_D / 2; the grid has
+ * one z plane and the z populations are not used. */
+static const double EPS_D2 = 1.0 / 3.0;
+static const double W2[Q] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 0.0, 0.0};
 
 enum { BC_PERIODIC = 0, BC_MIRROR = 1 };
 
@@ -81,19 +86,19 @@ static size_t sidx(const grid_t* g, int x, int y, int z)
 }
 
 /* Eq. tau_def: tau = 1/2 + dt*D / (eps_D dx^2). */
-static double tau_of(double D, double dt, double dx)
+static double tau_of(double D, double dt, double dx, double eps)
 {
-    return 0.5 + dt * D / (EPS_D * dx * dx);
+    return 0.5 + dt * D / (eps * dx * dx);
 }
 
 /* Eqs. P_def and B5: P = eps_D dx / (2 kappa dt); reflected share r = P/(1+P),
  * transmitted share s = 1/(1+P).  kappa = 0 -> P = inf (bounce-back);
  * kappa = inf -> P = 0 (plain streaming). */
-static void membrane_shares(double kappa, double dt, double dx, double* r, double* s)
+static void membrane_shares(double kappa, double dt, double dx, double eps, double* r, double* s)
 {
     if (kappa == 0.0) { *r = 1.0; *s = 0.0; return; }
     if (isinf(kappa)) { *r = 0.0; *s = 1.0; return; }
-    double P = EPS_D * dx / (2.0 * kappa * dt);
+    double P = eps * dx / (2.0 * kappa * dt);
     *r = P / (1.0 + P);
     *s = 1.0 / (1.0 + P);
 }
@@ -125,14 +130,14 @@ static void coef_d(double d, double c[4])
     c[3] = (3.0 - 2.0 * d) / (2.0 * d + 1.0);
 }
 
-void lbm_oracle_link_coefficients(double dl, double kappa, double dt, double dx, double* A, double* B)
+static void link_coefficients(double dl, double kappa, double dt, double dx, double eps, double* A, double* B)
 {
     double cn[4], cd[4], cns[4], cds[4];
     coef_n(dl, cn);
     coef_d(dl, cd);
     coef_n(1.0 - dl, cns);
     coef_d(1.0 - dl, cds);
-    const double ex = EPS_D * dx, kd = kappa * dt;
+    const double ex = eps * dx, kd = kappa * dt;
     const double F = cd[3] * cds[3] * ex + (cd[3] * cns[3] + cn[3] * cds[3]) * kd;
     for (int j = 0; j < 3; ++j) {
         A[j] = (cd[3] * cds[3] * cn[j] * ex + (cds[3] * cn[3] * cd[j] + cns[3] * cd[3] * cn[j]) * kd) / F;
@@ -140,11 +145,16 @@ void lbm_oracle_link_coefficients(double dl, double kappa, double dt, double dx,
     }
 }
 
+void lbm_oracle_link_coefficients(double dl, double kappa, double dt, double dx, double* A, double* B)
+{
+    link_coefficients(dl, kappa, dt, dx, EPS_D, A, B);
+}
+
 /* Scalar parameters as the oracle derives them: out = {tau, r, s}. */
 void lbm_oracle_params(double D, double dt, double dx, double kappa, double* out)
 {
-    out[0] = tau_of(D, dt, dx);
-    membrane_shares(kappa, dt, dx, &out[1], &out[2]);
+    out[0] = tau_of(D, dt, dx, EPS_D);
+    membrane_shares(kappa, dt, dx, EPS_D, &out[1], &out[2]);
 }
 
 /*
@@ -208,10 +218,14 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
                     const int* bc, int n_phases, const double* D, const double* T2,
                     double kappa, double dt, long n_steps, const double* f,
-                    const double* gG, int n_threads, const double* delta, int substeps,
+                    const double* gG, int n_threads, const double* delta, int substeps, int d2q5,
                     double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0 || substeps < 1) return -1;
+    if (d2q5 && nz != 1) return -1;
+    const int nq = d2q5 ? 5 : Q;                  /* populations in use */
+    const double eps = d2q5 ? EPS_D2 : EPS_D;
+    const double* w = d2q5 ? W2 : W;
     if (n_phases < 1 || n_phases > 4) return -1;
     for (int a = 0; a < 3; ++a)
         if (bc[a] != BC_PERIODIC && bc[a] != BC_MIRROR) return -1;
@@ -243,11 +257,11 @@ static int run_impl(int nx, int ny, int nz, double dx,
     double tau[4], decay[4];
     for (int p = 0; p < n_phases; ++p) {
         if (!(D[p] > 0.0)) return -1;
-        tau[p] = tau_of(D[p], dt, dx);
+        tau[p] = tau_of(D[p], dt, dx, eps);
         decay[p] = exp(-dt / substeps / T2[p]); /* per reaction sub-step; T2 = inf -> 1 */
     }
     double r, s;
-    membrane_shares(kappa, dt, dx, &r, &s);
+    membrane_shares(kappa, dt, dx, eps, &r, &s);
     if (delta)
         for (size_t i = 0; i < 6 * N; ++i)
             if (!(delta[i] > 0.0 && delta[i] < 1.0)) return -1;
@@ -293,7 +307,7 @@ static int run_impl(int nx, int ny, int nz, double dx,
 
     /* Initial condition M = 1 + 0i at equilibrium: g_i = omega_i M (Eq. g_eq). */
     for (size_t x = 0; x < N; ++x)
-        for (int i = 0; i < Q; ++i) gs[x * Q + i] = W[i];
+        for (int i = 0; i < Q; ++i) gs[x * Q + i] = w[i];   /* D2Q5: the z populations stay 0 */
 
     double F = 0.0; /* F_k = sum_{m<k} f_m dt */
     for (long k = 0; k < n_steps; ++k) {
@@ -304,11 +318,11 @@ static int run_impl(int nx, int ny, int nz, double dx,
                 for (int x = 0; x < nx; ++x) {
                     size_t si = sidx(&g, x, y, z), pi = pidx(&g, x, y, z);
                     cplx M = 0;
-                    for (int i = 0; i < Q; ++i) M += gs[si * Q + i];
+                    for (int i = 0; i < nq; ++i) M += gs[si * Q + i];
                     double t = tau[ph[si]];
-                    for (int i = 0; i < Q; ++i) {
+                    for (int i = 0; i < nq; ++i) {
                         cplx gi = gs[si * Q + i];
-                        gh[pi * Q + i] = gi - (gi - W[i] * M) / t;
+                        gh[pi * Q + i] = gi - (gi - w[i] * M) / t;
                     }
                 }
 
@@ -337,7 +351,7 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     lo[o2] = hi[o2] = c0[o2] = cN[o2] = u;
                     size_t plo = pidx(&g, lo[0], lo[1], lo[2]), phi_ = pidx(&g, hi[0], hi[1], hi[2]);
                     size_t p0 = pidx(&g, c0[0], c0[1], c0[2]), pN = pidx(&g, cN[0], cN[1], cN[2]);
-                    for (int i = 0; i < Q; ++i) {
+                    for (int i = 0; i < nq; ++i) {
                         if (bc[a] == BC_PERIODIC) {
                             gh[plo * Q + i] = wrap_lo * gh[pN * Q + i];
                             gh[phi_ * Q + i] = wrap_hi * gh[p0 * Q + i];
@@ -372,7 +386,7 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     int Lx = lab[pi];
                     cplx gbar[Q];
                     gbar[0] = gh[pi * Q + 0];
-                    for (int i = 1; i < Q; ++i) {
+                    for (int i = 1; i < nq; ++i) {
                         size_t py_ = pidx(&g, x - EX[i], y - EY[i], z - EZ[i]);
                         if (lab[py_] == Lx) {
                             gbar[i] = gh[py_ * Q + i];
@@ -388,7 +402,7 @@ static int run_impl(int nx, int ny, int nz, double dx,
                         size_t pe = pidx(&g, x - 2 * EX[i], y - 2 * EY[i], z - 2 * EZ[i]);
                         if (delta && !isinf(kappa) && lab[pb] == Lx && lab[pe] == lab[py_]) {
                             double A[3], B[3];
-                            lbm_oracle_link_coefficients(delta[si * 6 + (ib - 1)], kappa, dt, dx, A, B);
+                            link_coefficients(delta[si * 6 + (ib - 1)], kappa, dt, dx, eps, A, B);
                             gbar[i] = A[0] * gh[pi * Q + ib] + A[1] * gh[pb * Q + ib] + A[2] * gh[pi * Q + i] +
                                       B[0] * gh[py_ * Q + i] + B[1] * gh[pe * Q + i] + B[2] * gh[py_ * Q + ib];
                         } else {
@@ -398,9 +412,9 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     double xdotG = (x * dx) * gG[0] + (y * dx) * gG[1] + (z * dx) * gG[2];
                     for (int j = 0; j < substeps; ++j) {
                         cplx fac = cexp(-I * xdotG * f[k * substeps + j] * dts) * decay[ph[si]];
-                        for (int i = 0; i < Q; ++i) gbar[i] = fac * gbar[i];
+                        for (int i = 0; i < nq; ++i) gbar[i] = fac * gbar[i];
                     }
-                    for (int i = 0; i < Q; ++i) gs[si * Q + i] = gbar[i];
+                    for (int i = 0; i < nq; ++i) gs[si * Q + i] = gbar[i];
                 }
         for (int j = 0; j < substeps; ++j) F += f[k * substeps + j] * dts;
 
@@ -439,7 +453,7 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
                    double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, NULL, 1, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, NULL, 1, 0, Z_out, field_out, series_out, state_out);
 }
 
 /*
@@ -458,22 +472,23 @@ int lbm_oracle_run_links(int nx, int ny, int nz, double dx,
 {
     if (!delta) return -1;
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, 1, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, 1, 0, Z_out, field_out, series_out, state_out);
 }
 
 /*
  * General form: optional membrane positions (as lbm_oracle_run_links, or
- * NULL) and `substeps` >= 1 reaction steps of dt / substeps after each
- * diffusion step (Sec. 2.3, dt = k dt'); f then holds n_steps * substeps
- * samples on the dt' grid.
+ * NULL), `substeps` >= 1 reaction steps of dt / substeps after each
+ * diffusion step (Sec. 2.3, dt = k dt'; f then holds n_steps * substeps
+ * samples on the dt' grid), and d2q5 != 0 for the 2-D D2Q5 lattice of
+ * Sec. 2.3 (nz = 1).
  */
 int lbm_oracle_run_ex(int nx, int ny, int nz, double dx,
                       const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
                       const int* bc, int n_phases, const double* D, const double* T2,
                       double kappa, double dt, long n_steps, const double* f,
-                      const double* gG, int n_threads, const double* delta, int substeps,
+                      const double* gG, int n_threads, const double* delta, int substeps, int d2q5,
                       double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, substeps, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, substeps, d2q5, Z_out, field_out, series_out, state_out);
 }

@@ -537,6 +537,27 @@ extern "C" int lbmbt_set_sequence(lbmbt_ctx* c, double dt, int64_t n_steps, cons
     return sync(c);
 }
 
+// Reaction sub-steps (Sec. 2.3, dt = k dt'): k reaction steps of dt' after
+// each diffusion step.  The reaction factors of one site are scalars that
+// commute, so the k sub-steps equal one reaction with the step-mean waveform
+// exp(-i gamma x.G0 dt' sum_j f_j) (the T2 factors multiply to exp(-dt/T2)),
+// and F_k = sum f dt' is unchanged: the sequence becomes the step means.
+extern "C" int lbmbt_set_sequence_substeps(lbmbt_ctx* c, double dt, int64_t n_steps, int substeps,
+                                           const double* f_fine, const double gG[3])
+{
+    if (!c) return LBMBT_EINVAL;
+    if (substeps < 1) return fail(c, LBMBT_EINVAL, "substeps must be >= 1");
+    if (!f_fine) return fail(c, LBMBT_EINVAL, "f missing");
+    if (n_steps < 1 || n_steps > (1LL << 30) / substeps) return fail(c, LBMBT_EINVAL, "n_steps out of range");
+    std::vector<double> fm(n_steps);
+    for (long long k = 0; k < n_steps; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j < substeps; ++j) acc += f_fine[k * substeps + j];
+        fm[k] = acc / substeps;
+    }
+    return lbmbt_set_sequence(c, dt, n_steps, fm.data(), gG);
+}
+
 extern "C" int lbmbt_pgse(double b, double delta, double Delta, double dt, const double dir[3], double gG_out[3],
                           int64_t* n_steps_out, double* f_out)
 {

@@ -33,7 +33,7 @@ EXPORTS = [
     "lbmbt_set_sequence", "lbmbt_pgse", "lbmbt_run", "lbmbt_run_batch", "lbmbt_grad",
     "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
     "lbmbt_launch_count", "lbmbt_sweep_noalloc", "lbmbt_set_geometry_slab", "lbmbt_slab_faces",
-    "lbmbt_slab_set_halos", "lbmbt_set_field", "lbmbt_set_link_distances",
+    "lbmbt_slab_set_halos", "lbmbt_set_field", "lbmbt_set_link_distances", "lbmbt_set_sequence_substeps",
 ]
 
 
@@ -85,6 +85,7 @@ def lib():
                 "lbmbt_slab_set_halos": [P, I, P, P],
                 "lbmbt_set_field": [P, P],
                 "lbmbt_set_link_distances": [P, I, P, I],
+                "lbmbt_set_sequence_substeps": [P, D, I64, I, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -276,6 +277,17 @@ class Solver:
         gv = np.ascontiguousarray(gG, np.float64)
         self._chk(self.L.lbmbt_set_sequence(self.h, float(dt), int(fv.size), _p(fv), _p(gv)), "set_sequence")
         self.n_steps = int(fv.size)
+
+    def set_sequence_substeps(self, dt, f_fine, gG, substeps):
+        """Waveform sampled on the dt/substeps grid (Sec. 2.3, dt = k dt')."""
+        fv = np.ascontiguousarray(f_fine, np.float64)
+        gv = np.ascontiguousarray(gG, np.float64)
+        if fv.size % substeps:
+            raise ValueError("len(f_fine) must be a multiple of substeps")
+        n = fv.size // substeps
+        self._chk(self.L.lbmbt_set_sequence_substeps(self.h, float(dt), int(n), int(substeps), _p(fv), _p(gv)),
+                  "set_sequence_substeps")
+        self.n_steps = n
 
     def set_option(self, opt, value):
         self._chk(self.L.lbmbt_set_option(self.h, int(opt), int(value)), "set_option")

@@ -29,29 +29,37 @@ WTS = np.array([0.25] + [0.125] * 6)
 EPS = 0.25
 
 
-def tau(D, dt, dx):
-    return 0.5 + dt * D / (EPS * dx * dx)
+# D2Q5 (Sec. 2.3): eps_D = 1/3, w0 = 1/3, w_i = 1/6
+E2 = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0]])
+WTS2 = np.array([1 / 3] + [1 / 6] * 4)
+EPS2 = 1 / 3
+
+
+def tau(D, dt, dx, eps=EPS):
+    return 0.5 + dt * D / (eps * dx * dx)
 
 
 # ---------------------------------------------------------------- plane wave
-def planewave_signal(n, dx, D, T2, dt, f, gG, series=False):
+def planewave_signal(n, dx, D, T2, dt, f, gG, series=False, lattice="D3Q7"):
     """S(t^K) (and optionally Z(t^k)/N for all k) of a uniform periodic n^3 box.
 
     State g_i(x) = a_i exp(-i kv.x).  Collision acts on a; streaming from
     x - e_i dx multiplies a_i by exp(+i kv.e_i dx); the reaction adds
-    gG f_k dt to kv and damps by exp(-dt/T2).
+    gG f_k dt to kv and damps by exp(-dt/T2).  ``lattice`` = "D2Q5": the
+    five-velocity 2-D set (the box then has one z plane).
     """
     nxyz = np.array([n, n, n]) if np.isscalar(n) else np.array(n)
-    om = 1.0 / tau(D, dt, dx)
+    Ev, Wv, eps = (E, WTS, EPS) if lattice == "D3Q7" else (E2, WTS2, EPS2)
+    om = 1.0 / tau(D, dt, dx, eps)
     dec = math.exp(-dt / T2)
-    a = WTS.astype(np.complex128).copy()
+    a = Wv.astype(np.complex128).copy()
     kv = np.zeros(3)
     gG = np.asarray(gG, float)
     out = []
     for fk in f:
         M = a.sum()
-        a = a - om * (a - WTS * M)
-        a = a * np.exp(1j * (E @ kv) * dx)
+        a = a - om * (a - Wv * M)
+        a = a * np.exp(1j * (Ev @ kv) * dx)
         kv = kv + gG * fk * dt
         a = a * dec
         if series:

@@ -452,3 +452,33 @@ def test_full_schedule_tissue_25600_steps(lb, direction):
     s.close()
     o = _oracle(geom, (1, 1, 1), bench.D, bench.T2, bench.KAPPA, bench.DT, f, gG)
     assert abs(r["S"] - o["S"]) <= S_TOL * o["S"], (r["S"], o["S"])
+
+
+# ------------------------------------------------------- reaction sub-steps
+@pytest.mark.parametrize("bc, gdir", [((0, 0, 0), (0.6, 0.0, 0.8)), ((1, 1, 1), (0.0, 0.0, 1.0))])
+def test_reaction_substeps_match_oracle(lb, bc, gdir):
+    """dt = k dt' (Sec. 2.3): a fine waveform (a sine-modulated gradient plus
+    a PGSE whose edges fall inside diffusion steps) through
+    lbmbt_set_sequence_substeps against the oracle's literal k reaction
+    sub-steps."""
+    geom = synth.cylinders(32, 0.5, seed=4) if bc == (0, 0, 0) else synth.crop(synth.voronoi_tissue(48, 0.5, seed=3), 32)
+    n_ph = int(geom.phase_of_label.max()) + 1
+    D, T2 = [2.0, 1.0, 1.5][:n_ph], [80.0, 50.0, 60.0][:n_ph]
+    dt, k = 0.02, 3
+    K = 90
+    t = (np.arange(K * k) + 0.5) * dt / k
+    f_fine = np.sin(2 * np.pi * t / 0.9)
+    f_fine[(t > 0.55) & (t < 0.61)] = 1.0
+    gG = 0.08 * np.asarray(gdir) / np.linalg.norm(gdir)
+    s = lb.Solver(0)
+    s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, bc)
+    s.set_phases(D, T2)
+    s.set_permeability(0.03)
+    s.set_sequence_substeps(dt, f_fine, gG, k)
+    fld = torch.zeros(geom.n_sites, dtype=torch.complex64, device="cuda")
+    r = s.run(field=fld)
+    torch.cuda.synchronize()
+    s.close()
+    o = _oracle(geom, bc, D, T2, 0.03, dt, f_fine, gG, want_field=True, substeps=k)
+    assert abs(r["S"] - o["S"]) <= S_TOL * o["S"]
+    assert _field_err(fld.cpu().numpy().reshape(geom.shape), o["field"]) < FIELD_TOL
