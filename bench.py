@@ -394,6 +394,74 @@ def run_links(args):
     return 0
 
 
+# ---------------------------------------------------------------- scheme variants
+def run_variants(args):
+    """The paper's cheap variants, each timed against its plain counterpart:
+    the 2-D D2Q5 lattice (Sec. 2.3) on a 4096^2 cell pattern, and reaction
+    sub-steps (dt = 4 dt', an OGSE-like sine waveform, so every step takes
+    the general rotation) on the 256^3 cylinders."""
+    import torch
+    from paper_1907_00908_gb300 import lbmbt, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def timed(s, n_sites, members, steps):
+        s.set_option(lbmbt.OPT_AUTOTUNE, 1)
+        s.prepare(members)
+        s.advance(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        return {"MLUPS": n_sites * len(members) / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                "kernel": "bulk-copy" if s.get_option(lbmbt.OPT_KERNEL_USED) == 2 else "register"}
+
+    # D2Q5 vs D3Q7 on the same one-plane grid (cells of ~10 um in a 1 mm square)
+    n2 = 4096
+    cell = 40
+    lab = (np.arange(n2)[:, None] // cell * (n2 // cell) + np.arange(n2)[None, :] // cell).astype(np.int64)
+    lab = (lab * 2654435761 % 97).astype(np.int32)[None]   # neighbouring cells get different labels
+    pol = (np.arange(97) % 2).astype(np.uint8)
+    gG, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, 0.005, (1, 1, 0))
+    mem = lbmbt.Solver.members([gG], 0, C2_KAPPA)
+    for lat in (1, 0):
+        s = lbmbt.Solver(0, stream)
+        s.set_option(lbmbt.OPT_LATTICE, lat)
+        s.set_geometry(lab, pol, 0.25, (0, 0, 0))
+        s.set_phases(C2_D, C2_T2)
+        s.set_sequence(0.005, f, gG)
+        out["D2Q5_4096sq" if lat else "D3Q7_same_grid"] = timed(s, lab.size, mem, args.steps)
+        s.close()
+    # reaction sub-steps on the cylinders
+    geom = synth.cylinders(256, 0.25, seed=1)
+    dt, k, K = 0.0015625, 4, 2000
+    t = (np.arange(K * k) + 0.5) * dt / k
+    f_fine = np.sin(2 * np.pi * t / 1.0)
+    gG3 = [0.2 * np.asarray(d, float) / np.linalg.norm(d) for d in ((1, 0, 0), (0, 1, 0), (1, 1, 1))]
+    mem3 = lbmbt.Solver.members(gG3, 0, C2_KAPPA)
+    for name, sub in (("substeps4_sine", k), ("pgse_one_reaction", 1)):
+        s = lbmbt.Solver(0, stream)
+        s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, (0, 0, 0))
+        s.set_phases(C2_D, C2_T2)
+        if sub > 1:
+            s.set_sequence_substeps(dt, f_fine, gG3[0], sub)
+        else:
+            _, fp = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, dt, (1, 0, 0))
+            s.set_sequence(dt, fp, gG3[0])
+        out[name] = timed(s, geom.n_sites, mem3, args.steps)
+        s.close()
+    line = {"metric": "MLUPS (scheme variants, FP32)", "value": out["D2Q5_4096sq"]["MLUPS"], "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "variants_d2q5_4096sq_and_substeps_cyl256"}, "compare": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- slabs (strips)
 def run_slab(args):
     """The 512^3 tissue batch cut into z slabs on one GPU (one context per
@@ -471,11 +539,12 @@ def main():
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
     ap.add_argument("--slabs", type=int, default=4, help="slab workload: number of z slabs")
-    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint", "slab", "links"],
+    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint", "slab", "links", "variants"],
                     help="tissue512 (default): the 512^3 tissue batch of 3 directions; batch: 528 members on "
                          "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack; slab: the "
                          "tissue batch cut into --slabs z slabs with a face exchange per step; links: membranes at "
-                         "their exact positions on the links (256^3 cylinders) against the half-link rule")
+                         "their exact positions on the links (256^3 cylinders) against the half-link rule; variants: "
+                         "D2Q5 and reaction sub-steps against their plain counterparts")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -487,6 +556,8 @@ def main():
         return run_slab(args)
     if args.workload == "links":
         return run_links(args)
+    if args.workload == "variants":
+        return run_variants(args)
 
     import torch
     import torch.distributed as dist

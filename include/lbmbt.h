@@ -259,8 +259,14 @@ enum {
                                 3 = 352 x 3 (default)                         */
     LBMBT_OPT_ADJOINT_KERNEL = 9, /* 0 (default) auto, 1 register adjoint sweep,
                                 2 bulk-copy adjoint sweep (nx % 16 == 0, nx <= 512) */
-    LBMBT_OPT_ADJOINT_SHAPE = 10 /* bulk-copy adjoint consumers x sites per thread:
+    LBMBT_OPT_ADJOINT_SHAPE = 10, /* bulk-copy adjoint consumers x sites per thread:
                                 0 = 256 x 2, 1 = 512 x 1 (default)              */
+    LBMBT_OPT_LATTICE = 11   /* 0 (default) D3Q7; 1 the 2-D D2Q5 lattice of
+                                Sec. 2.3 (eps_D = 1/3, omega_0 = 1/3,
+                                omega_1..4 = 1/6; tau, P and the membrane
+                                coefficients use eps_D = 1/3) on geometries of
+                                one z plane, register sweep only; the adjoint
+                                returns EUNSUPPORTED                           */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

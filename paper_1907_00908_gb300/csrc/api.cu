@@ -83,6 +83,7 @@ struct lbmbt_ctx {
     bool adj_tma_ok = false;
     int adj_cap = 0;
     int adjoint_opt = 0;          // 0 auto, 1 register adjoint, 2 bulk-copy adjoint
+    int lattice = 0;              // 0 D3Q7, 1 D2Q5 (Sec. 2.3; grids of one z plane)
     int adj_shape = 1;            // bulk-copy adjoint consumer shape (16 warps x 1 site)
     bool use_tma = false;
     int tma_cap = 0;
@@ -588,6 +589,7 @@ static constexpr int TMA_MAX_CAP = 1024;
 
 static bool tma_eligible(const lbmbt_ctx* c)
 {
+    if (c->lattice != 0) return false;   // the bulk-copy sweep has the D3Q7 weights built in
     for (auto& d : c->descs)
         if (d.nx % 16 != 0 || d.nx > TMA_MAX_CAP || d.dlt != nullptr) return false;
     return true;
@@ -678,6 +680,8 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.links = 0;
     for (auto& d : c->descs)
         if (d.dlt) a.links = 1;
+    if (c->lattice == 1) { a.w0 = 1.f / 3.f; a.wxy = 1.f / 6.f; a.wz = 0.f; }
+    else { a.w0 = W0; a.wxy = WI; a.wz = WI; }
     return a;
 }
 
@@ -847,15 +851,19 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
             d.zbc[h] = (!g.slab || g.zkind[h] == LBMBT_FACE_OWN) ? d.bc[2]
                        : g.zkind[h] == LBMBT_FACE_HALO          ? BC_HALO
                                                                 : BC_HALO_PER;
+        const double eps = c->lattice == 1 ? EPS_D2 : EPS_D;
+        if (c->lattice == 1 && (g.nz != 1 || g.slab))
+            return fail(c, LBMBT_EINVAL, "the D2Q5 lattice needs geometries of one z plane (geometry %d has %d)",
+                        mm.geometry, g.nz);
         for (int p = 0; p < 4; ++p) {
-            const double tau = 0.5 + c->dt * c->D[p] / (EPS_D * g.dx * g.dx);   // Eq. tau_def
+            const double tau = 0.5 + c->dt * c->D[p] / (eps * g.dx * g.dx);   // Eq. tau_def
             if (p < c->n_phases && !(tau > 0.5))
                 return fail(c, LBMBT_EUNSTABLE, "phase %d: tau = %.17g <= 1/2", p, tau);
             d.omega[p] = (float)(1.0 / tau);
             d.eps[p] = std::isinf(c->T2[p]) ? 0.f : (float)(-std::expm1(-c->dt / c->T2[p]));
         }
         const double kap = mm.kappa_um_ms;
-        const double cP = EPS_D * g.dx / (2.0 * c->dt);   // P = cP / kappa  (Eq. P_def)
+        const double cP = eps * g.dx / (2.0 * c->dt);   // P = cP / kappa  (Eq. P_def)
         d.s_share = std::isinf(kap) ? 1.f : (float)(kap / (kap + cP));
         d.axes = 0;
         for (int a = 0; a < 3; ++a)
@@ -864,7 +872,7 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         if (g.d_dlt && !std::isinf(kap)) {
             if (g.slab) return fail(c, LBMBT_EUNSUPPORTED, "membrane positions on a slab are not supported");
             d.dlt = g.d_dlt;
-            d.lrho = (float)(kap * c->dt / (EPS_D * g.dx));
+            d.lrho = (float)(kap * c->dt / (eps * g.dx));
         }
         div_magic((unsigned)g.nx, &d.div_m[0], &d.div_s[0]);
         div_magic((unsigned)g.ny, &d.div_m[1], &d.div_s[1]);
@@ -1183,6 +1191,11 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         if (v < 0 || v > 1) return fail(c, LBMBT_EINVAL, "adjoint shape must be 0 or 1");
         c->adj_shape = (int)v;
         break;
+    case LBMBT_OPT_LATTICE:
+        if (v != 0 && v != 1) return fail(c, LBMBT_EINVAL, "lattice must be 0 (D3Q7) or 1 (D2Q5)");
+        invalidate_run(c);
+        c->lattice = (int)v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -1202,6 +1215,7 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_TMA_SHAPE: *v = c->tma_variant; break;
     case LBMBT_OPT_ADJOINT_KERNEL: *v = c->adjoint_opt; break;
     case LBMBT_OPT_ADJOINT_SHAPE: *v = c->adj_shape; break;
+    case LBMBT_OPT_LATTICE: *v = c->lattice; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
@@ -1392,6 +1406,7 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
     if (any_slab(c)) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not run on slabs");
     for (auto& g : c->geoms)
         if (g.d_dlt) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not take membrane positions");
+    if (c->lattice != 0) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep runs on the D3Q7 lattice only");
     const int ck = checkpoint_every > 0 ? checkpoint_every : 64;
     int rc = set_device(c);
     if (rc) return rc;

@@ -18,6 +18,9 @@ constexpr int Q = 7;
 constexpr float W0 = 0.25f;
 constexpr float WI = 0.125f;
 constexpr double EPS_D = 0.25;
+// D2Q5 (Sec. 2.3, Eq. omega_i): eps_D = 1/3, w0 = 1/3, w1..4 = 1/6; run as
+// the first five D3Q7 velocities on a grid of one z plane, z weights 0.
+constexpr double EPS_D2 = 1.0 / 3.0;
 
 // Outer-boundary handling of one axis for one member.
 enum BcMode : int {
@@ -98,6 +101,8 @@ struct SweepArgs {
     const float2* fac;            // [2][n_members][6] boundary factors, level k & 1
     int links;                    // a member has membrane positions (register sweep
                                   // variant with the Eqs. B4a-B4c rule)
+    float w0, wxy, wz;            // equilibrium weights (register sweep, init):
+                                  // D3Q7 1/4, 1/8, 1/8; D2Q5 1/3, 1/6, 0 (Sec. 2.3)
 };
 
 // ---- launchers (sweep.cu) ------------------------------------------------

@@ -65,7 +65,7 @@ __global__ void build_mask_kernel(const int32_t* __restrict__ labels, const uint
 
 // ---------------------------------------------------------------- init
 __global__ void init_kernel(const MemberDesc* __restrict__ members, const long long* __restrict__ tile_start,
-                            int n_members, int spt, int slot)
+                            int n_members, int spt, int slot, float w0, float wxy, float wz)
 {
     __shared__ int sm;
     if (threadIdx.x == 0) sm = find_member(tile_start, n_members, blockIdx.x);
@@ -77,13 +77,13 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
     for (int j = 0; j < spt; ++j) {
         const unsigned s = base + j * blockDim.x + threadIdx.x;
         if (s < (unsigned)d.N) {
-            out[s] = make_float2(W0, 0.f);
+            out[s] = make_float2(w0, 0.f);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) out[(size_t)i * P + s] = make_float2(WI, 0.f);
+            for (int i = 1; i < Q; ++i) out[(size_t)i * P + s] = make_float2(i < 5 ? wxy : wz, 0.f);
             // slab halo planes start at the neighbours' initial values
             if (s < (unsigned)(d.nx * d.ny))
                 for (int h = 0; h < 2; ++h)
-                    if (d.halo[h]) const_cast<float2*>(d.halo[h])[s] = make_float2(WI, 0.f);
+                    if (d.halo[h]) const_cast<float2*>(d.halo[h])[s] = make_float2(wz, 0.f);
         }
     }
 }
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
                                    : make_float2(-sd->eps[ph], 0.f);
         float mr, mi;
         react(g, q, mr, mi);
-        collide(g, sd->omega[ph], mr, mi);
+        collide_w(g, sd->omega[ph], mr, mi, a.w0, a.wxy, a.wz);
 #pragma unroll
         for (int i = 0; i < Q; ++i) __stcs(dst + (size_t)i * P + s, g[i]);
 
@@ -295,7 +295,8 @@ cudaError_t launch_build_mask(const int32_t* labels, const uint8_t* phase_of_lab
 
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot, cudaStream_t st)
 {
-    init_kernel<<<(unsigned)n_tiles, block, 0, st>>>(a.members, a.tile_start, a.n_members, spt, slot);
+    init_kernel<<<(unsigned)n_tiles, block, 0, st>>>(a.members, a.tile_start, a.n_members, spt, slot, a.w0, a.wxy,
+                                                     a.wz);
     return cudaGetLastError();
 }
 

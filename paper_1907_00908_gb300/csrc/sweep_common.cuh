@@ -258,6 +258,19 @@ __device__ __forceinline__ void collide(float2 (&g)[Q], float om, float mr, floa
     }
 }
 
+// collide() with the weights given at run time (w0 rest, wxy the four
+// in-plane velocities, wz the two z velocities); the same operations, so
+// with the D3Q7 weights it gives collide()'s bits.
+__device__ __forceinline__ void collide_w(float2 (&g)[Q], float om, float mr, float mi, float w0, float wxy, float wz)
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float w = i == 0 ? w0 : i < 5 ? wxy : wz;
+        g[i].x = __fmaf_rn(om, __fmaf_rn(w, mr, -g[i].x), g[i].x);
+        g[i].y = __fmaf_rn(om, __fmaf_rn(w, mi, -g[i].y), g[i].y);
+    }
+}
+
 // boundary_factors() into a flat [6] array: index 2*axis + (0 low, 1 high).
 __device__ __forceinline__ void boundary_factors6(const MemberDesc& sd, double F, float2* out6)
 {

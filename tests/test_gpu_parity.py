@@ -482,3 +482,38 @@ def test_reaction_substeps_match_oracle(lb, bc, gdir):
     o = _oracle(geom, bc, D, T2, 0.03, dt, f_fine, gG, want_field=True, substeps=k)
     assert abs(r["S"] - o["S"]) <= S_TOL * o["S"]
     assert _field_err(fld.cpu().numpy().reshape(geom.shape), o["field"]) < FIELD_TOL
+
+
+# ------------------------------------------------------------- D2Q5 lattice
+@pytest.mark.parametrize("bc, gdir", [((0, 0, 0), (0.6, 0.8, 0.0)), ((1, 1, 0), (1.0, 0.0, 0.0))])
+def test_d2q5_matches_oracle(lb, bc, gdir):
+    """The 2-D D2Q5 lattice (Sec. 2.3, eps_D = 1/3) on one z plane with dense
+    membranes, against the oracle's D2Q5 run."""
+    rng = np.random.default_rng(17)
+    lab = rng.integers(0, 3, size=(1, 40, 48)).astype(np.int32)
+    geom = synth.Geometry(lab, np.array([0, 1, 2], np.uint8), 0.5)
+    D, T2, kap, dt = [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.04, 0.01
+    gG, f = oracle.pgse(1500.0, 0.3, 0.6, dt, gdir)
+    s = _solver(lb, geom, bc, D, T2, kap, dt, f, gG)
+    s.set_option(lb.OPT_LATTICE, 1)
+    r, fld = _gpu_field(s, geom.n_sites)
+    assert s.get_option(lb.OPT_KERNEL_USED) == 1
+    with pytest.raises(lb.LbmbtError) as e:
+        s.grad()
+    assert e.value.code == -5
+    s.close()
+    o = _oracle(geom, bc, D, T2, kap, dt, f, gG, want_field=True, lattice="D2Q5")
+    assert abs(r["S"] - o["S"]) <= S_TOL * o["S"]
+    assert _field_err(fld.reshape(geom.shape), o["field"]) < FIELD_TOL
+
+
+def test_d2q5_needs_one_plane(lb):
+    geom = synth.uniform((2, 16, 16), 1.0)
+    s = _solver(lb, geom, (0, 0, 0), [2.0], [INF], INF, 0.05, np.zeros(4), [0, 0, 0])
+    s.set_option(lb.OPT_LATTICE, 1)
+    with pytest.raises(lb.LbmbtError) as e:
+        s.run()
+    assert e.value.code == -1
+    s.set_option(lb.OPT_LATTICE, 0)
+    s.run()
+    s.close()
