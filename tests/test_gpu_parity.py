@@ -304,6 +304,15 @@ def test_error_codes(lb):
     assert math.isfinite(s.run()["S"])
     with pytest.raises(lb.LbmbtError):
         s.set_option(lb.OPT_SPT, 3)
+    # sizes: an empty axis and a grid beyond 2^28 sites are refused before
+    # any label is read (the buffer passed is deliberately tiny)
+    tiny = np.zeros(8, np.int32)
+    pol = np.zeros(1, np.uint8)
+    bcv = np.zeros(3, np.int32)
+    for dims in [(0, 4, 4), (4, 0, 4), (1024, 1024, 257)]:
+        rc = lb.lib().lbmbt_set_geometry(s.h, dims[0], dims[1], dims[2], 1.0, lb._p(tiny), 0, 1, lb._p(pol),
+                                         lb._p(bcv))
+        assert rc == -1, dims
     s.close()
 
 

@@ -254,6 +254,25 @@ def test_slab_reference_matches_sgp_diffraction():
         assert E == pytest.approx(expect, abs=2e-3)
 
 
+def test_slab_reference_matches_mitra_short_time_limit():
+    """Pin of the continuum reference at short times: narrow pulses, low q,
+    sqrt(D Delta) << a -- the apparent diffusivity -ln E / (q^2 (Delta -
+    delta/3)) follows Mitra's surface-to-volume law 1 - D_app/D =
+    4/(3 sqrt(pi)) (S/V) sqrt(D Delta) with S/V = 2/a for a slab (flat walls:
+    no curvature term at the next order)."""
+    a, D, q, dt, nd = 20.0, 2.0, 0.01, 0.0005, 2
+    for Delta in (0.25, 1.0, 4.0):
+        gG = q / (nd * dt)
+        n = int(round(Delta / dt))
+        f = np.zeros(n + nd)
+        f[:nd] = 1.0
+        f[n:n + nd] = -1.0
+        E = refs.slab_signal(a, D, gG, f, dt, n_modes=300)
+        dev = 1.0 - (-math.log(E) / (q * q * (Delta - nd * dt / 3))) / D
+        mitra = 4.0 / (3.0 * math.sqrt(math.pi)) * (2.0 / a) * math.sqrt(D * Delta)
+        assert dev == pytest.approx(mitra, rel=3e-3)
+
+
 def test_exchange_reference_matches_karger_limit():
     """Pin of the exchange reference: for kappa a/D << 1 the compartments are
     well mixed and the Karger two-compartment ODE holds."""
