@@ -88,10 +88,48 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
     }
 }
 
+// Warp-compacted membrane links (Eqs. B4a-B4c): the links of one warp's 32
+// sites that take the position rule are listed in shared memory and shared
+// out one per lane, so the rule's loads and coefficients run once per link
+// instead of once per direction for the whole warp.  Per warp: LINK_SLOTS
+// results (float2) and LINK_SLOTS items (lane << 3 | direction).
+constexpr int LINK_SLOTS = 32 * 6;
+inline size_t link_smem_bytes(int block) { return (size_t)(block / 32) * LINK_SLOTS * (sizeof(float2) + 1); }
+
+// Arriving population i at site so (coordinates xo, yo, zo) across the
+// membrane on its link to y = so - e_i, at the position dl (from so): the
+// position rule when so + e_i lies in so's compartment and y - e_i in y's
+// (the caller checked the first, the mask byte of y decides the second),
+// else the half-link rule (Eq. B5).
+__device__ __forceinline__ float2 link_population(const MemberDesc* __restrict__ sd,
+                                                  const float2* __restrict__ src, const float2* __restrict__ fac,
+                                                  unsigned so, int xo, int yo, int zo, int i)
+{
+    const unsigned P = (unsigned)sd->plane;
+    const int ax = (i - 1) >> 1, e = (i & 1) ? 1 : -1, ib = (i & 1) ? i + 1 : i - 1;
+    const int c = ax == 0 ? xo : ax == 1 ? yo : zo;
+    const int dim = ax == 0 ? sd->nx : ax == 1 ? sd->ny : sd->nz;
+    const unsigned st = ax == 0 ? 1u : ax == 1 ? (unsigned)sd->nx : (unsigned)sd->nx * sd->ny;
+    const int bl = ax == 2 ? sd->zbc[0] : sd->bc[ax], bh = ax == 2 ? sd->zbc[1] : sd->bc[ax];
+    const int cy = c - e;   // y = so - e_i, wrapped when periodic (a membrane never crosses a mirror face)
+    const unsigned sy = (unsigned)((int)so + (cy < 0 ? dim - 1 : cy >= dim ? 1 - dim : -e) * (int)st);
+    const unsigned mky = __ldg(sd->mask + sy);
+    const float dl = __ldg(sd->dlt + (size_t)(ib - 1) * P + so);
+    const float2 own_ib = __ldg(src + (size_t)ib * P + so);
+    const float2 own_i = __ldg(src + (size_t)i * P + so);
+    const float2 v1 = read_along(src, P, so, i, ax, -e, c, dim, st, bl, bh, fac);        // the plain pull
+    const float2 vb = read_along(src, P, so, ib, ax, e, c, dim, st, bl, bh, fac);        // g_ib(so + e_i)
+    const float2 vf = read_along(src, P, so, i, ax, -2 * e, c, dim, st, bl, bh, fac);    // g_i(y - e_i)
+    const float2 wy = read_along(src, P, so, ib, ax, -e, c, dim, st, bl, bh, fac);       // g_ib(y)
+    if (mky & (1u << (ib - 1))) return mix(own_ib, v1, sd->s_share);
+    return link_combine(dl, sd->lrho, own_ib, vb, own_i, v1, vf, wy);
+}
+
 template <int SPT, bool LINKS>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 {
     __shared__ double2 s_red[32];
+    extern __shared__ __align__(16) unsigned char s_link[];   // LINKS only: link_smem_bytes(blockDim.x)
     // Every thread looks up its member, step and flags itself (broadcast
     // loads): there is no per-block prologue to wait for.
     const int m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, blockIdx.x);
@@ -118,8 +156,16 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-        const unsigned s = base + j * blockDim.x + threadIdx.x;
-        if (s >= N) break;
+        const unsigned s_at = base + j * blockDim.x + threadIdx.x;
+        const bool in = s_at < N;
+        if (LINKS) {
+            // the link lists are warp-collective: a lane past the end stays
+            // (on the last site, without storing) while any lane of its warp works
+            if (!__any_sync(0xffffffffu, in)) break;
+        } else if (!in) {
+            break;
+        }
+        const unsigned s = in ? s_at : N - 1;
         int x, y, z;
         coords(sd, s, nx, ny, x, y, z);
         const unsigned mk = mask[s];
@@ -138,31 +184,55 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
         // population is r * (own population sent towards the membrane) +
         // s * (population streaming across), written A + s (B - A).
         // Bit (ibar - 1) marks the link to the upstream neighbour of i.
-        if (mk & 0x3fu) {
-            const float* __restrict__ dlt = LINKS ? sd->dlt : nullptr;
+        if (LINKS && sd->dlt != nullptr) {   // block-uniform
+            // Membranes at given positions: a link whose node behind s (s +
+            // e_i) lies in another compartment keeps the half-link rule here;
+            // the others go to the warp's list.
+            unsigned cand = 0;
+            if (in && (mk & 0x3fu)) {
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int ib = (i & 1) ? i + 1 : i - 1;
+                    if (!(mk & (1u << (ib - 1)))) continue;
+                    if (mk & (1u << (i - 1))) g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
+                    else cand |= 1u << i;
+                }
+            }
+            const unsigned lane = threadIdx.x & 31u, nc = __popc(cand);
+            unsigned incl = nc;   // inclusive prefix of the warp's link counts
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (unsigned)o) incl += v;
+            }
+            const unsigned K = __shfl_sync(0xffffffffu, incl, 31);
+            if (K != 0) {   // warp-uniform
+                float2* const res = reinterpret_cast<float2*>(s_link) + (threadIdx.x >> 5) * LINK_SLOTS;
+                uint8_t* const item = s_link + (size_t)(blockDim.x >> 5) * LINK_SLOTS * sizeof(float2) +
+                                      (threadIdx.x >> 5) * LINK_SLOTS;
+                unsigned o = incl - nc;
+                for (unsigned c = cand; c; c &= c - 1) item[o++] = (uint8_t)((lane << 3) | (__ffs(c) - 1));
+                __syncwarp();
+                for (unsigned t0 = 0; t0 < K; t0 += 32) {   // warp-uniform
+                    const unsigned t = t0 + lane;
+                    const unsigned it = item[t < K ? t : 0];
+                    const unsigned sl = it >> 3;
+                    const int xo = __shfl_sync(0xffffffffu, x, sl), yo = __shfl_sync(0xffffffffu, y, sl),
+                              zo = __shfl_sync(0xffffffffu, z, sl);
+                    if (t < K) res[t] = link_population(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
+                }
+                __syncwarp();
+                o = incl - nc;
+#pragma unroll
+                for (int i = 1; i < Q; ++i)
+                    if (cand & (1u << i)) g[i] = res[o++];
+                __syncwarp();   // the lists are rewritten for the warp's next sites
+            }
+        } else if (mk & 0x3fu) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int ib = (i & 1) ? i + 1 : i - 1;
-                if (!(mk & (1u << (ib - 1)))) continue;
-                const float2 own = __ldg(src + (size_t)ib * P + s);
-                // membrane at a given position (Eqs. B4a-B4c) where the node
-                // behind s and the node beyond y stay in their compartments
-                if (LINKS && dlt != nullptr && !(mk & (1u << (i - 1)))) {
-                    const int a = (i - 1) >> 1, e = (i & 1) ? 1 : -1;
-                    const int c = a == 0 ? x : a == 1 ? y : z;
-                    const int dim = a == 0 ? nx : a == 1 ? ny : nz;
-                    const unsigned st = a == 0 ? 1u : a == 1 ? (unsigned)nx : sxy;
-                    const int bl = a == 0 ? bcx : a == 1 ? bcy : bcz0, bh = a == 0 ? bcx : a == 1 ? bcy : bcz1;
-                    const int cy = c - e;   // the far node y = s - e_i (a periodic wrap: a membrane never
-                                            // crosses a mirror face)
-                    const unsigned sy = (unsigned)((int)s + (cy < 0 ? dim - 1 : cy >= dim ? 1 - dim : -e) * (int)st);
-                    if (!(__ldg(mask + sy) & (1u << (ib - 1)))) {
-                        g[i] = link_rule(src, P, s, i, a, c, dim, st, bl, bh, fac, __ldg(dlt + (size_t)(ib - 1) * P + s),
-                                         sd->lrho, g[i], own, __ldg(src + (size_t)i * P + s));
-                        continue;
-                    }
-                }
-                g[i] = mix(own, g[i], sh);
+                if (mk & (1u << (ib - 1))) g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
             }
         }
 
@@ -175,6 +245,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
         float mr, mi;
         react(g, q, mr, mi);
         collide_w(g, sd->omega[ph], mr, mi, a.w0, a.wxy, a.wz);
+        if (LINKS && !in) continue;
 #pragma unroll
         for (int i = 0; i < Q; ++i) __stcs(dst + (size_t)i * P + s, g[i]);
 
@@ -304,15 +375,15 @@ cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int s
 {
     switch (spt) {
     case 1:
-        if (a.links) sweep_kernel<1, true><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        if (a.links) sweep_kernel<1, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
         else sweep_kernel<1, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 2:
-        if (a.links) sweep_kernel<2, true><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        if (a.links) sweep_kernel<2, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
         else sweep_kernel<2, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 4:
-        if (a.links) sweep_kernel<4, true><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        if (a.links) sweep_kernel<4, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
         else sweep_kernel<4, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;

@@ -133,30 +133,23 @@ __device__ __forceinline__ float2 read_along(const float2* __restrict__ src, uns
 // with the membrane at dl*dx from s (theta = 0, Eqs. B4a-B4c): the arriving
 // population i is
 //   A1 g_ib(s) + A2 g_ib(s + e_i) + A3 g_i(s) + B1 g_i(y) + B2 g_i(y - e_i) + B3 g_ib(y)
-// (ib = opposite of i, post-collision values), with the coefficients from the
-// Neumann (Eq. c_n) and Dirichlet (Eq. c_d) coefficients of dl and 1 - dl and
-// rho = kappa dt / (eps_D dx).  v1 = g_i(y) as pulled, own_ib = g_ib(s).
-// Used only when s + e_i lies in s's compartment and y - e_i in y's (the
-// caller checks the mask bits), and kappa is finite.
-__device__ __noinline__ float2 link_rule(const float2* __restrict__ src, unsigned P, unsigned s, int i, int a,
-                                         int c, int dim, unsigned stride, int bc_lo, int bc_hi,
-                                         const float2* __restrict__ fac, float dl, float rho, float2 v1,
-                                         float2 own_ib, float2 own_i)
+// (ib = opposite of i, post-collision values, each read with the outer-face
+// transforms), with the coefficients from the Neumann (Eq. c_n) and Dirichlet
+// (Eq. c_d) coefficients of dl and 1 - dl and rho = kappa dt / (eps_D dx).
+// Used only when s + e_i lies in s's compartment and y - e_i in y's, and
+// kappa is finite.
+__device__ __forceinline__ float2 link_combine(float dl, float rho, float2 own_ib, float2 v_behind, float2 own_i,
+                                               float2 v1, float2 v_far, float2 w_y)
 {
-    const int ib = (i & 1) ? i + 1 : i - 1;
-    const int e = (i & 1) ? 1 : -1;                      // e_i along axis a
-    const float2 v_behind = read_along(src, P, s, ib, a, e, c, dim, stride, bc_lo, bc_hi, fac);
-    const float2 v_far = read_along(src, P, s, i, a, -2 * e, c, dim, stride, bc_lo, bc_hi, fac);
-    const float2 w_y = read_along(src, P, s, ib, a, -e, c, dim, stride, bc_lo, bc_hi, fac);
     float cn[4], cd[4], cns[4], cds[4];
     const float ds = 1.f - dl;
-    const float q = 1.f / (2.f * dl + 1.f), qs = 1.f / (2.f * ds + 1.f);
+    const float q = __frcp_rn(2.f * dl + 1.f), qs = __frcp_rn(2.f * ds + 1.f);
     const float u = 2.f * dl - 1.f, us = 2.f * ds - 1.f;
     cn[0] = 1.f; cn[1] = -u * q; cn[2] = u * q; cn[3] = 2.f * q;
     cd[0] = 2.f * (dl - 1.f); cd[1] = -u * u * q; cd[2] = 2.f * u * q; cd[3] = (3.f - 2.f * dl) * q;
     cns[0] = 1.f; cns[1] = -us * qs; cns[2] = us * qs; cns[3] = 2.f * qs;
     cds[0] = 2.f * (ds - 1.f); cds[1] = -us * us * qs; cds[2] = 2.f * us * qs; cds[3] = (3.f - 2.f * ds) * qs;
-    const float invF = 1.f / (cd[3] * cds[3] + (cd[3] * cns[3] + cn[3] * cds[3]) * rho);
+    const float invF = __frcp_rn(cd[3] * cds[3] + (cd[3] * cns[3] + cn[3] * cds[3]) * rho);
     float A[3], B[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
