@@ -396,7 +396,7 @@ def run_links(args):
                        n_memb_links / (6.0 * geom.n_sites), "geometry_gen_s": round(t_geo, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": peak_kind, "bytes_per_site_member": bytes_site,
-                         "kernel": "sweep_kernel (register)"},
+                         "kernel": "sweep_links_kernel (register)"},
             "compare": res}
     print(json.dumps(line), flush=True)
     return 0

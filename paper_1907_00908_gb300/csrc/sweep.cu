@@ -13,6 +13,8 @@
 //    maps hat g(t^k) -> hat g(t^{k+1}), i.e. the paper's step order re-cut at
 //    the collision, so every site reads 7 complex values (one from each
 //    upstream neighbour) and writes 7.
+//  * sweep_links_kernel: the same step with membranes at given positions on
+//        the links (Eqs. B4a-B4c), the rule's links compacted per warp
 //  * ctl_kernel        : sets / advances the step word between sweeps and
 //                        computes the next step's FP64 boundary factors
 //  * reduce_kernel     : fixed-order FP64 sum of the per-tile partials.
@@ -21,6 +23,7 @@
 // block finds its member by binary search over the tile prefix.
 #include "lbmbt_internal.cuh"
 #include "sweep_common.cuh"
+#include "links.cuh"
 
 namespace lbmbt {
 namespace {
@@ -96,37 +99,8 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
 constexpr int LINK_SLOTS = 32 * 6;
 inline size_t link_smem_bytes(int block) { return (size_t)(block / 32) * LINK_SLOTS * (sizeof(float2) + 1); }
 
-// Arriving population i at site so (coordinates xo, yo, zo) across the
-// membrane on its link to y = so - e_i, at the position dl (from so): the
-// position rule when so + e_i lies in so's compartment and y - e_i in y's
-// (the caller checked the first, the mask byte of y decides the second),
-// else the half-link rule (Eq. B5).
-__device__ __forceinline__ float2 link_population(const MemberDesc* __restrict__ sd,
-                                                  const float2* __restrict__ src, const float2* __restrict__ fac,
-                                                  unsigned so, int xo, int yo, int zo, int i)
-{
-    const unsigned P = (unsigned)sd->plane;
-    const int ax = (i - 1) >> 1, e = (i & 1) ? 1 : -1, ib = (i & 1) ? i + 1 : i - 1;
-    const int c = ax == 0 ? xo : ax == 1 ? yo : zo;
-    const int dim = ax == 0 ? sd->nx : ax == 1 ? sd->ny : sd->nz;
-    const unsigned st = ax == 0 ? 1u : ax == 1 ? (unsigned)sd->nx : (unsigned)sd->nx * sd->ny;
-    const int bl = ax == 2 ? sd->zbc[0] : sd->bc[ax], bh = ax == 2 ? sd->zbc[1] : sd->bc[ax];
-    const int cy = c - e;   // y = so - e_i, wrapped when periodic (a membrane never crosses a mirror face)
-    const unsigned sy = (unsigned)((int)so + (cy < 0 ? dim - 1 : cy >= dim ? 1 - dim : -e) * (int)st);
-    const unsigned mky = __ldg(sd->mask + sy);
-    const float dl = __ldg(sd->dlt + (size_t)(ib - 1) * P + so);
-    const float2 own_ib = __ldg(src + (size_t)ib * P + so);
-    const float2 own_i = __ldg(src + (size_t)i * P + so);
-    const float2 v1 = read_along(src, P, so, i, ax, -e, c, dim, st, bl, bh, fac);        // the plain pull
-    const float2 vb = read_along(src, P, so, ib, ax, e, c, dim, st, bl, bh, fac);        // g_ib(so + e_i)
-    const float2 vf = read_along(src, P, so, i, ax, -2 * e, c, dim, st, bl, bh, fac);    // g_i(y - e_i)
-    const float2 wy = read_along(src, P, so, ib, ax, -e, c, dim, st, bl, bh, fac);       // g_ib(y)
-    if (mky & (1u << (ib - 1))) return mix(own_ib, v1, sd->s_share);
-    return link_combine(dl, sd->lrho, own_ib, vb, own_i, v1, vf, wy);
-}
-
 template <int SPT, bool LINKS>
-__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
+__device__ __forceinline__ void sweep_body(const SweepArgs& a)
 {
     __shared__ double2 s_red[32];
     extern __shared__ __align__(16) unsigned char s_link[];   // LINKS only: link_smem_bytes(blockDim.x)
@@ -171,6 +145,40 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
         const unsigned mk = mask[s];
         const int ph = mk >> 6;
 
+        // Membranes at given positions: the warp lists its links that take
+        // the position rule (those whose node behind s, s + e_i, lies in s's
+        // compartment) before the pulls, so that the rule's loads and the
+        // pulls are in flight together; the list is shared out one link per
+        // lane below.
+        const bool links_on = LINKS && sd->dlt != nullptr;   // block-uniform
+        const unsigned lane = threadIdx.x & 31u;
+        unsigned cand = 0, incl = 0, K = 0;
+        float2* res = nullptr;
+        uint8_t* item = nullptr;
+        if (links_on) {
+            if (in && (mk & 0x3fu)) {
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    const int ib = (i & 1) ? i + 1 : i - 1;
+                    if ((mk & (1u << (ib - 1))) && !(mk & (1u << (i - 1)))) cand |= 1u << i;
+                }
+            }
+            incl = __popc(cand);   // inclusive prefix of the warp's link counts
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (unsigned)o) incl += v;
+            }
+            K = __shfl_sync(0xffffffffu, incl, 31);
+            if (K != 0) {   // warp-uniform
+                res = reinterpret_cast<float2*>(s_link) + (threadIdx.x >> 5) * LINK_SLOTS;
+                item = s_link + (size_t)(blockDim.x >> 5) * LINK_SLOTS * sizeof(float2) + (threadIdx.x >> 5) * LINK_SLOTS;
+                unsigned o = incl - __popc(cand);
+                for (unsigned c = cand; c; c &= c - 1) item[o++] = (uint8_t)((lane << 3) | (__ffs(c) - 1));
+                __syncwarp();
+            }
+        }
+
         float2 g[Q];
         g[0] = __ldg(src + s);
         g[1] = pull<0, +1>(src, P, s, x, nx, 1u, bcx, fac);
@@ -184,35 +192,17 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
         // population is r * (own population sent towards the membrane) +
         // s * (population streaming across), written A + s (B - A).
         // Bit (ibar - 1) marks the link to the upstream neighbour of i.
-        if (LINKS && sd->dlt != nullptr) {   // block-uniform
-            // Membranes at given positions: a link whose node behind s (s +
-            // e_i) lies in another compartment keeps the half-link rule here;
-            // the others go to the warp's list.
-            unsigned cand = 0;
-            if (in && (mk & 0x3fu)) {
+        // With positions, the listed links take their lane's result instead.
+        if (links_on) {
+            if (mk & 0x3fu) {   // node behind s in another compartment: half-link rule
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     const int ib = (i & 1) ? i + 1 : i - 1;
-                    if (!(mk & (1u << (ib - 1)))) continue;
-                    if (mk & (1u << (i - 1))) g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
-                    else cand |= 1u << i;
+                    if ((mk & (1u << (ib - 1))) && (mk & (1u << (i - 1))))
+                        g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
                 }
             }
-            const unsigned lane = threadIdx.x & 31u, nc = __popc(cand);
-            unsigned incl = nc;   // inclusive prefix of the warp's link counts
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (unsigned)o) incl += v;
-            }
-            const unsigned K = __shfl_sync(0xffffffffu, incl, 31);
             if (K != 0) {   // warp-uniform
-                float2* const res = reinterpret_cast<float2*>(s_link) + (threadIdx.x >> 5) * LINK_SLOTS;
-                uint8_t* const item = s_link + (size_t)(blockDim.x >> 5) * LINK_SLOTS * sizeof(float2) +
-                                      (threadIdx.x >> 5) * LINK_SLOTS;
-                unsigned o = incl - nc;
-                for (unsigned c = cand; c; c &= c - 1) item[o++] = (uint8_t)((lane << 3) | (__ffs(c) - 1));
-                __syncwarp();
                 for (unsigned t0 = 0; t0 < K; t0 += 32) {   // warp-uniform
                     const unsigned t = t0 + lane;
                     const unsigned it = item[t < K ? t : 0];
@@ -222,7 +212,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
                     if (t < K) res[t] = link_population(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
                 }
                 __syncwarp();
-                o = incl - nc;
+                unsigned o = incl - __popc(cand);
 #pragma unroll
                 for (int i = 1; i < Q; ++i)
                     if (cand & (1u << i)) g[i] = res[o++];
@@ -273,6 +263,20 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
             if (l == 0) a.partial[blockIdx.x] = v;
         }
     }
+}
+
+template <int SPT>
+__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
+{
+    sweep_body<SPT, false>(a);
+}
+
+// With membrane positions: two blocks of 512 per SM (64 registers), since
+// the position rule's extra loads need more warps in flight to hide them.
+template <int SPT>
+__global__ void __launch_bounds__(512, 2) sweep_links_kernel(const SweepArgs a)
+{
+    sweep_body<SPT, true>(a);
 }
 
 // Control word: set (or advance k), then the boundary factors of the new step
@@ -375,16 +379,16 @@ cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int s
 {
     switch (spt) {
     case 1:
-        if (a.links) sweep_kernel<1, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
-        else sweep_kernel<1, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        if (a.links) sweep_links_kernel<1><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        else sweep_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 2:
-        if (a.links) sweep_kernel<2, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
-        else sweep_kernel<2, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        if (a.links) sweep_links_kernel<2><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        else sweep_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 4:
-        if (a.links) sweep_kernel<4, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
-        else sweep_kernel<4, false><<<(unsigned)n_tiles, block, 0, st>>>(a);
+        if (a.links) sweep_links_kernel<4><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        else sweep_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;
     }

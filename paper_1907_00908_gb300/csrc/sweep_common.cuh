@@ -102,66 +102,6 @@ __device__ __forceinline__ float2 pull(const float2* __restrict__ src, unsigned 
     return v;
 }
 
-// Value of population p (lying along axis a) at the node d steps along axis
-// a from site s (coordinate c of dim nodes, stride between nodes), with the
-// outer-boundary transforms of a node beyond a face: periodic -> the wrapped
-// node times the face's wrap factor; mirror -> the node mirrored in the face
-// (node -1-m mirrors m, node dim+m mirrors dim-1-m), opposite population,
-// conjugated and rewound when G is normal to the face.  |d| <= 2.
-__device__ __forceinline__ float2 read_along(const float2* __restrict__ src, unsigned P, unsigned s, int p, int a,
-                                             int d, int c, int dim, unsigned stride, int bc_lo, int bc_hi,
-                                             const float2* __restrict__ fac)
-{
-    const int cp = c + d;
-    if (cp >= 0 && cp < dim) return __ldg(src + (size_t)p * P + (unsigned)((int)s + d * (int)stride));
-    const bool lo = cp < 0;
-    const int bc = lo ? bc_lo : bc_hi;
-    const float2 f = __ldg(fac + 2 * a + (lo ? 0 : 1));
-    if (bc == BC_PER) {
-        const int dw = lo ? d + dim : d - dim;
-        return cmul(__ldg(src + (size_t)p * P + (unsigned)((int)s + dw * (int)stride)), f);
-    }
-    const int m = lo ? -1 - cp : 2 * dim - 1 - cp;      // mirrored node
-    const int pr = (p & 1) ? p + 1 : p - 1;             // opposite population
-    float2 v = __ldg(src + (size_t)pr * P + (unsigned)((int)s + (m - c) * (int)stride));
-    if (bc == BC_MIR) return v;
-    v.y = -v.y;
-    return cmul(v, f);
-}
-
-// Membrane on the link from site s towards its upstream neighbour y = s - e_i
-// with the membrane at dl*dx from s (theta = 0, Eqs. B4a-B4c): the arriving
-// population i is
-//   A1 g_ib(s) + A2 g_ib(s + e_i) + A3 g_i(s) + B1 g_i(y) + B2 g_i(y - e_i) + B3 g_ib(y)
-// (ib = opposite of i, post-collision values, each read with the outer-face
-// transforms), with the coefficients from the Neumann (Eq. c_n) and Dirichlet
-// (Eq. c_d) coefficients of dl and 1 - dl and rho = kappa dt / (eps_D dx).
-// Used only when s + e_i lies in s's compartment and y - e_i in y's, and
-// kappa is finite.
-__device__ __forceinline__ float2 link_combine(float dl, float rho, float2 own_ib, float2 v_behind, float2 own_i,
-                                               float2 v1, float2 v_far, float2 w_y)
-{
-    float cn[4], cd[4], cns[4], cds[4];
-    const float ds = 1.f - dl;
-    const float q = __frcp_rn(2.f * dl + 1.f), qs = __frcp_rn(2.f * ds + 1.f);
-    const float u = 2.f * dl - 1.f, us = 2.f * ds - 1.f;
-    cn[0] = 1.f; cn[1] = -u * q; cn[2] = u * q; cn[3] = 2.f * q;
-    cd[0] = 2.f * (dl - 1.f); cd[1] = -u * u * q; cd[2] = 2.f * u * q; cd[3] = (3.f - 2.f * dl) * q;
-    cns[0] = 1.f; cns[1] = -us * qs; cns[2] = us * qs; cns[3] = 2.f * qs;
-    cds[0] = 2.f * (ds - 1.f); cds[1] = -us * us * qs; cds[2] = 2.f * us * qs; cds[3] = (3.f - 2.f * ds) * qs;
-    const float invF = __frcp_rn(cd[3] * cds[3] + (cd[3] * cns[3] + cn[3] * cds[3]) * rho);
-    float A[3], B[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        A[j] = (cd[3] * cds[3] * cn[j] + (cds[3] * cn[3] * cd[j] + cns[3] * cd[3] * cn[j]) * rho) * invF;
-        B[j] = cd[3] * cn[3] * (cns[j] - cds[j]) * rho * invF;
-    }
-    float2 r;
-    r.x = A[0] * own_ib.x + A[1] * v_behind.x + A[2] * own_i.x + B[0] * v1.x + B[1] * v_far.x + B[2] * w_y.x;
-    r.y = A[0] * own_ib.y + A[1] * v_behind.y + A[2] * own_i.y + B[0] * v1.y + B[1] * v_far.y + B[2] * w_y.y;
-    return r;
-}
-
 // Exact n / d for n < 2^28 with host-computed (m, s) (Granlund-Montgomery,
 // 28-bit dividends: m = floor(2^(28+l)/d) + 1, s = 28 + l, l = ceil(log2 d)).
 __device__ __forceinline__ unsigned fdiv(unsigned n, unsigned m, int s)
