@@ -16,6 +16,9 @@ arXiv 1907.00908:
                    streaming_LBM, reaction_LBM, permeability_BC/B5,
                    collision_BC (modified periodic) and Sec. 2.4.4 (mirror).
 * ``mask``      -- half-link membrane links on label changes (Sec. 2.4.2).
+* ``link_coefficients`` / ``angled_coefficients`` -- the membrane rule with
+                   positions (Eqs. B4a-B4c) and its general-angle form
+                   (Appendix B, Eqs. B2a, phi_1, phi_2, B1, B1.5).
 """
 from __future__ import annotations
 
@@ -69,9 +72,11 @@ def _load():
             lib.lbm_oracle_run_ex.argtypes = [
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                 P, ctypes.c_int, P, P, ctypes.c_int, P, P,
-                ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
-                P, P, P, P]
+                ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P, P, ctypes.c_int,
+                ctypes.c_int, P, P, P, P]
             lib.lbm_oracle_run_ex.restype = ctypes.c_int
+            lib.lbm_oracle_angled_coefficients.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, P, P, P, P]
+            lib.lbm_oracle_angled_coefficients.restype = None
             lib.lbm_oracle_link_coefficients.argtypes = [ctypes.c_double] * 4 + [P, P]
             lib.lbm_oracle_link_coefficients.restype = None
             lib.lbm_oracle_mask.argtypes = [
@@ -132,6 +137,16 @@ def link_coefficients(delta_m, kappa, dt, dx):
     return A, B
 
 
+def angled_coefficients(delta_m, theta, kappa, dt, dx, lattice="D2Q5"):
+    """(A[3], B[3], C[3], D[3]) of the general-angle membrane rule (Appendix
+    B, Eq. B2a), obtained by linearity from the oracle's solve of Eqs.
+    dirichlet_1-neumann_2, phi_1, phi_2, B1 and B1.5."""
+    A, B, C, D = np.zeros(3), np.zeros(3), np.zeros(3), np.zeros(3)
+    _load().lbm_oracle_angled_coefficients(float(delta_m), float(theta), float(kappa), float(dt), float(dx),
+                                           int(lattice == "D2Q5"), _ptr(A), _ptr(B), _ptr(C), _ptr(D))
+    return A, B, C, D
+
+
 def mask(labels, phase_of_label, bc):
     """Bit-packed membrane/phase byte per site (see ``lbm_oracle_mask``)."""
     labels = np.ascontiguousarray(labels, dtype=np.int32)
@@ -147,7 +162,7 @@ def mask(labels, phase_of_label, bc):
 
 def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
         want_field=False, want_series=False, want_state=False, threads=0, delta=None, substeps=1,
-        lattice="D3Q7"):
+        lattice="D3Q7", theta=None):
     """Run the scheme from M = 1 to t = len(f)*dt.
 
     ``labels``: int32 [nz, ny, nx] compartment ids; ``phase_of_label``: phase
@@ -161,6 +176,9 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     k reaction steps of dt/k after each diffusion step (Sec. 2.3, dt = k dt'),
     ``f`` then sampled on the dt/k grid (len(f) = k * number of steps).
     ``lattice`` = "D2Q5": the 2-D lattice of Sec. 2.3 (eps_D = 1/3, nz = 1).
+    ``theta`` (D2Q5, with ``delta``): [6, 1, ny, nx] signed angles between the
+    membrane normal and each link (see ``angled_arrival`` in the C source),
+    which selects the general-angle rule of Appendix B.
     """
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     nz, ny, nx = labels.shape
@@ -180,13 +198,16 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     state = np.empty(2 * 7 * N) if want_state else None
     if lattice not in ("D3Q7", "D2Q5"):
         raise ValueError("lattice must be D3Q7 or D2Q5")
+    if theta is not None and (delta is None or lattice != "D2Q5"):
+        raise ValueError("membrane angles need positions and the D2Q5 lattice")
     if substeps != 1 or lattice == "D2Q5":
         dl = None if delta is None else np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(6, N).T)
+        th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(6, N).T)
         rc = _load().lbm_oracle_run_ex(
             nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
             int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
-            int(threads), _ptr(dl), int(substeps), int(lattice == "D2Q5"), _ptr(Z), _ptr(field), _ptr(series),
-            _ptr(state))
+            int(threads), _ptr(dl), _ptr(th), int(substeps), int(lattice == "D2Q5"), _ptr(Z), _ptr(field),
+            _ptr(series), _ptr(state))
     elif delta is None:
         rc = _load().lbm_oracle_run(
             nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),

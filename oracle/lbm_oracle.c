@@ -150,6 +150,115 @@ void lbm_oracle_link_coefficients(double dl, double kappa, double dt, double dx,
     link_coefficients(dl, kappa, dt, dx, EPS_D, A, B);
 }
 
+/*
+ * General-angle membrane rule in 2-D (Appendix B: Eqs. dirichlet_1-neumann_2
+ * for the link, Eqs. phi_1 and phi_2 for the lattice-direction fluxes, Eqs.
+ * B1 and B1.5 for the membrane), for the population X = g'_abar(x_i)
+ * arriving at the node x_i from the membrane on its link to x_e, alpha
+ * pointing from x_i towards the membrane.  theta is the angle between the
+ * membrane normal and the link; beta is the perpendicular lattice direction
+ * with a positive component along the normal from x_i's side to x_e's.
+ * Inputs (post-collision values):
+ *   a = (hat g_alpha(x_i), hat g_alpha(x_ii), hat g_abar(x_i))
+ *   b = (hat g_abar(x_e), hat g_abar(x_ee), hat g_alpha(x_e))
+ *   p = (hat g_beta(x'_i), hat g_beta(x'_ii), hat g_bbar(x'_i))
+ *   q = (hat g_bbar(x'_e), hat g_bbar(x'_ee), hat g_beta(x'_e))
+ * The unknowns X, Y = g'_alpha(x_e) and V = (dt/dx) Phi_n,in satisfy three
+ * linear equations (each relation written out below), solved by Cramer's
+ * rule.  c' are the coefficients of Eqs. c_n, c_d at Delta_m = 0, c* at
+ * 1 - Delta_m.  kappa = 0 gives the impermeable wall.
+ */
+static cplx angled_link(double dl, double th, double kappa, double dt, double dx, double eps,
+                        const cplx a[3], const cplx b[3], const cplx p[3], const cplx q[3])
+{
+    double cn[4], cd[4], cns[4], cds[4], cnp[4], cdp[4];
+    coef_n(dl, cn);
+    coef_d(dl, cd);
+    coef_n(1.0 - dl, cns);
+    coef_d(1.0 - dl, cds);
+    coef_n(0.0, cnp);
+    coef_d(0.0, cdp);
+    const double st = fabs(sin(th)), ct = cos(th);
+    const double rho = kappa * dt / (eps * dx);
+    /* the three-term sums of the Dirichlet and Neumann relations on each side
+     * (Eqs. dirichlet_1, neumann_1 with a; dirichlet_2, neumann_2 with b) and
+     * the Neumann-minus-Dirichlet sums along beta (Eqs. phi_1, phi_2) */
+    cplx Sd = 0, Sn = 0, Sds = 0, Sns = 0, Tp = 0, Tq = 0;
+    for (int j = 0; j < 3; ++j) {
+        Sd += cd[j] * a[j];
+        Sn += cn[j] * a[j];
+        Sds += cds[j] * b[j];
+        Sns += cns[j] * b[j];
+        Tp += (cnp[j] - cdp[j]) * p[j];
+        Tq += (cnp[j] - cdp[j]) * q[j];
+    }
+    const double rp = cnp[3] / cdp[3];
+    const double Ki = cn[3] / cd[3] * st + rp * ct, Ke = cns[3] / cds[3] * st + rp * ct;
+    /* Eq. neumann_1: (dt/dx) Phi_nabar = (X - Sn) / c_n4; Eq. phi_1 then reads
+     *   (X - Sn)/c_n4 * Ki = Tp st / c'_d4 - (Sn - Sd) st / c_d4 + rp V        (row 0)
+     * Eq. neumann_2 and Eq. phi_2 with Phi_n,ex = -Phi_n,in (Eq. B1.5):
+     *   (Y - Sns)/c*_n4 * Ke = Tq st / c'_d4 - (Sns - Sds) st / c*_d4 - rp V   (row 1)
+     * Eq. B1 with Eqs. dirichlet_1/2 (eps_D Phi_d = (X - Sd)/c_d4 ...):
+     *   V = rho ((Y - Sds)/c*_d4 - (X - Sd)/c_d4)                              (row 2) */
+    const double M[3][3] = {{Ki / cn[3], 0.0, -rp},
+                            {0.0, Ke / cns[3], rp},
+                            {rho / cd[3], -rho / cds[3], 1.0}};
+    const cplx R[3] = {Tp * st / cdp[3] - (Sn - Sd) * st / cd[3] + Ki * Sn / cn[3],
+                       Tq * st / cdp[3] - (Sns - Sds) * st / cds[3] + Ke * Sns / cns[3],
+                       rho * (Sd / cd[3] - Sds / cds[3])};
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    /* X by Cramer's rule: column 0 replaced by R */
+    const cplx detX = R[0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                      M[0][1] * (R[1] * M[2][2] - M[1][2] * R[2]) +
+                      M[0][2] * (R[1] * M[2][1] - M[1][1] * R[2]);
+    return detX / det;
+}
+
+/* Coefficients of the general-angle rule by linearity: X for each unit input
+ * in turn; A, B, C, D multiply a, b, p, q (the paper's A^i_j, B^i_j, C^i_j,
+ * D^i_j of Eq. B3a).  d2q5 != 0 takes eps_D = 1/3, else 1/4. */
+void lbm_oracle_angled_coefficients(double dl, double th, double kappa, double dt, double dx, int d2q5,
+                                    double* A, double* B, double* C, double* D)
+{
+    double* out[4] = {A, B, C, D};
+    for (int v = 0; v < 4; ++v)
+        for (int j = 0; j < 3; ++j) {
+            cplx in[4][3] = {{0}};
+            in[v][j] = 1.0;
+            out[v][j] = creal(angled_link(dl, th, kappa, dt, dx, d2q5 ? EPS_D2 : EPS_D, in[0], in[1], in[2], in[3]));
+        }
+}
+
+/* Value of hat g_p at node (x, y, z) of the padded state, the node possibly
+ * beyond periodic faces on several axes (a corner of the buffer layers):
+ * the wrapped node times the wrap factor of each face crossed (Sec. 2.4.3).
+ * Returns 0 if the node lies beyond a mirror face (not covered here). */
+static int ghat_periodic(const cplx* gh, const grid_t* g, const int* bc, const cplx* wrap_lo, const cplx* wrap_hi,
+                         int x, int y, int z, int p, cplx* out)
+{
+    int c[3] = {x, y, z};
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    cplx f = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] >= 0 && c[a] < dims[a]) continue;
+        if (bc[a] != BC_PERIODIC) return 0;
+        f *= c[a] < 0 ? wrap_lo[a] : wrap_hi[a];
+        c[a] = (c[a] % dims[a] + dims[a]) % dims[a];
+    }
+    *out = f * gh[pidx(g, c[0], c[1], c[2]) * Q + p];
+    return 1;
+}
+
+static int32_t label_periodic(const int32_t* labels, const grid_t* g, int x, int y, int z)
+{
+    int c[3] = {x, y, z};
+    const int dims[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; ++a) c[a] = (c[a] % dims[a] + dims[a]) % dims[a];
+    return labels[sidx(g, c[0], c[1], c[2])];
+}
+
 /* Scalar parameters as the oracle derives them: out = {tau, r, s}. */
 void lbm_oracle_params(double D, double dt, double dx, double kappa, double* out)
 {
@@ -200,6 +309,73 @@ int lbm_oracle_mask(int nx, int ny, int nz, const int32_t* labels, int n_labels,
 }
 
 /*
+ * Population i arriving at node x = (x, y, z) across the membrane on its
+ * link to y = x - e_i by the general-angle rule (2-D): theta[x][ibar] gives
+ * the membrane normal from x's compartment to y's as cos(theta) e_ibar +
+ * sin(theta) e_perp, e_perp = +y for a link along x and +x for a link along y;
+ * beta = sign(theta) e_perp.  The values at the membrane point x'_i = x'_e =
+ * x_m = x + Delta_m e_ibar and at x'_ii = x_m - e_beta, x'_ee = x_m + e_beta
+ * are extrapolated along the link, quadratically, from the three nearest
+ * nodes of the same compartment: x, x + e_i, x + 2 e_i (shifted by -e_beta
+ * for x'_ii) on x's side; y, y - e_i, y - 2 e_i (shifted by +e_beta for
+ * x'_ee) on y's side.  Returns 0 (the caller keeps the theta = 0 rule) when
+ * one of those nodes lies in another compartment or beyond a mirror face,
+ * or an axis is shorter than 4 nodes.
+ */
+static int angled_arrival(const cplx* gh, const grid_t* g, const int* bc, const int32_t* labels,
+                          const cplx* wlo, const cplx* whi, int x, int y, int z, int i, double dl, double th,
+                          double kappa, double dt, double dx, double eps, cplx* out)
+{
+    if (g->nx < 4 || g->ny < 4) return 0;
+    const int ib = OPP[i];
+    const int ex = EX[i], ey = EY[i];
+    int bet;                                      /* beta */
+    if (ex != 0) bet = th > 0 ? 3 : 4;            /* link along x: beta = +-y */
+    else bet = th > 0 ? 1 : 2;                    /* link along y: beta = +-x */
+    const int bbar = OPP[bet];
+    const int bx = EX[bet], by = EY[bet];
+    const int32_t Lx = label_periodic(labels, g, x, y, z);
+    const int32_t Le = label_periodic(labels, g, x - ex, y - ey, z);
+
+    /* a: alpha = ibar at x and x_ii = x + e_i, abar = i at x;
+     * b: abar = i at x_e = y and x_ee = y - e_i, alpha = ibar at y */
+    const int na[6][3] = {{0, 0, ib}, {ex, ey, ib}, {0, 0, i}, {-ex, -ey, i}, {-2 * ex, -2 * ey, i}, {-ex, -ey, ib}};
+    cplx v[6];
+    for (int k = 0; k < 6; ++k)
+        if (!ghat_periodic(gh, g, bc, wlo, whi, x + na[k][0], y + na[k][1], z, na[k][2], &v[k])) return 0;
+    const cplx a3[3] = {v[0], v[1], v[2]}, b3[3] = {v[3], v[4], v[5]};
+
+    /* Lagrange weights of the nodes at 0, 1, 2 steps for the point t steps
+     * the other way: t = dl on x's side, 1 - dl on y's side */
+    double wi[3], we[3];
+    const double ti = dl, te = 1.0 - dl;
+    wi[0] = (1.0 + ti) * (2.0 + ti) / 2.0; wi[1] = -ti * (2.0 + ti); wi[2] = ti * (1.0 + ti) / 2.0;
+    we[0] = (1.0 + te) * (2.0 + te) / 2.0; we[1] = -te * (2.0 + te); we[2] = te * (1.0 + te) / 2.0;
+    /* the six extrapolated values: {side (0 = x, 1 = y), shift along beta,
+     * population}: p = (g_beta(x'_i), g_beta(x'_ii), g_bbar(x'_i)),
+     * q = (g_bbar(x'_e), g_bbar(x'_ee), g_beta(x'_e)) */
+    const int pts[6][3] = {{0, 0, bet}, {0, -1, bet}, {0, 0, bbar}, {1, 0, bbar}, {1, 1, bbar}, {1, 0, bet}};
+    cplx pq[6];
+    for (int k = 0; k < 6; ++k) {
+        const int side = pts[k][0], sh = pts[k][1], pop = pts[k][2];
+        cplx acc = 0;
+        for (int m = 0; m < 3; ++m) {
+            /* x side: x + m e_i; y side: y - m e_i = x - (1 + m) e_i */
+            const int step = side ? -(1 + m) : m;
+            const int nx_ = x + step * ex + sh * bx, ny_ = y + step * ey + sh * by;
+            if (label_periodic(labels, g, nx_, ny_, z) != (side ? Le : Lx)) return 0;
+            cplx u;
+            if (!ghat_periodic(gh, g, bc, wlo, whi, nx_, ny_, z, pop, &u)) return 0;
+            acc += (side ? we[m] : wi[m]) * u;
+        }
+        pq[k] = acc;
+    }
+    const cplx p3[3] = {pq[0], pq[1], pq[2]}, q3[3] = {pq[3], pq[4], pq[5]};
+    *out = angled_link(dl, th, kappa, dt, dx, eps, a3, b3, p3, q3);
+    return 1;
+}
+
+/*
  * One complete run from the initial condition M = 1 + 0i (Sec. 2.1) to
  * t = n_steps * dt.
  *
@@ -218,11 +394,12 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
                     const int* bc, int n_phases, const double* D, const double* T2,
                     double kappa, double dt, long n_steps, const double* f,
-                    const double* gG, int n_threads, const double* delta, int substeps, int d2q5,
-                    double* Z_out, double* field_out, double* series_out, double* state_out)
+                    const double* gG, int n_threads, const double* delta, const double* theta, int substeps,
+                    int d2q5, double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0 || substeps < 1) return -1;
     if (d2q5 && nz != 1) return -1;
+    if (theta && (!delta || !d2q5)) return -1;   /* the angle rule is the paper's 2-D one */
     const int nq = d2q5 ? 5 : Q;                  /* populations in use */
     const double eps = d2q5 ? EPS_D2 : EPS_D;
     const double* w = d2q5 ? W2 : W;
@@ -265,6 +442,9 @@ static int run_impl(int nx, int ny, int nz, double dx,
     if (delta)
         for (size_t i = 0; i < 6 * N; ++i)
             if (!(delta[i] > 0.0 && delta[i] < 1.0)) return -1;
+    if (theta)
+        for (size_t i = 0; i < 6 * N; ++i)
+            if (!(fabs(theta[i]) < 1.5707963267948966)) return -1;
 
     cplx* gs = malloc(sizeof(cplx) * Q * N);     /* g_i(x, t^k)             */
     cplx* gh = malloc(sizeof(cplx) * Q * NP);    /* hat g_i with buffers    */
@@ -369,6 +549,14 @@ static int run_impl(int nx, int ny, int nz, double dx,
                 }
         }
 
+        /* wrap factors of this step per axis (for the corner nodes of the
+         * general-angle rule) */
+        cplx wlo[3], whi[3];
+        for (int a = 0; a < 3; ++a) {
+            wlo[a] = cexp(I * gG[a] * dims[a] * dx * F);
+            whi[a] = cexp(-I * gG[a] * dims[a] * dx * F);
+        }
+
         /* 3. Streaming (Eq. streaming_LBM), with the half-link membrane rule
          *    on links whose end nodes carry different labels (Eqs. B2a_text,
          *    B2b_text with the B5 coefficients): the population arriving at x
@@ -401,8 +589,13 @@ static int run_impl(int nx, int ny, int nz, double dx,
                         size_t pb = pidx(&g, x + EX[i], y + EY[i], z + EZ[i]);
                         size_t pe = pidx(&g, x - 2 * EX[i], y - 2 * EY[i], z - 2 * EZ[i]);
                         if (delta && !isinf(kappa) && lab[pb] == Lx && lab[pe] == lab[py_]) {
+                            const double dl = delta[si * 6 + (ib - 1)];
+                            const double th = theta ? theta[si * 6 + (ib - 1)] : 0.0;
+                            if (th != 0.0 && angled_arrival(gh, &g, bc, labels, wlo, whi, x, y, z, i, dl, th, kappa,
+                                                            dt, dx, eps, &gbar[i]))
+                                continue;
                             double A[3], B[3];
-                            link_coefficients(delta[si * 6 + (ib - 1)], kappa, dt, dx, eps, A, B);
+                            link_coefficients(dl, kappa, dt, dx, eps, A, B);
                             gbar[i] = A[0] * gh[pi * Q + ib] + A[1] * gh[pb * Q + ib] + A[2] * gh[pi * Q + i] +
                                       B[0] * gh[py_ * Q + i] + B[1] * gh[pe * Q + i] + B[2] * gh[py_ * Q + ib];
                         } else {
@@ -453,7 +646,7 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
                    double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, NULL, 1, 0, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, NULL, NULL, 1, 0, Z_out, field_out, series_out, state_out);
 }
 
 /*
@@ -472,23 +665,26 @@ int lbm_oracle_run_links(int nx, int ny, int nz, double dx,
 {
     if (!delta) return -1;
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, 1, 0, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, NULL, 1, 0, Z_out, field_out, series_out, state_out);
 }
 
 /*
  * General form: optional membrane positions (as lbm_oracle_run_links, or
  * NULL), `substeps` >= 1 reaction steps of dt / substeps after each
  * diffusion step (Sec. 2.3, dt = k dt'; f then holds n_steps * substeps
- * samples on the dt' grid), and d2q5 != 0 for the 2-D D2Q5 lattice of
- * Sec. 2.3 (nz = 1).
+ * samples on the dt' grid), d2q5 != 0 for the 2-D D2Q5 lattice of
+ * Sec. 2.3 (nz = 1), and with it optional membrane angles theta[6*s + (j-1)]
+ * (radians, |theta| < pi/2, read on membrane links with a position) for
+ * the general-angle rule (angled_arrival); a consistent input has
+ * theta[s][j] = -theta[s + e_j][jbar].
  */
 int lbm_oracle_run_ex(int nx, int ny, int nz, double dx,
                       const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
                       const int* bc, int n_phases, const double* D, const double* T2,
                       double kappa, double dt, long n_steps, const double* f,
-                      const double* gG, int n_threads, const double* delta, int substeps, int d2q5,
-                      double* Z_out, double* field_out, double* series_out, double* state_out)
+                      const double* gG, int n_threads, const double* delta, const double* theta, int substeps,
+                      int d2q5, double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, substeps, d2q5, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, theta, substeps, d2q5, Z_out, field_out, series_out, state_out);
 }

@@ -17,10 +17,14 @@ micrograph, here replaced by a Voronoi tessellation):
 * ``spheres``    -- non-overlapping sphere pack, uniform radii
 * ``voronoi_tissue`` -- Voronoi cells + extracellular band + vessel tubes
 * ``walls``      -- planes at arbitrary positions (membranes off the half-links)
+* ``stripes``    -- 2-D periodic stripes oblique to the lattice (one z plane)
+* ``disks``      -- 2-D discs at given centres and radii (one z plane)
 
-``link_distances`` gives, for the analytic geometries (walls, spheres,
-cylinders), where each membrane cuts its lattice link: the input of the
-theta = 0 membrane rule with a per-link distance (Eqs. B4a-B4c).
+``link_distances`` gives, for the analytic geometries (walls, stripes,
+spheres, cylinders, discs), where each membrane cuts its lattice link: the
+input of the membrane rule with a per-link distance (Eqs. B4a-B4c);
+``link_angles`` gives, for the 2-D ones, the angle between the membrane
+normal and each cut link (the general-angle rule of Appendix B).
 """
 from __future__ import annotations
 
@@ -116,7 +120,137 @@ def walls(n, dx, positions, axis=0, cross=(1, 1), phases=None, periodic=True):
                     {"kind": "walls", "positions": pos.tolist(), "axis": axis})
 
 
+def stripes(n, dx, slope=(1, 1), width=0.5, offset=0.0, phases=None):
+    """Periodic stripes on an n x n grid of one z plane, running along
+    (q, p) for ``slope`` = (p, q) (coprime integers): with the unit normal
+    N = (-p, q) / sqrt(p^2 + q^2) and the pattern period Lam = n dx /
+    sqrt(p^2 + q^2) (so the pattern is periodic on the box), label 1 where
+    (N.x - offset) mod Lam < width * Lam, label 0 elsewhere; the walls are the
+    lines N.x = offset + m Lam and N.x = offset + width Lam + m Lam."""
+    p, q = slope
+    h = math.hypot(p, q)
+    N = np.array([-p / h, q / h])
+    lam = n * dx / h
+    xk = np.arange(n) * dx
+    u = N[0] * xk[None, :] + N[1] * xk[:, None]
+    lab2 = (np.mod(u - offset, lam) < width * lam).astype(np.int32)
+    labels = np.ascontiguousarray(lab2[None], np.int32)
+    pol = np.zeros(2, np.uint8) if phases is None else np.array(phases[:2], np.uint8)
+    return Geometry(labels, pol, dx, {"kind": "stripes", "normal": N.tolist(), "period": lam,
+                                      "walls": [offset, offset + width * lam]})
+
+
+def disks(n, dx, centers, radii, phases=None):
+    """Discs (x, y centres in um, radii in um) on an n x n periodic grid of one
+    z plane: label j >= 1 inside disc j (minimum image; the first disc wins
+    where two overlap), label 0 outside."""
+    L = n * dx
+    xk = np.arange(n) * dx
+    lab2 = np.zeros((n, n), np.int32)
+    for j, (c, r) in enumerate(zip(centers, radii)):
+        dxv = xk[None, :] - c[0]
+        dyv = xk[:, None] - c[1]
+        dxv -= L * np.round(dxv / L)
+        dyv -= L * np.round(dyv / L)
+        lab2[(dxv * dxv + dyv * dyv < r * r) & (lab2 == 0)] = j + 1
+    pol = np.full(len(radii) + 1, PHASE_IN, np.uint8)
+    pol[0] = PHASE_EX
+    if phases is not None:
+        pol[:] = phases[1]
+        pol[0] = phases[0]
+    g = Geometry(np.ascontiguousarray(lab2[None], np.int32), pol, dx,
+                 {"kind": "cylinders", "centers": np.asarray(centers, float).tolist(),
+                  "radii": np.asarray(radii, float).tolist()})
+    g.info["intra_fraction"] = float((lab2 > 0).mean())
+    return g
+
+
 _DIRS = ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))   # +x -x +y -y +z -z
+
+
+def _membrane_links(lab, bc, j):
+    """Nodes whose link along direction j carries a membrane (periodic wrap;
+    none across a mirror face)."""
+    nz, ny, nx = lab.shape
+    dims = (nx, ny, nz)
+    e = _DIRS[j]
+    a = j // 2
+    nb = np.roll(lab, -e[a], axis=2 - a)
+    memb = nb != lab
+    if bc[a] != 0:
+        zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        node = (xx, yy, zz)[a]
+        memb &= node != (dims[a] - 1 if e[a] > 0 else 0)
+    return memb, nb
+
+
+def _stripe_cut(geom, idx, j):
+    """Distance (um) along direction j from the nodes idx to the first stripe
+    wall, for a ``stripes`` geometry."""
+    N = np.asarray(geom.info["normal"])
+    lam = geom.info["period"]
+    e = np.array(_DIRS[j][:2], float)
+    ne = N @ e
+    px = np.stack([idx[2] * geom.dx, idx[1] * geom.dx], 1)
+    u = px @ N
+    best = np.full(len(u), np.inf)
+    for w in geom.info["walls"]:
+        for m in range(-3, 4):
+            # N.(x + t e) = w + (k + m) Lam with k the period index near x
+            k = np.floor((u - w) / lam)
+            t = (w + (k + m) * lam - u) / ne
+            ok = (t > 0) & (t <= geom.dx * (1 + 1e-12))
+            best = np.where(ok & (t < best), t, best)
+    return best
+
+
+def link_angles(geom: Geometry, bc=(0, 0, 0)):
+    """Angle between the membrane normal and each cut link, for the 2-D
+    analytic geometries (stripes, discs).
+
+    Returns float32 [6, 1, ny, nx]: entry j at node s is theta such that the
+    unit normal of the membrane on the link from s to s + e_j, pointing from
+    s's compartment to the other, is cos(theta) e_j + sin(theta) e_perp, with
+    e_perp = +y for the x links and +x for the y links (so the two ends of a
+    link carry opposite angles); 0 where the link carries no membrane and on
+    the z links.  |theta| is kept below pi/2 - 1e-3.
+    """
+    lab = geom.labels
+    nz, ny, nx = lab.shape
+    if nz != 1:
+        raise ValueError("membrane angles are defined for one-plane (2-D) geometries")
+    kind = geom.info.get("kind")
+    if kind not in ("stripes", "cylinders"):
+        raise ValueError(f"no membrane angles for a '{kind}' geometry")
+    out = np.zeros((6, 1, ny, nx), np.float32)
+    dl = link_distances(geom, bc)
+    L = np.array([nx, ny], float) * geom.dx
+    for j in range(4):
+        memb, nb = _membrane_links(lab, bc, j)
+        if not memb.any():
+            continue
+        idx = np.nonzero(memb)
+        e = np.array(_DIRS[j][:2], float)
+        perp = np.array([0.0, 1.0]) if j < 2 else np.array([1.0, 0.0])
+        if kind == "stripes":
+            N = np.asarray(geom.info["normal"], float)
+            n_out = np.sign(N @ e) * np.tile(N, (len(idx[0]), 1))
+        else:
+            cen = np.asarray(geom.info["centers"], float)[:, :2]
+            la, lb = lab[idx], nb[idx]
+            k = np.where((la > 0) & (lb > 0), np.minimum(la, lb), np.where(la > 0, la, lb)) - 1
+            px = np.stack([idx[2] * geom.dx, idx[1] * geom.dx], 1)
+            cut = px + (dl[j][idx].astype(np.float64) * geom.dx)[:, None] * e[None, :]
+            r = cut - cen[k]
+            r -= L * np.round(r / L)
+            r /= np.linalg.norm(r, axis=1)[:, None]
+            # outward from the disc; from s's side towards the other
+            n_out = np.where((la == k + 1)[:, None], r, -r)
+        c = n_out @ e
+        sn = n_out @ perp
+        th = np.arctan2(sn, np.maximum(c, 1e-12))
+        out[j][idx] = np.clip(th, -(math.pi / 2 - 1e-3), math.pi / 2 - 1e-3)
+    return out
 
 
 def link_distances(geom: Geometry, bc=(0, 0, 0)):
@@ -135,7 +269,7 @@ def link_distances(geom: Geometry, bc=(0, 0, 0)):
     dx = geom.dx
     out = np.full((6, nz, ny, nx), 0.5, np.float32)
     kind = geom.info.get("kind")
-    if kind not in ("walls", "spheres", "cylinders"):
+    if kind not in ("walls", "spheres", "cylinders", "stripes"):
         raise ValueError(f"no sub-voxel membrane positions for a '{kind}' geometry")
     zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     node = [xx, yy, zz]
@@ -152,7 +286,11 @@ def link_distances(geom: Geometry, bc=(0, 0, 0)):
         if not memb.any():
             continue
         idx = np.nonzero(memb)
-        if kind == "walls":
+        if kind == "stripes":
+            if a == 2:
+                continue
+            d = _stripe_cut(geom, idx, j) / dx
+        elif kind == "walls":
             if geom.info["axis"] != a:
                 continue
             pos = np.asarray(geom.info["positions"])
