@@ -44,7 +44,7 @@ enum {
     LBMBT_EINVAL = -1,       /* invalid argument                                */
     LBMBT_ENOMEM = -2,       /* device or host allocation failed                */
     LBMBT_ECUDA = -3,        /* CUDA runtime error (message has the CUDA text)  */
-    LBMBT_EUNSTABLE = -4,    /* tau <= 1/2 (Eq. tau_def)                        */
+    LBMBT_EUNSTABLE = -4,    /* tau <= 1/2 (Eq. tau_def); < 0.75 with angles     */
     LBMBT_EUNSUPPORTED = -5, /* mirror face with a gradient neither normal nor
                                 parallel to it (Sec. 2.4.4)                     */
     LBMBT_EDEVICE = -6,      /* a device-side check failed (e.g. bad label)     */
@@ -158,6 +158,31 @@ int lbmbt_slab_set_halos(lbmbt_ctx* ctx, int member, const void* lo_in, const vo
  * return EUNSUPPORTED.
  */
 int lbmbt_set_link_distances(lbmbt_ctx* ctx, int index, const float* delta, int delta_on_device);
+
+/*
+ * Membrane angles on the links of a one-plane (2-D) geometry `index`, for
+ * the general-angle membrane rule (Appendix B: the Dirichlet and Neumann
+ * relations of Eqs. dirichlet_1-neumann_2, the flux relations phi_1 and
+ * phi_2, Eqs. B1 and B1.5; coefficients as Eqs. B3a-B3c).  theta: float32
+ * [6][1][ny][nx], host or device (theta_on_device != 0 means device); entry
+ * j-1 at a node is the signed angle between the membrane normal, pointing
+ * from the node's compartment to the neighbour's, and its link to the
+ * neighbour across +e_j: normal = cos(theta) e_j + sin(theta) e_perp, e_perp
+ * = +y for x links and +x for y links; |theta| < pi/2 (host input is
+ * checked: EINVAL); a consistent input gives the two ends of a link opposite
+ * angles.  The values at the membrane point and one lattice step to either
+ * side along the perpendicular direction are extrapolated quadratically along
+ * the link from the three nearest nodes of the same compartment; where such
+ * a node lies in another compartment or beyond a mirror face, or an axis is
+ * shorter than 4 nodes, the link keeps the theta = 0 rule.  Requires the
+ * positions (lbmbt_set_link_distances, else EINVAL), a geometry of one z
+ * plane (else EINVAL) and the D2Q5 lattice (LBMBT_OPT_LATTICE = 1; a run
+ * on D3Q7 returns EUNSUPPORTED).  The extrapolation is unstable for tau near
+ * 1/2: a run needs tau >= 0.75 in every phase (else EUNSTABLE).  Removing
+ * the positions removes the angles; theta = NULL removes the angles only.
+ * The paper gives this rule in 2-D only; there is no 3-D form here.
+ */
+int lbmbt_set_link_angles(lbmbt_ctx* ctx, int index, const float* theta, int theta_on_device);
 
 /* Copy the per-node mask byte of geometry `index` (encoding above) to host
  * memory mask_out[nz*ny*nx]. */

@@ -36,6 +36,7 @@ struct Geom {
     int slab = 0, z0 = 0, nzg = 0;
     int zkind[2] = {0, 0};
     float* d_dlt = nullptr;       // membrane positions on the links, [6][plane], or nullptr
+    float* d_dth = nullptr;       // membrane angles on the links (2-D), [6][plane], or nullptr
 };
 
 constexpr int GRAPH_CHUNK = 16;
@@ -247,7 +248,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
     drop_graph(c);
-    for (auto& g : c->geoms) { cudaFree(g.d_mask); cudaFree(g.d_dlt); }
+    for (auto& g : c->geoms) { cudaFree(g.d_mask); cudaFree(g.d_dlt); cudaFree(g.d_dth); }
     cudaFree(c->d_f); cudaFree(c->d_F);
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
@@ -334,7 +335,7 @@ extern "C" int lbmbt_set_geometry(lbmbt_ctx* c, int nx, int ny, int nz, double d
     int rc = make_geom(c, nx, ny, nz, dx, labels, on_dev, n_labels, pol, bc, &g);
     if (rc) return rc;
     invalidate_run(c);
-    for (auto& o : c->geoms) { cudaFree(o.d_mask); cudaFree(o.d_dlt); }
+    for (auto& o : c->geoms) { cudaFree(o.d_mask); cudaFree(o.d_dlt); cudaFree(o.d_dth); }
     c->geoms.clear();
     c->geoms.push_back(g);
     return LBMBT_OK;
@@ -433,7 +434,7 @@ extern "C" int lbmbt_set_geometry_slab(lbmbt_ctx* c, int nx, int ny, int nz, dou
     g.zkind[0] = lo_kind;
     g.zkind[1] = hi_kind;
     invalidate_run(c);
-    for (auto& o : c->geoms) { cudaFree(o.d_mask); cudaFree(o.d_dlt); }
+    for (auto& o : c->geoms) { cudaFree(o.d_mask); cudaFree(o.d_dlt); cudaFree(o.d_dth); }
     c->geoms.clear();
     c->geoms.push_back(g);
     return LBMBT_OK;
@@ -465,7 +466,11 @@ extern "C" int lbmbt_set_link_distances(lbmbt_ctx* c, int index, const float* de
     invalidate_run(c);
     cudaFree(g.d_dlt);
     g.d_dlt = nullptr;
-    if (!delta) return LBMBT_OK;
+    if (!delta) {   // the angles go with the positions
+        cudaFree(g.d_dth);
+        g.d_dth = nullptr;
+        return LBMBT_OK;
+    }
     if (g.slab) return fail(c, LBMBT_EUNSUPPORTED, "membrane positions on a slab are not supported");
     if (!on_device)
         for (long long i = 0; i < 6 * g.N; ++i)
@@ -476,6 +481,42 @@ extern "C" int lbmbt_set_link_distances(lbmbt_ctx* c, int index, const float* de
     const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     for (int j = 0; j < 6; ++j)
         CU(c, cudaMemcpyAsync(g.d_dlt + j * plane, delta + j * g.N, sizeof(float) * g.N, kind, c->stream));
+    return sync(c);
+}
+
+// Smallest tau (every phase) at which runs with membrane angles are accepted.
+constexpr double ANGLE_TAU_MIN = 0.75;
+
+// Membrane angles on the links of a one-plane geometry `index` (the
+// general-angle rule of Appendix B): theta [6][1][ny][nx] float32, entry j-1
+// at a node is the signed angle between the membrane normal (from the node's
+// compartment to the neighbour's) and its link to the neighbour across +e_j,
+// normal = cos(theta) e_j + sin(theta) e_perp with e_perp = +y for x links,
+// +x for y links; |theta| < pi/2.  Needs the positions first.  NULL removes
+// them.
+extern "C" int lbmbt_set_link_angles(lbmbt_ctx* c, int index, const float* theta, int on_device)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (index < 0 || index >= (int)c->geoms.size()) return fail(c, LBMBT_EINVAL, "geometry %d not set", index);
+    int rc = set_device(c);
+    if (rc) return rc;
+    Geom& g = c->geoms[index];
+    invalidate_run(c);
+    cudaFree(g.d_dth);
+    g.d_dth = nullptr;
+    if (!theta) return LBMBT_OK;
+    if (!g.d_dlt) return fail(c, LBMBT_EINVAL, "membrane angles need the membrane positions first");
+    if (g.nz != 1) return fail(c, LBMBT_EINVAL, "membrane angles are defined on one-plane (2-D) grids only");
+    if (!on_device)
+        for (long long i = 0; i < 6 * g.N; ++i)
+            if (!(std::fabs(theta[i]) < 1.5707963f))
+                return fail(c, LBMBT_EINVAL, "membrane angle %g at entry %lld not in (-pi/2, pi/2)",
+                            (double)theta[i], i);
+    const long long plane = (g.N + 63) / 64 * 64;
+    CU(c, cudaMalloc(&g.d_dth, sizeof(float) * 6 * plane));
+    const auto kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int j = 0; j < 6; ++j)
+        CU(c, cudaMemcpyAsync(g.d_dth + j * plane, theta + j * g.N, sizeof(float) * g.N, kind, c->stream));
     return sync(c);
 }
 
@@ -678,8 +719,10 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.partial = c->d_partial;
     a.fac = c->d_fac;
     a.links = 0;
-    for (auto& d : c->descs)
-        if (d.dlt) a.links = 1;
+    for (auto& d : c->descs) {
+        if (d.dth) a.links = 2;
+        else if (d.dlt && a.links == 0) a.links = 1;
+    }
     if (c->lattice == 1) { a.w0 = 1.f / 3.f; a.wxy = 1.f / 6.f; a.wz = 0.f; }
     else { a.w0 = W0; a.wxy = WI; a.wz = WI; }
     return a;
@@ -873,6 +916,20 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
             if (g.slab) return fail(c, LBMBT_EUNSUPPORTED, "membrane positions on a slab are not supported");
             d.dlt = g.d_dlt;
             d.lrho = (float)(kap * c->dt / (eps * g.dx));
+            if (g.d_dth) {
+                if (c->lattice != 1)
+                    return fail(c, LBMBT_EUNSUPPORTED, "membrane angles need the D2Q5 lattice (LBMBT_OPT_LATTICE 1)");
+                // the general-angle rule's extrapolation is unstable for tau
+                // near 1/2 (measured: diverging at tau 0.65, and at 0.7 with
+                // grazing links of high permeability)
+                for (int p = 0; p < c->n_phases; ++p) {
+                    const double tau = 0.5 + c->dt * c->D[p] / (eps * g.dx * g.dx);
+                    if (!(tau >= ANGLE_TAU_MIN))
+                        return fail(c, LBMBT_EUNSTABLE, "membrane angles need tau >= %.2f in every phase (phase %d: %.4g)",
+                                    ANGLE_TAU_MIN, p, tau);
+                }
+                d.dth = g.d_dth;
+            }
         }
         div_magic((unsigned)g.nx, &d.div_m[0], &d.div_s[0]);
         div_magic((unsigned)g.ny, &d.div_m[1], &d.div_s[1]);

@@ -73,6 +73,10 @@ struct MemberDesc {
     // link to s + e_j; nullptr = half-link rule (Eq. B5) everywhere
     const float* dlt;
     float lrho;           // kappa dt / (eps_D dx): the coefficients depend on it only
+    // membrane angles (one-plane D2Q5 grids, general-angle rule of Appendix
+    // B): dth[(j-1)*plane + s] = signed angle between the membrane normal and
+    // the link from s to s + e_j; nullptr = theta = 0 everywhere
+    const float* dth;
 };
 
 // Step control word in device memory.  The sweep reads k here; a one-block
@@ -99,8 +103,8 @@ struct SweepArgs {
     const double* F;              // F_k = sum_{m<k} f_m dt, per step
     double2* partial;             // per-tile (sum Re M, sum Im M)
     const float2* fac;            // [2][n_members][6] boundary factors, level k & 1
-    int links;                    // a member has membrane positions (register sweep
-                                  // variant with the Eqs. B4a-B4c rule)
+    int links;                    // 1: a member has membrane positions (register sweep
+                                  // variant with the Eqs. B4a-B4c rule); 2: and angles
     float w0, wxy, wz;            // equilibrium weights (register sweep, init):
                                   // D3Q7 1/4, 1/8, 1/8; D2Q5 1/3, 1/6, 0 (Sec. 2.3)
 };

@@ -99,7 +99,8 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
 constexpr int LINK_SLOTS = 32 * 6;
 inline size_t link_smem_bytes(int block) { return (size_t)(block / 32) * LINK_SLOTS * (sizeof(float2) + 1); }
 
-template <int SPT, bool LINKS>
+// LINKS: 0 half-link rule only, 1 membrane positions, 2 positions and angles
+template <int SPT, int LINKS>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a)
 {
     __shared__ double2 s_red[32];
@@ -209,7 +210,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
                     const unsigned sl = it >> 3;
                     const int xo = __shfl_sync(0xffffffffu, x, sl), yo = __shfl_sync(0xffffffffu, y, sl),
                               zo = __shfl_sync(0xffffffffu, z, sl);
-                    if (t < K) res[t] = link_population(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
+                    if (t < K)
+                        res[t] = link_population<LINKS == 2>(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
                 }
                 __syncwarp();
                 unsigned o = incl - __popc(cand);
@@ -268,15 +270,17 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
 template <int SPT>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 {
-    sweep_body<SPT, false>(a);
+    sweep_body<SPT, 0>(a);
 }
 
 // With membrane positions: two blocks of 512 per SM (64 registers), since
 // the position rule's extra loads need more warps in flight to hide them.
-template <int SPT>
-__global__ void __launch_bounds__(512, 2) sweep_links_kernel(const SweepArgs a)
+// ANG: with membrane angles too (one-plane D2Q5 grids); the general-angle
+// rule's 18 extrapolation reads would spill at 64 registers, so one block.
+template <int SPT, bool ANG>
+__global__ void __launch_bounds__(512, ANG ? 1 : 2) sweep_links_kernel(const SweepArgs a)
 {
-    sweep_body<SPT, true>(a);
+    sweep_body<SPT, ANG ? 2 : 1>(a);
 }
 
 // Control word: set (or advance k), then the boundary factors of the new step
@@ -379,15 +383,18 @@ cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int s
 {
     switch (spt) {
     case 1:
-        if (a.links) sweep_links_kernel<1><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        if (a.links == 2) sweep_links_kernel<1, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        else if (a.links) sweep_links_kernel<1, false><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
         else sweep_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 2:
-        if (a.links) sweep_links_kernel<2><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        if (a.links == 2) sweep_links_kernel<2, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        else if (a.links) sweep_links_kernel<2, false><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
         else sweep_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 4:
-        if (a.links) sweep_links_kernel<4><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        if (a.links == 2) sweep_links_kernel<4, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        else if (a.links) sweep_links_kernel<4, false><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
         else sweep_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;

@@ -34,6 +34,7 @@ EXPORTS = [
     "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
     "lbmbt_launch_count", "lbmbt_sweep_noalloc", "lbmbt_set_geometry_slab", "lbmbt_slab_faces",
     "lbmbt_slab_set_halos", "lbmbt_set_field", "lbmbt_set_link_distances", "lbmbt_set_sequence_substeps",
+    "lbmbt_set_link_angles",
 ]
 
 
@@ -85,6 +86,7 @@ def lib():
                 "lbmbt_slab_set_halos": [P, I, P, P],
                 "lbmbt_set_field": [P, P],
                 "lbmbt_set_link_distances": [P, I, P, I],
+                "lbmbt_set_link_angles": [P, I, P, I],
                 "lbmbt_set_sequence_substeps": [P, D, I64, I, P, P],
             }
             for name, args in sig.items():
@@ -256,6 +258,17 @@ class Solver:
         if not on_dev:
             delta = np.ascontiguousarray(delta, np.float32)
         self._chk(self.L.lbmbt_set_link_distances(self.h, int(index), _p(delta), int(on_dev)), "set_link_distances")
+
+    def set_link_angles(self, theta, index=0):
+        """Membrane angles on the links of a one-plane geometry (float32
+        [6, 1, ny, nx], numpy or torch CUDA), or None to remove them."""
+        if theta is None:
+            self._chk(self.L.lbmbt_set_link_angles(self.h, int(index), None, 0), "set_link_angles")
+            return
+        on_dev = hasattr(theta, "is_cuda") and theta.is_cuda
+        if not on_dev:
+            theta = np.ascontiguousarray(theta, np.float32)
+        self._chk(self.L.lbmbt_set_link_angles(self.h, int(index), _p(theta), int(on_dev)), "set_link_angles")
 
     def get_mask(self, index=0, shape=None):
         n = self.n_sites[index]
