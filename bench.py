@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -402,6 +403,70 @@ def run_links(args):
     return 0
 
 
+# ---------------------------------------------------------------- membrane-rule study
+def run_membrane_study(args):
+    """The paper's four-variant membrane study (Sec. 3.6) on the GPU: a 40 um
+    disc at intracellular fraction 0.5 in a periodic square (D 2.3 um^2/ms
+    on both sides, kappa 0.05 um/ms, PGSE delta 5 / Delta 20 ms, b 1000
+    s/mm^2 along x, tau 0.8, D2Q5 on one plane), S at the echo for the full
+    general-angle rule, Delta_m = 1/2 with the angles, theta = 0 with the
+    positions, and the half-link rule, on grids of 100^2 to 800^2.  The
+    reported throughput is the full rule's sweep on the finest grid."""
+    import torch
+    from paper_1907_00908_gb300 import lbmbt, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    D, kap, b, delta, Delta, R = 2.3, 0.05, 1000.0, 5.0, 20.0, 20.0
+    Lb = math.sqrt(math.pi * R * R / 0.5)
+    study, timing = {}, {}
+    grids = (100, 200, 400, 800)
+    with Clocks(0) as clk:
+        for n in grids:
+            dx = Lb / n
+            dt = delta / math.ceil(delta / (0.3 * (1.0 / 3.0) * dx * dx / D))   # tau <= 0.8
+            g = synth.disks(n, dx, [[Lb / 2 + 0.123, Lb / 2 - 0.071]], [R])
+            dl, th = synth.link_distances(g, (0, 0, 0)), synth.link_angles(g, (0, 0, 0))
+            gG, f = lbmbt.pgse(b, delta, Delta, dt, (1, 0, 0))
+            row = {}
+            for name, pos, ang in (("full", dl, th), ("delta_half", np.full_like(dl, 0.5), th),
+                                   ("theta_zero", dl, None), ("half_link", None, None)):
+                s = lbmbt.Solver(0, stream)
+                s.set_option(lbmbt.OPT_LATTICE, 1)
+                s.set_geometry(g.labels, g.phase_of_label, dx, (0, 0, 0))
+                if pos is not None:
+                    s.set_link_distances(pos)
+                if ang is not None:
+                    s.set_link_angles(ang)
+                s.set_phases([D, D], [math.inf, math.inf])
+                s.set_sequence(dt, f, gG)
+                s.prepare(lbmbt.Solver.members([gG], 0, kap))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                sig = s.advance(len(f), want_signal=True, n_members=1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                row[name] = float(abs(sig[0, 0] + 1j * sig[0, 1]) / g.n_sites)
+                if n == grids[-1]:
+                    timing[name] = {"MLUPS": g.n_sites * len(f) / (ms * 1e-3) / 1e6, "ms_run": ms, "steps": len(f)}
+                s.close()
+            study[str(n)] = {"dx_um": dx, "dt_ms": dt, "steps": len(f), "S": row}
+    v = timing["full"]["MLUPS"]
+    fin = study[str(grids[-1])]["S"]
+    line = {"metric": "MLUPS (2-D sweep, membrane positions and angles, FP32)", "value": v, "unit": "MLUPS",
+            "n_gpus": 1, "steps": timing["full"]["steps"], "warmup": 0,
+            "ms_per_step": timing["full"]["ms_run"] / timing["full"]["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "disc40um_fraction0.5_four_membrane_variants", "grids": list(grids),
+                       "kappa_um_ms": kap, "D": D, "b_s_mm2": b, "lattice": "D2Q5"},
+            "study": study,
+            "finest_grid_relative_to_full": {k: (val - fin["full"]) / fin["full"] for k, val in fin.items()},
+            "timing_finest_grid": timing, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- scheme variants
 def run_variants(args):
     """The paper's cheap variants, each timed against its plain counterpart:
@@ -547,12 +612,14 @@ def main():
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
     ap.add_argument("--slabs", type=int, default=4, help="slab workload: number of z slabs")
-    ap.add_argument("--workload", default="tissue512", choices=["tissue512", "batch", "adjoint", "slab", "links", "variants"],
+    ap.add_argument("--workload", default="tissue512",
+                    choices=["tissue512", "batch", "adjoint", "slab", "links", "variants", "membrane_study"],
                     help="tissue512 (default): the 512^3 tissue batch of 3 directions; batch: 528 members on "
                          "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack; slab: the "
                          "tissue batch cut into --slabs z slabs with a face exchange per step; links: membranes at "
                          "their exact positions on the links (256^3 cylinders) against the half-link rule; variants: "
-                         "D2Q5 and reaction sub-steps against their plain counterparts")
+                         "D2Q5 and reaction sub-steps against their plain counterparts; membrane_study: the "
+                         "paper's four membrane-rule variants on a 40 um disc, 100^2 to 800^2")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -564,6 +631,8 @@ def main():
         return run_slab(args)
     if args.workload == "links":
         return run_links(args)
+    if args.workload == "membrane_study":
+        return run_membrane_study(args)
     if args.workload == "variants":
         return run_variants(args)
 
