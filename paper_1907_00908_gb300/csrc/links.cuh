@@ -230,7 +230,7 @@ __device__ __forceinline__ float2 link_population(const MemberDesc* __restrict__
     const float2 vf = read_along(src, P, so, i, ax, -2 * e, c, dim, st, bl, bh, fac);    // g_i(y - e_i)
     const float2 wy = read_along(src, P, so, ib, ax, -e, c, dim, st, bl, bh, fac);       // g_ib(y)
     if (mky & (1u << (ib - 1))) return mix(own_ib, v1, sd->s_share);
-    if (ANG) {
+    if (ANG && sd->dth != nullptr) {   // a batch member may have positions without angles
         const float th = __ldg(sd->dth + (size_t)(ib - 1) * P + so);
         float2 r;
         if (th != 0.f && angled_population(sd, src, fac, xo, yo, i, dl, th, own_ib, vb, own_i, v1, vf, wy, &r))

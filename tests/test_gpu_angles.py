@@ -173,3 +173,36 @@ def test_angles_refused_where_unsupported(lb):
     assert e.value.code == -1
     s.close()
     assert r1["S"] > 0
+
+
+def test_batch_mixes_members_with_and_without_angles(lb):
+    """One launch of the angle kernel over a disc pack with angles, the same
+    pack with positions only, and oblique stripes with angles, each against
+    its own oracle run."""
+    g1 = synth.disks(40, 0.5, [[6.1, 7.3], [14.2, 13.9]], [4.2, 3.6])
+    g2 = synth.stripes(32, 0.5, (1, 2), 0.4, 0.21, phases=[0, 1])
+    dl1, th1 = synth.link_distances(g1, (0, 0, 0)), synth.link_angles(g1, (0, 0, 0))
+    dl2, th2 = synth.link_distances(g2, (0, 0, 0)), synth.link_angles(g2, (0, 0, 0))
+    D, T2 = [2.0, 1.0], [80.0, 50.0]
+    gG, f = oracle.pgse(1500.0, 0.5, 1.0, DT, (1.0, 0.0, 0.0))
+    gG2 = np.array([0.6, 0.8, 0.0]) * np.linalg.norm(gG)
+    s = lb.Solver(0)
+    s.set_option(lb.OPT_LATTICE, 1)
+    s.set_geometry(g1.labels, g1.phase_of_label, g1.dx, (0, 0, 0))
+    s.add_geometry(g1.labels, g1.phase_of_label, g1.dx, (0, 0, 0))
+    s.add_geometry(g2.labels, g2.phase_of_label, g2.dx, (0, 0, 0))
+    s.set_link_distances(dl1, index=0)
+    s.set_link_angles(th1, index=0)
+    s.set_link_distances(dl1, index=1)
+    s.set_link_distances(dl2, index=2)
+    s.set_link_angles(th2, index=2)
+    s.set_phases(D, T2)
+    s.set_sequence(DT, f, gG)
+    r = s.run_batch(lb.Solver.members([gG, gG, gG2], [0, 1, 2], [0.03, 0.03, 0.2]))
+    s.close()
+    cases = [(g1, dl1, th1, gG, 0.03), (g1, dl1, None, gG, 0.03), (g2, dl2, th2, gG2, 0.2)]
+    for m, (g, dl, th, gv, kap) in enumerate(cases):
+        o = oracle.run(g.labels, g.dx, g.phase_of_label, (0, 0, 0), D, T2, kap, DT, f, gv,
+                       delta=dl.astype(np.float64), theta=None if th is None else th.astype(np.float64),
+                       lattice="D2Q5")
+        assert abs(r["S"][m] - o["S"]) <= S_TOL * o["S"], (m, r["S"][m], o["S"])
