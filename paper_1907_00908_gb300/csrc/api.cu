@@ -723,7 +723,15 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
         if (d.dth) a.links = 2;
         else if (d.dlt && a.links == 0) a.links = 1;
     }
-    if (c->lattice == 1) { a.w0 = 1.f / 3.f; a.wxy = 1.f / 6.f; a.wz = 0.f; }
+    if (c->lattice == 1) {
+        // D2Q5 weights 1/3, 1/6 are not binary fractions: take w0 = 1 - 4 wxy
+        // (exact in FP32) so the FP32 weights sum to exactly 1; with
+        // fl(1/3) + 4 fl(1/6) = 1 + 3e-8 every collision would scale M by
+        // 1 + omega 3e-8 (0.5 % over 1.5e5 steps)
+        a.wxy = 1.f / 6.f;
+        a.w0 = 1.f - 4.f * a.wxy;
+        a.wz = 0.f;
+    }
     else { a.w0 = W0; a.wxy = WI; a.wz = WI; }
     return a;
 }
