@@ -78,6 +78,26 @@ def sweep_source_hash():
     return h.hexdigest()[:16]
 
 
+def links_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "links.cuh", "sweep_common.cuh", "lbmbt_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def links_traffic_per_launch(n):
+    """DRAM bytes per launch of the membrane-position sweep on the n^3
+    cylinders (3 members) from the committed ncu summary, or None when the
+    kernel source changed since, or the capture was of another size."""
+    p = os.path.join(ROOT, "profiles", "links_traffic.json")
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    if j.get("source_hash") != links_source_hash() or j.get("n") != n:
+        return None
+    return j["dram_bytes_read"] + j["dram_bytes_write"]
+
+
 def traffic_per_launch():
     """DRAM bytes per sweep launch from the committed ncu summary, or None
     when the kernel source changed since it was captured."""
@@ -365,7 +385,10 @@ def run_links(args):
                                  ("half_link_bulk_copy", 2, False)):
         s = lbmbt.Solver(0, stream)
         s.set_option(lbmbt.OPT_KERNEL, kernel)
-        s.set_option(lbmbt.OPT_AUTOTUNE, 1)
+        s.set_option(lbmbt.OPT_AUTOTUNE, 0 if args.no_autotune else 1)
+        if args.no_autotune and use_dl:   # the tuner's usual choice for this kernel
+            s.set_option(lbmbt.OPT_BLOCK, 512)
+            s.set_option(lbmbt.OPT_SPT, 2)
         s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, (0, 0, 0))
         if use_dl:
             s.set_link_distances(dl)
@@ -390,13 +413,14 @@ def run_links(args):
     # algorithmic bytes: 113 per site update + 4 per membrane link (its position)
     bytes_site = BYTES_PER_SITE + 4.0 * n_memb_links / geom.n_sites
     achieved = bytes_site * v * 1e6 / 1e9
+    traffic = links_traffic_per_launch(n)
     line = {"metric": "MLUPS (fused sweep with membrane positions on the links, FP32)", "value": v, "unit": "MLUPS",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["links_register"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"cylinders{n}_dx0.25_links_3dir", "grid": [n] * 3, "membrane_link_fraction":
                        n_memb_links / (6.0 * geom.n_sites), "geometry_gen_s": round(t_geo, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_source": peak_kind, "bytes_per_site_member": bytes_site,
+                         "traffic": traffic, "peak_source": peak_kind, "bytes_per_site_member": bytes_site,
                          "kernel": "sweep_links_kernel (register)"},
             "compare": res}
     print(json.dumps(line), flush=True)

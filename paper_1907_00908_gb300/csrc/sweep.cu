@@ -148,9 +148,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
 
         // Membranes at given positions: the warp lists its links that take
         // the position rule (those whose node behind s, s + e_i, lies in s's
-        // compartment) before the pulls, so that the rule's loads and the
-        // pulls are in flight together; the list is shared out one link per
-        // lane below.
+        // compartment), shares the list out one link per lane and leaves the
+        // results in shared memory, all before the pulls: the seven pulled
+        // values are then not live across the rule's loads and arithmetic
+        // (at 64 registers the other order spilled).
         const bool links_on = LINKS && sd->dlt != nullptr;   // block-uniform
         const unsigned lane = threadIdx.x & 31u;
         unsigned cand = 0, incl = 0, K = 0;
@@ -177,6 +178,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
                 unsigned o = incl - __popc(cand);
                 for (unsigned c = cand; c; c &= c - 1) item[o++] = (uint8_t)((lane << 3) | (__ffs(c) - 1));
                 __syncwarp();
+                for (unsigned t0 = 0; t0 < K; t0 += 32) {   // warp-uniform
+                    const unsigned t = t0 + lane;
+                    const unsigned it = item[t < K ? t : 0];
+                    const unsigned sl = it >> 3;
+                    const int xo = __shfl_sync(0xffffffffu, x, sl), yo = __shfl_sync(0xffffffffu, y, sl),
+                              zo = __shfl_sync(0xffffffffu, z, sl);
+                    if (t < K)
+                        res[t] = link_population<LINKS == 2>(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
+                }
+                __syncwarp();
             }
         }
 
@@ -193,7 +204,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         // population is r * (own population sent towards the membrane) +
         // s * (population streaming across), written A + s (B - A).
         // Bit (ibar - 1) marks the link to the upstream neighbour of i.
-        // With positions, the listed links take their lane's result instead.
+        // With positions, the listed links take the result left in shared
+        // memory instead.
         if (links_on) {
             if (mk & 0x3fu) {   // node behind s in another compartment: half-link rule
 #pragma unroll
@@ -204,16 +216,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
                 }
             }
             if (K != 0) {   // warp-uniform
-                for (unsigned t0 = 0; t0 < K; t0 += 32) {   // warp-uniform
-                    const unsigned t = t0 + lane;
-                    const unsigned it = item[t < K ? t : 0];
-                    const unsigned sl = it >> 3;
-                    const int xo = __shfl_sync(0xffffffffu, x, sl), yo = __shfl_sync(0xffffffffu, y, sl),
-                              zo = __shfl_sync(0xffffffffu, z, sl);
-                    if (t < K)
-                        res[t] = link_population<LINKS == 2>(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
-                }
-                __syncwarp();
                 unsigned o = incl - __popc(cand);
 #pragma unroll
                 for (int i = 1; i < Q; ++i)
