@@ -387,7 +387,7 @@ def run_links(args):
         s.set_option(lbmbt.OPT_KERNEL, kernel)
         s.set_option(lbmbt.OPT_AUTOTUNE, 0 if args.no_autotune else 1)
         if args.no_autotune and use_dl:   # the tuner's usual choice for this kernel
-            s.set_option(lbmbt.OPT_BLOCK, 512)
+            s.set_option(lbmbt.OPT_BLOCK, 128)
             s.set_option(lbmbt.OPT_SPT, 2)
         s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, (0, 0, 0))
         if use_dl:

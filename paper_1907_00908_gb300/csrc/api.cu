@@ -681,6 +681,11 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
         if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
         c->tma_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_units);
     }
+    for (auto& d : c->descs)
+        if (d.dlt) {
+            CU(c, links_prepare());
+            break;
+        }
     const long long n_part = std::max(c->n_tiles, c->n_units * tma_partials_per_unit(c->tma_variant));
     int rc = grow(c, &c->d_desc, &c->cap_desc, sizeof(MemberDesc) * c->n_members);
     if (!rc) rc = grow(c, &c->d_tile_start, &c->cap_ts, sizeof(long long) * (c->n_members + 1));

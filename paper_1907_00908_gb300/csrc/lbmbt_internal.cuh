@@ -123,6 +123,7 @@ cudaError_t launch_factor_table(const MemberDesc* members, int n_members, const 
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot,
                         cudaStream_t st);
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
+cudaError_t links_prepare();   // dynamic shared memory of the membrane-position sweeps
 // Sums partial[tile_start[m]*per .. tile_start[m+1]*per) per member.
 cudaError_t launch_reduce(const double2* partial, const long long* tile_start, int per, int n_members,
                           double2* out, double2* series, long long series_stride,

@@ -94,17 +94,21 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
 // Warp-compacted membrane links (Eqs. B4a-B4c): the links of one warp's 32
 // sites that take the position rule are listed in shared memory and shared
 // out one per lane, so the rule's loads and coefficients run once per link
-// instead of once per direction for the whole warp.  Per warp: LINK_SLOTS
-// results (float2) and LINK_SLOTS items (lane << 3 | direction).
+// instead of once per direction for the whole warp.  One list covers all SPT
+// sites of the warp's threads.  Per warp: SPT * LINK_SLOTS results (float2)
+// and as many items (site << 8 | lane << 3 | direction, 16 bits).
 constexpr int LINK_SLOTS = 32 * 6;
-inline size_t link_smem_bytes(int block) { return (size_t)(block / 32) * LINK_SLOTS * (sizeof(float2) + 1); }
+inline size_t link_smem_bytes(int block, int spt)
+{
+    return (size_t)(block / 32) * spt * LINK_SLOTS * (sizeof(float2) + sizeof(uint16_t));
+}
 
 // LINKS: 0 half-link rule only, 1 membrane positions, 2 positions and angles
 template <int SPT, int LINKS>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a)
 {
     __shared__ double2 s_red[32];
-    extern __shared__ __align__(16) unsigned char s_link[];   // LINKS only: link_smem_bytes(blockDim.x)
+    extern __shared__ __align__(16) unsigned char s_link[];   // LINKS only: link_smem_bytes(blockDim.x, SPT)
     // Every thread looks up its member, step and flags itself (broadcast
     // loads): there is no per-block prologue to wait for.
     const int m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, blockIdx.x);
@@ -129,67 +133,73 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const float sh = sd->s_share;
     float zr = 0.f, zi = 0.f;   // per-thread sums in FP32, FP64 from the warp level up
 
+    // Membranes at given positions: the warp lists the links of all its
+    // sites that take the position rule (those whose node behind s, s + e_i,
+    // lies in s's compartment), shares the list out one link per lane and
+    // leaves the results in shared memory, all before any pull: the pulled
+    // values are then not live across the rule's loads and arithmetic.
+    const bool links_on = LINKS && sd->dlt != nullptr;   // block-uniform
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned cand[SPT], off[SPT];   // per site: listed directions (bits 1..6), first list slot
+    float2* res = nullptr;
+    if (links_on) {
+        res = reinterpret_cast<float2*>(s_link) + (threadIdx.x >> 5) * (SPT * LINK_SLOTS);
+        uint16_t* const item = reinterpret_cast<uint16_t*>(reinterpret_cast<float2*>(s_link) +
+                                                           (blockDim.x >> 5) * (SPT * LINK_SLOTS)) +
+                               (threadIdx.x >> 5) * (SPT * LINK_SLOTS);
+        unsigned K = 0;
 #pragma unroll
-    for (int j = 0; j < SPT; ++j) {
-        const unsigned s_at = base + j * blockDim.x + threadIdx.x;
-        const bool in = s_at < N;
-        if (LINKS) {
-            // the link lists are warp-collective: a lane past the end stays
-            // (on the last site, without storing) while any lane of its warp works
-            if (!__any_sync(0xffffffffu, in)) break;
-        } else if (!in) {
-            break;
-        }
-        const unsigned s = in ? s_at : N - 1;
-        int x, y, z;
-        coords(sd, s, nx, ny, x, y, z);
-        const unsigned mk = mask[s];
-        const int ph = mk >> 6;
-
-        // Membranes at given positions: the warp lists its links that take
-        // the position rule (those whose node behind s, s + e_i, lies in s's
-        // compartment), shares the list out one link per lane and leaves the
-        // results in shared memory, all before the pulls: the seven pulled
-        // values are then not live across the rule's loads and arithmetic
-        // (at 64 registers the other order spilled).
-        const bool links_on = LINKS && sd->dlt != nullptr;   // block-uniform
-        const unsigned lane = threadIdx.x & 31u;
-        unsigned cand = 0, incl = 0, K = 0;
-        float2* res = nullptr;
-        uint8_t* item = nullptr;
-        if (links_on) {
-            if (in && (mk & 0x3fu)) {
+        for (int j = 0; j < SPT; ++j) {
+            const unsigned s_at = base + j * blockDim.x + threadIdx.x;
+            unsigned c = 0;
+            if (s_at < N) {
+                const unsigned mk = mask[s_at];
+                if (mk & 0x3fu) {
 #pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int ib = (i & 1) ? i + 1 : i - 1;
-                    if ((mk & (1u << (ib - 1))) && !(mk & (1u << (i - 1)))) cand |= 1u << i;
+                    for (int i = 1; i < Q; ++i) {
+                        const int ib = (i & 1) ? i + 1 : i - 1;
+                        if ((mk & (1u << (ib - 1))) && !(mk & (1u << (i - 1)))) c |= 1u << i;
+                    }
                 }
             }
-            incl = __popc(cand);   // inclusive prefix of the warp's link counts
+            unsigned incl = __popc(c);   // inclusive prefix of the warp's link counts
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= (unsigned)o) incl += v;
             }
-            K = __shfl_sync(0xffffffffu, incl, 31);
-            if (K != 0) {   // warp-uniform
-                res = reinterpret_cast<float2*>(s_link) + (threadIdx.x >> 5) * LINK_SLOTS;
-                item = s_link + (size_t)(blockDim.x >> 5) * LINK_SLOTS * sizeof(float2) + (threadIdx.x >> 5) * LINK_SLOTS;
-                unsigned o = incl - __popc(cand);
-                for (unsigned c = cand; c; c &= c - 1) item[o++] = (uint8_t)((lane << 3) | (__ffs(c) - 1));
-                __syncwarp();
-                for (unsigned t0 = 0; t0 < K; t0 += 32) {   // warp-uniform
-                    const unsigned t = t0 + lane;
-                    const unsigned it = item[t < K ? t : 0];
-                    const unsigned sl = it >> 3;
-                    const int xo = __shfl_sync(0xffffffffu, x, sl), yo = __shfl_sync(0xffffffffu, y, sl),
-                              zo = __shfl_sync(0xffffffffu, z, sl);
-                    if (t < K)
-                        res[t] = link_population<LINKS == 2>(sd, src, fac, s_at - lane + sl, xo, yo, zo, (int)(it & 7));
-                }
-                __syncwarp();
-            }
+            cand[j] = c;
+            off[j] = K + incl - __popc(c);
+            unsigned o = off[j];
+            for (unsigned cc = c; cc; cc &= cc - 1)
+                item[o++] = (uint16_t)(((unsigned)j << 8) | (lane << 3) | (__ffs(cc) - 1));
+            K += __shfl_sync(0xffffffffu, incl, 31);
         }
+        if (K != 0) {   // warp-uniform
+            __syncwarp();
+            const unsigned wbase = base + (threadIdx.x - lane);
+            for (unsigned t0 = 0; t0 < K; t0 += 32) {   // warp-uniform
+                const unsigned t = t0 + lane;
+                if (t < K) {
+                    const unsigned it = item[t];
+                    const unsigned so = wbase + (it >> 8) * blockDim.x + ((it >> 3) & 31u);
+                    int xo, yo, zo;
+                    coords(sd, so, nx, ny, xo, yo, zo);
+                    res[t] = link_population<LINKS == 2>(sd, src, fac, so, xo, yo, zo, (int)(it & 7));
+                }
+            }
+            __syncwarp();
+        }
+    }
+
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const unsigned s = base + j * blockDim.x + threadIdx.x;
+        if (s >= N) break;
+        int x, y, z;
+        coords(sd, s, nx, ny, x, y, z);
+        const unsigned mk = mask[s];
+        const int ph = mk >> 6;
 
         float2 g[Q];
         g[0] = __ldg(src + s);
@@ -215,13 +225,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
                         g[i] = mix(__ldg(src + (size_t)ib * P + s), g[i], sh);
                 }
             }
-            if (K != 0) {   // warp-uniform
-                unsigned o = incl - __popc(cand);
+            unsigned o = off[j];
 #pragma unroll
-                for (int i = 1; i < Q; ++i)
-                    if (cand & (1u << i)) g[i] = res[o++];
-                __syncwarp();   // the lists are rewritten for the warp's next sites
-            }
+            for (int i = 1; i < Q; ++i)
+                if (cand[j] & (1u << i)) g[i] = res[o++];
         } else if (mk & 0x3fu) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
@@ -239,7 +246,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         float mr, mi;
         react(g, q, mr, mi);
         collide_w(g, sd->omega[ph], mr, mi, a.w0, a.wxy, a.wz);
-        if (LINKS && !in) continue;
 #pragma unroll
         for (int i = 0; i < Q; ++i) __stcs(dst + (size_t)i * P + s, g[i]);
 
@@ -381,22 +387,37 @@ cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int sp
     return cudaGetLastError();
 }
 
+// The membrane-position kernels take up to link_smem_bytes(512, 4) of
+// dynamic shared memory (above the default 48 KB); set once per run set-up.
+cudaError_t links_prepare()
+{
+    const int bytes = (int)link_smem_bytes(512, 4);
+    const void* k[6] = {(const void*)sweep_links_kernel<1, false>, (const void*)sweep_links_kernel<2, false>,
+                        (const void*)sweep_links_kernel<4, false>, (const void*)sweep_links_kernel<1, true>,
+                        (const void*)sweep_links_kernel<2, true>, (const void*)sweep_links_kernel<4, true>};
+    for (const void* f : k) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st)
 {
     switch (spt) {
     case 1:
-        if (a.links == 2) sweep_links_kernel<1, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
-        else if (a.links) sweep_links_kernel<1, false><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        if (a.links == 2) sweep_links_kernel<1, true><<<(unsigned)n_tiles, block, link_smem_bytes(block, 1), st>>>(a);
+        else if (a.links) sweep_links_kernel<1, false><<<(unsigned)n_tiles, block, link_smem_bytes(block, 1), st>>>(a);
         else sweep_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 2:
-        if (a.links == 2) sweep_links_kernel<2, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
-        else if (a.links) sweep_links_kernel<2, false><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        if (a.links == 2) sweep_links_kernel<2, true><<<(unsigned)n_tiles, block, link_smem_bytes(block, 2), st>>>(a);
+        else if (a.links) sweep_links_kernel<2, false><<<(unsigned)n_tiles, block, link_smem_bytes(block, 2), st>>>(a);
         else sweep_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     case 4:
-        if (a.links == 2) sweep_links_kernel<4, true><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
-        else if (a.links) sweep_links_kernel<4, false><<<(unsigned)n_tiles, block, link_smem_bytes(block), st>>>(a);
+        if (a.links == 2) sweep_links_kernel<4, true><<<(unsigned)n_tiles, block, link_smem_bytes(block, 4), st>>>(a);
+        else if (a.links) sweep_links_kernel<4, false><<<(unsigned)n_tiles, block, link_smem_bytes(block, 4), st>>>(a);
         else sweep_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;
