@@ -290,8 +290,9 @@ enum {
                                 Sec. 2.3 (eps_D = 1/3, omega_0 = 1/3,
                                 omega_1..4 = 1/6; tau, P and the membrane
                                 coefficients use eps_D = 1/3) on geometries of
-                                one z plane, register sweep only; the adjoint
-                                returns EUNSUPPORTED                           */
+                                one z plane, register sweep and register
+                                adjoint only (a forced bulk-copy adjoint
+                                returns EUNSUPPORTED)                          */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
         float lwr = 0.f, lwi = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float w = i == 0 ? W0 : WI;
+            const float w = i == 0 ? a.w0 : i < 5 ? a.wxy : a.wz;
             dOm += lam[i].x * (w * Mr - gg[i].x) + lam[i].y * (w * Mi - gg[i].y);
             lwr += w * lam[i].x;
             lwi += w * lam[i].y;

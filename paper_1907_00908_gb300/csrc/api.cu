@@ -1408,6 +1408,12 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     aa.ftab = c->d_ftab;
     aa.unit_start = c->d_adj_unit_start;
     aa.ctl_err = &c->d_ctl->err;
+    {
+        const SweepArgs sa = sweep_args(c);   // the forward's equilibrium weights
+        aa.w0 = sa.w0;
+        aa.wxy = sa.wxy;
+        aa.wz = sa.wz;
+    }
     int parity = 1;
     for (long long seg = n_ck - 1; seg >= 0; --seg) {
         const long long k0 = seg * ck, k1 = std::min(K, k0 + ck);
@@ -1443,13 +1449,14 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     if ((rc = check_device_error(c))) return rc;
     c->prepared = false;  // descriptors now describe the reverse pass
     // chain rule to the physical parameters
+    const double eps = c->lattice == 1 ? EPS_D2 : EPS_D;
     for (int m = 0; m < n; ++m) {
         const double dx = c->descs[m].dx, dt = c->dt;
         const double* g = &G[(size_t)NGACC * m];
         for (int p = 0; p < c->n_phases; ++p) {
-            const double tau = 0.5 + dt * c->D[p] / (EPS_D * dx * dx);
+            const double tau = 0.5 + dt * c->D[p] / (eps * dx * dx);
             const double om = 1.0 / tau;
-            dD[(size_t)m * c->n_phases + p] = g[p] * (-om * om * dt / (EPS_D * dx * dx));
+            dD[(size_t)m * c->n_phases + p] = g[p] * (-om * om * dt / (eps * dx * dx));
             const double T2 = c->T2[p];
             if (std::isinf(T2)) {
                 dT2[(size_t)m * c->n_phases + p] = 0.0;
@@ -1459,7 +1466,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
             }
         }
         const double kap = mem[m].kappa_um_ms;
-        const double cP = EPS_D * dx / (2.0 * dt);
+        const double cP = eps * dx / (2.0 * dt);
         dk[m] = std::isinf(kap) ? 0.0 : g[8] * cP / ((kap + cP) * (kap + cP));
     }
     return LBMBT_OK;
@@ -1476,7 +1483,8 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
     if (any_slab(c)) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not run on slabs");
     for (auto& g : c->geoms)
         if (g.d_dlt) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not take membrane positions");
-    if (c->lattice != 0) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep runs on the D3Q7 lattice only");
+    if (c->lattice != 0 && c->adjoint_opt == 2)
+        return fail(c, LBMBT_EUNSUPPORTED, "the bulk-copy adjoint runs on the D3Q7 lattice only");
     const int ck = checkpoint_every > 0 ? checkpoint_every : 64;
     int rc = set_device(c);
     if (rc) return rc;

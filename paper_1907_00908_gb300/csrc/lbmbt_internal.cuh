@@ -156,6 +156,8 @@ struct AdjointArgs {
     const float2* ftab;           // [K+1][n_members][6] boundary factors
     const long long* unit_start;  // bulk-copy adjoint: row-unit prefix
     int* ctl_err;                 // error word of the step control
+    float w0, wxy, wz;            // equilibrium weights (register adjoint; the
+                                  // bulk-copy adjoint has the D3Q7 ones built in)
 };
 cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
 // Sums gacc slots [tile_start[m]*per, tile_start[m+1]*per) per member.

@@ -187,3 +187,31 @@ def test_bulk_copy_adjoint_matches_register_adjoint(lb, name):
         b = _logvec(out[key], c["D"], c["T2"], c["kap"])
         assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max(), key
         assert out[(1, 0)]["S"] == out[key]["S"]
+
+
+@pytest.mark.parametrize("bc,d", [((0, 0, 0), (0.6, 0.8, 0.0)), ((1, 1, 0), (1.0, 0.0, 0.0))])
+def test_adjoint_d2q5_matches_oracle_finite_differences(lb, bc, d):
+    """The register adjoint on the 2-D D2Q5 lattice (weights 1/3, 1/6 and
+    eps_D = 1/3 in the chain rule) against central differences of the
+    oracle's D2Q5 runs; a forced bulk-copy adjoint is refused."""
+    geom = synth.disks(40, 0.5, [[5.3, 6.1], [14.8, 13.2], [4.9, 15.7]], [3.6, 4.1, 2.4])
+    D, T2, kap, dt = [2.0, 1.0], [80.0, 50.0], 0.05, 0.02
+    gG, f = oracle.pgse(2000.0, 0.4, 1.0, dt, d)
+    s = _setup(lb, geom, bc, D, T2, kap, dt, f, gG)
+    s.set_option(lb.OPT_LATTICE, 1)
+    g = s.grad(checkpoint_every=8)
+    s.set_option(lb.OPT_ADJOINT_KERNEL, 2)
+    with pytest.raises(lb.LbmbtError) as e:
+        s.grad()
+    assert e.value.code == -5
+    s.close()
+
+    def S(D_, T2_, kap_):
+        return oracle.run(geom.labels, geom.dx, geom.phase_of_label, bc, D_, T2_, kap_, dt, f, gG,
+                          lattice="D2Q5")["S"]
+
+    fd = _fd(S, D, T2, kap)
+    a, b = _logvec(g, D, T2, kap), _logvec(fd, D, T2, kap)
+    err = np.abs(a - b).max() / np.abs(b).max()
+    assert err < 1e-3, (a, b, err)
+    assert abs(g["S"] - S(D, T2, kap)) < 1e-5 * g["S"]
