@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
     const unsigned base = (unsigned)(blockIdx.x - sd->tile0) * blockDim.x * SPT;
     const float sh = sd->s_share;
     const float fk = a.fprev;
+    // D2Q5: the z populations and their adjoints are exactly 0 (weight 0,
+    // nothing couples them to the others), so their planes are not touched
+    const bool zpl = a.wz != 0.f;
     float acc[NGACC];
 #pragma unroll
     for (int j = 0; j < NGACC; ++j) acc[j] = 0.f;
@@ -130,8 +133,12 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
         gp[2] = pull<0, -1>(u, P, s, x, nx, 1u, bcx, facP);
         gp[3] = pull<1, +1>(u, P, s, y, ny, (unsigned)nx, bcy, facP);
         gp[4] = pull<1, -1>(u, P, s, y, ny, (unsigned)nx, bcy, facP);
-        gp[5] = pull<2, +1>(u, P, s, z, nz, sxy, bcz, facP);
-        gp[6] = pull<2, -1>(u, P, s, z, nz, sxy, bcz, facP);
+        if (zpl) {
+            gp[5] = pull<2, +1>(u, P, s, z, nz, sxy, bcz, facP);
+            gp[6] = pull<2, -1>(u, P, s, z, nz, sxy, bcz, facP);
+        } else {
+            gp[5] = gp[6] = make_float2(0.f, 0.f);
+        }
         if (mk & 0x3fu) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
@@ -162,8 +169,12 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
             lam[2] = adj_pull<0, -1>(nu, P, s, x, nx, 1u, bcx, facK, mk & 2u, sh);
             lam[3] = adj_pull<1, +1>(nu, P, s, y, ny, (unsigned)nx, bcy, facK, mk & 4u, sh);
             lam[4] = adj_pull<1, -1>(nu, P, s, y, ny, (unsigned)nx, bcy, facK, mk & 8u, sh);
-            lam[5] = adj_pull<2, +1>(nu, P, s, z, nz, sxy, bcz, facK, mk & 16u, sh);
-            lam[6] = adj_pull<2, -1>(nu, P, s, z, nz, sxy, bcz, facK, mk & 32u, sh);
+            if (zpl) {
+                lam[5] = adj_pull<2, +1>(nu, P, s, z, nz, sxy, bcz, facK, mk & 16u, sh);
+                lam[6] = adj_pull<2, -1>(nu, P, s, z, nz, sxy, bcz, facK, mk & 32u, sh);
+            } else {
+                lam[5] = lam[6] = make_float2(0.f, 0.f);
+            }
         }
 
         // d/d omega: <lambda_i, w_i M - g_i>, g_i = (1 + q) g'_i
@@ -188,7 +199,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
             // conj(1 + q) * mu
             lam[i].x = mr + (mr * qr + mi * qi);
             lam[i].y = mi + (mi * qr - mr * qi);
-            __stcs(out + (size_t)i * P + s, lam[i]);
+            if (i < 5 || zpl) __stcs(out + (size_t)i * P + s, lam[i]);
         }
         // d/d s on membrane links of step k-1: <nu_i, v_i - o_i>
         float dS = 0.f;

@@ -12,7 +12,8 @@
 //    The loop state is the post-collision population hat g(t^k); one pass
 //    maps hat g(t^k) -> hat g(t^{k+1}), i.e. the paper's step order re-cut at
 //    the collision, so every site reads 7 complex values (one from each
-//    upstream neighbour) and writes 7.
+//    upstream neighbour) and writes 7 (5 on the D2Q5 lattice, whose z
+//    populations stay exactly 0 and are not touched).
 //  * sweep_links_kernel: the same step with membranes at given positions on
 //        the links (Eqs. B4a-B4c), the rule's links compacted per warp
 //  * ctl_kernel        : sets / advances the step word between sweeps and
@@ -132,6 +133,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const unsigned base = (unsigned)(blockIdx.x - sd->tile0) * blockDim.x * SPT;
     const float sh = sd->s_share;
     float zr = 0.f, zi = 0.f;   // per-thread sums in FP32, FP64 from the warp level up
+    // D2Q5 (the z populations carry weight 0): they are exactly 0 at the
+    // start and stay 0, so the z planes are neither read nor written
+    const bool zpl = a.wz != 0.f;
 
     // Membranes at given positions: the warp lists the links of all its
     // sites that take the position rule (those whose node behind s, s + e_i,
@@ -207,8 +211,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         g[2] = pull<0, -1>(src, P, s, x, nx, 1u, bcx, fac);
         g[3] = pull<1, +1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
         g[4] = pull<1, -1>(src, P, s, y, ny, (unsigned)nx, bcy, fac);
-        g[5] = pull<2, +1>(src, P, s, z, nz, sxy, bcz0, fac, &sd->halo[0]);
-        g[6] = pull<2, -1>(src, P, s, z, nz, sxy, bcz1, fac, &sd->halo[1]);
+        if (zpl) {
+            g[5] = pull<2, +1>(src, P, s, z, nz, sxy, bcz0, fac, &sd->halo[0]);
+            g[6] = pull<2, -1>(src, P, s, z, nz, sxy, bcz1, fac, &sd->halo[1]);
+        } else {
+            g[5] = g[6] = make_float2(0.f, 0.f);
+        }
 
         // Half-link membrane (Eq. B5): on a membrane link the arriving
         // population is r * (own population sent towards the membrane) +
@@ -247,7 +255,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         react(g, q, mr, mi);
         collide_w(g, sd->omega[ph], mr, mi, a.w0, a.wxy, a.wz);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(dst + (size_t)i * P + s, g[i]);
+        for (int i = 0; i < Q; ++i)
+            if (i < 5 || zpl) __stcs(dst + (size_t)i * P + s, g[i]);
 
         zr += mr;
         zi += mi;
