@@ -278,7 +278,9 @@ enum {
                                 (TMA) sweep; auto takes the bulk-copy sweep when
                                 every member has nx % 16 == 0 and nx <= 1024  */
     LBMBT_OPT_KERNEL_USED = 6, /* read-only: 1 or 2 for the prepared run, else 0 */
-    LBMBT_OPT_STAGES = 7,    /* shared-memory stages of the bulk-copy sweep, 2..6 */
+    LBMBT_OPT_STAGES = 7,    /* shared-memory stages of the bulk-copy sweep, 2..6
+                                as far as they fit (3 of 1024-site units); more
+                                than fit give EINVAL                          */
     LBMBT_OPT_TMA_SHAPE = 8, /* bulk-copy consumers x sites per thread per unit:
                                 0 = 512 x 2, 1 = 384 x 3, 2 = 256 x 4,
                                 3 = 352 x 3 (default)                         */

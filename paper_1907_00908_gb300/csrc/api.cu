@@ -676,7 +676,13 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
         c->tma_cap = (cap + 15) / 16 * 16;
         c->tma_capx = (capx + 15) / 16 * 16;
         int per_sm = 0;
-        CU(c, tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, &per_sm));
+        const cudaError_t pe = tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, &per_sm);
+        if (pe == cudaErrorInvalidValue) {   // more shared memory than a block may have
+            cudaGetLastError();
+            return fail(c, LBMBT_EINVAL, "%d bulk-copy stages of %d sites (%zu bytes) do not fit in shared memory",
+                        c->tma_stages, c->tma_cap, tma_smem_bytes(c->tma_cap, c->tma_capx, c->tma_stages));
+        }
+        CU(c, pe);
         if (per_sm < 1) return fail(c, LBMBT_EINVAL, "bulk-copy sweep does not fit on an SM");
         if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
         c->tma_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_units);

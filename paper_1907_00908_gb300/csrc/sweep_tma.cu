@@ -12,8 +12,10 @@
 // its sites (phase 1, after which the stage is released), then reacts,
 // collides and stores them with no branch between sites (phase 2), so the
 // arithmetic of several sites interleaves.  The own-site values of planes
-// 3..6 (membrane links in y and z) are prefetched into registers one unit
-// ahead.
+// 3 and 4 (membrane links in y) are prefetched into registers one unit
+// ahead; the own rows of planes 5 and 6 (membrane links in z) are staged
+// with the unit, since those rows are otherwise first touched a whole plane
+// later, and a load at a membrane lane waited on DRAM.
 //
 // Source row-blocks of a unit starting at site s0 (all 16-byte aligned when
 // nx is even; the mask copy needs nx % 16 == 0):
@@ -25,6 +27,7 @@
 //   plane 4 (-y) rows y+1 (last row: wrapped row, or own row of plane 3)
 //   plane 5 (+z) plane z-1 (z = 0: wrapped plane, or own rows of plane 6)
 //   plane 6 (-z) plane z+1 (last plane: wrapped, or own rows of plane 5)
+//   own rows of planes 5 and 6 [s0, s0+L) (geometries with membranes only)
 // The boundary factors (periodic phase, mirror conjugation and rewind) are
 // applied per element after the copy, exactly as in the register kernel.
 //
@@ -41,11 +44,11 @@ namespace {
 constexpr int TMA_MAX_STAGES = 6;
 
 // Shared-memory stage (all parts 16-byte aligned): 7 pull rows of (cap + 2)
-// complex values (the sources listed above), capx spare complex values
-// (0 in use), then cap mask bytes.
+// complex values (the sources listed above), the own rows of planes 5 and 6
+// (slots 7 and 8), capx spare complex values (0 in use), then cap mask bytes.
 __host__ __device__ __forceinline__ size_t stage_bytes(int cap, int capx)
 {
-    return (((size_t)7 * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
+    return (((size_t)9 * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
 }
 __device__ __forceinline__ float2* stage_plane(unsigned char* stage, int cap, int i)
 {
@@ -53,7 +56,7 @@ __device__ __forceinline__ float2* stage_plane(unsigned char* stage, int cap, in
 }
 __device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, int capx)
 {
-    return stage + ((size_t)7 * (cap + 2) + capx) * sizeof(float2);
+    return stage + ((size_t)9 * (cap + 2) + capx) * sizeof(float2);
 }
 
 // Thread 0: copies of unit u into `stage`, completion on `bar`.
@@ -72,8 +75,12 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
     auto pl = [&](int i) { return src + (size_t)i * P; };
     const uint32_t rowb = (uint32_t)(nx * sizeof(float2));
     const uint32_t Lb = (uint32_t)(L * sizeof(float2));
-    const uint32_t total = 5 * Lb + 2 * (Lb + 16) + (uint32_t)L;
+    const uint32_t total = 5 * Lb + 2 * (Lb + 16) + (uint32_t)L + (d.memb ? 2 * Lb : 0u);
     mbar_arrive_expect_tx(bar, total);
+    if (d.memb) {   // own rows of planes 5 and 6 (membrane links in z)
+        bulk_g2s(stage_plane(stage, cap, 7), pl(5) + s0, Lb, bar);
+        bulk_g2s(stage_plane(stage, cap, 8), pl(6) + s0, Lb, bar);
+    }
     // rest, +x, -x
     bulk_g2s(stage_plane(stage, cap, 0), pl(0) + s0, Lb, bar);
     bulk_g2s(stage_plane(stage, cap, 1), pl(1) + s0 - 2, Lb + 16, bar);
@@ -181,10 +188,10 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     const int lsrc = (k - sbase) % smod, ldst = (k + 1 - sbase) % smod;
     const int warp = tid >> 5, lane = tid & 31;
 
-    // Own-site values of planes 3..6 on membrane links in y and z, prefetched
+    // Own-site values of planes 3 and 4 on membrane links in y, prefetched
     // into registers one unit ahead for the lanes whose mask needs them.
-    float2 own[TMA_SPT][4], nown[TMA_SPT][4];
-    auto prefetch = [&](long long j, float2 (&o)[TMA_SPT][4]) -> bool {
+    float2 own[TMA_SPT][2], nown[TMA_SPT][2];
+    auto prefetch = [&](long long j, float2 (&o)[TMA_SPT][2]) -> bool {
         if (unit_of(j) >= n_units) return true;
         const int st = (int)(j % nst);
         if (!mbar_wait(&full[st], (uint32_t)((j / nst) & 1))) return false;
@@ -203,8 +210,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 const unsigned s = G.s0 + (unsigned)l;
                 if (mk & 4u) o[jj][0] = __ldg(sp + (size_t)3 * P + s);
                 if (mk & 8u) o[jj][1] = __ldg(sp + (size_t)4 * P + s);
-                if (mk & 16u) o[jj][2] = __ldg(sp + (size_t)5 * P + s);
-                if (mk & 32u) o[jj][3] = __ldg(sp + (size_t)6 * P + s);
+
             }
         }
         return true;
@@ -294,8 +300,8 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 if (mk & 1u) g[j][2] = mix(r1[l + 2], g[j][2], sh);      // link to +x: own hat g_1
                 if (mk & 8u) g[j][3] = mix(own[j][1], g[j][3], sh);      // link to -y: own hat g_4
                 if (mk & 4u) g[j][4] = mix(own[j][0], g[j][4], sh);      // link to +y: own hat g_3
-                if (mk & 32u) g[j][5] = mix(own[j][3], g[j][5], sh);     // link to -z: own hat g_6
-                if (mk & 16u) g[j][6] = mix(own[j][2], g[j][6], sh);     // link to +z: own hat g_5
+                if (mk & 32u) g[j][5] = mix(stage_plane(sb, cap, 8)[l], g[j][5], sh);   // link to -z: own hat g_6
+                if (mk & 16u) g[j][6] = mix(stage_plane(sb, cap, 7)[l], g[j][6], sh);   // link to +z: own hat g_5
             }
             mks[j] = mk;
             xs[j] = x;
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 #pragma unroll
         for (int j = 0; j < TMA_SPT; ++j)
 #pragma unroll
-            for (int p = 0; p < 4; ++p) own[j][p] = nown[j][p];
+            for (int p = 0; p < 2; ++p) own[j][p] = nown[j][p];
         if (do_sig) {   // grid-uniform; FP64 from the warp level up, one slot per warp
             double dr = zr, di = zi;
             for (int o = 16; o > 0; o >>= 1) {
