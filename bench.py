@@ -630,7 +630,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
-    ap.add_argument("--adj-shape", type=int, default=1, help="bulk-copy adjoint consumer shape (0 or 1)")
+    ap.add_argument("--adj-shape", type=int, default=2, help="bulk-copy adjoint consumer shape (0, 1 or 2)")
     ap.add_argument("--members", type=int, default=60, help="adjoint workload: number of members (<= 60)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)

@@ -287,7 +287,9 @@ enum {
     LBMBT_OPT_ADJOINT_KERNEL = 9, /* 0 (default) auto, 1 register adjoint sweep,
                                 2 bulk-copy adjoint sweep (nx % 16 == 0, nx <= 512) */
     LBMBT_OPT_ADJOINT_SHAPE = 10, /* bulk-copy adjoint consumers x sites per thread:
-                                0 = 256 x 2, 1 = 512 x 1 (default)              */
+                                0 = 256 x 2, 1 = 512 x 1, 2 = 480 x 1 (default;
+                                units of <= 480 sites, so a run with an
+                                nx > 480 takes shape 1)                        */
     LBMBT_OPT_LATTICE = 11   /* 0 (default) D3Q7; 1 the 2-D D2Q5 lattice of
                                 Sec. 2.3 (eps_D = 1/3, omega_0 = 1/3,
                                 omega_1..4 = 1/6; tau, P and the membrane

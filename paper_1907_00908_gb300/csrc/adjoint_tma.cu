@@ -21,7 +21,6 @@ namespace lbmbt {
 namespace {
 
 constexpr int ADJ_MAX_STAGES = 4;
-constexpr int ADJ_UNIT_SITES = 512;            // units of <= 512 sites
 constexpr int ADJ_SLOTS = 16;                  // gradient slots per unit (>= consumer warps)
 
 __host__ __device__ __forceinline__ size_t adj_stage_bytes(int cap)
@@ -361,14 +360,20 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
 }  // namespace
 
 int adj_tma_slots_per_unit() { return ADJ_SLOTS; }
-int adj_tma_max_sites() { return ADJ_UNIT_SITES; }
+// units of <= 512 sites (shapes 0, 1) or <= 480 (shape 2)
+int adj_tma_max_sites(int shape) { return shape == 2 ? 480 : 512; }
 
-// shape 0: 8 consumer warps x 2 sites (168 registers); 1: 16 x 1 (96 registers)
+// shape 0: 8 consumer warps x 2 sites (168 registers); 1: 16 x 1 (96
+// registers: with the producer, 17 warps put 5 on one of the SM's four
+// register-file partitions); 2: 15 x 1 (16 warps, 4 a partition: 127
+// registers, no spills)
 static void* adj_kernel(int shape)
 {
-    return shape == 1 ? (void*)adjoint_tma_kernel<512, 1> : (void*)adjoint_tma_kernel<256, 2>;
+    return shape == 1   ? (void*)adjoint_tma_kernel<512, 1>
+           : shape == 2 ? (void*)adjoint_tma_kernel<480, 1>
+                        : (void*)adjoint_tma_kernel<256, 2>;
 }
-static int adj_threads(int shape) { return shape == 1 ? 544 : 288; }
+static int adj_threads(int shape) { return shape == 1 ? 544 : shape == 2 ? 512 : 288; }
 
 cudaError_t adj_tma_prepare(int cap, int nst, int shape, int* ctas_per_sm)
 {
@@ -384,6 +389,7 @@ cudaError_t launch_adjoint_tma(const AdjointArgs& a, long long n_units, int cap,
     if (nst < 2 || nst > ADJ_MAX_STAGES) return cudaErrorInvalidValue;
     const size_t sm = adj_stage_bytes(cap) * nst;
     if (shape == 1) adjoint_tma_kernel<512, 1><<<grid, 544, sm, st>>>(a, n_units, cap, nst);
+    else if (shape == 2) adjoint_tma_kernel<480, 1><<<grid, 512, sm, st>>>(a, n_units, cap, nst);
     else adjoint_tma_kernel<256, 2><<<grid, 288, sm, st>>>(a, n_units, cap, nst);
     return cudaGetLastError();
 }

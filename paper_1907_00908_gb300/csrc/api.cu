@@ -85,7 +85,8 @@ struct lbmbt_ctx {
     int adj_cap = 0;
     int adjoint_opt = 0;          // 0 auto, 1 register adjoint, 2 bulk-copy adjoint
     int lattice = 0;              // 0 D3Q7, 1 D2Q5 (Sec. 2.3; grids of one z plane)
-    int adj_shape = 1;            // bulk-copy adjoint consumer shape (16 warps x 1 site)
+    int adj_shape = 2;            // bulk-copy adjoint consumer shape (15 warps x 1 site)
+    int adj_shape_used = 2;       // the shape of the prepared run (2 falls back to 1 when an nx > 480)
     bool use_tma = false;
     int tma_cap = 0;
     int tma_capx = 0;
@@ -644,6 +645,10 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     c->adj_unit_start.assign(c->n_members + 1, 0);
     int adj_cap = 16;
     bool adj_ok = true;
+    c->adj_shape_used = c->adj_shape;
+    for (auto& d : c->descs)
+        if (c->adj_shape == 2 && d.nx > adj_tma_max_sites(2)) c->adj_shape_used = 1;
+    const int adj_sites = adj_tma_max_sites(c->adj_shape_used);
     const bool want = c->kernel_opt == 2 || (c->kernel_opt == 0 && c->tuned_kernel != 1);
     const bool tma = want && tma_eligible(c);
     if (c->kernel_opt == 2 && !tma)
@@ -657,11 +662,11 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
         d.rpu = std::max(1, std::min(d.ny, TMA_TARGET_SITES / std::max(1, d.nx)));
         d.unit0 = c->unit_start[m];
         c->unit_start[m + 1] = c->unit_start[m] + (long long)d.nz * ((d.ny + d.rpu - 1) / d.rpu);
-        d.rpu_adj = std::max(1, std::min(d.ny, adj_tma_max_sites() / std::max(1, d.nx)));
+        d.rpu_adj = std::max(1, std::min(d.ny, adj_sites / std::max(1, d.nx)));
         d.unit0_adj = c->adj_unit_start[m];
         c->adj_unit_start[m + 1] = c->adj_unit_start[m] + (long long)d.nz * ((d.ny + d.rpu_adj - 1) / d.rpu_adj);
         adj_cap = std::max(adj_cap, d.rpu_adj * d.nx);
-        if (d.nx > adj_tma_max_sites()) adj_ok = false;
+        if (d.nx > adj_sites) adj_ok = false;
         cap = std::max(cap, d.rpu * d.nx);
         (void)capx;   // the x rotation table is read through L1, not staged
     }
@@ -1264,7 +1269,7 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         c->adjoint_opt = (int)v;
         break;
     case LBMBT_OPT_ADJOINT_SHAPE:
-        if (v < 0 || v > 1) return fail(c, LBMBT_EINVAL, "adjoint shape must be 0 or 1");
+        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "adjoint shape must be 0, 1 or 2");
         c->adj_shape = (int)v;
         break;
     case LBMBT_OPT_LATTICE:
@@ -1331,7 +1336,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     if (!rc) rc = grow(c, &c->d_seg, &c->cap_seg, lvl_total * (ck + 1) * sizeof(float2));
     const bool adj_tma = c->adjoint_opt == 2 || (c->adjoint_opt == 0 && c->adj_tma_ok);
     if (c->adjoint_opt == 2 && !c->adj_tma_ok)
-        return fail(c, LBMBT_EINVAL, "bulk-copy adjoint needs nx %% 16 == 0 and nx <= %d", adj_tma_max_sites());
+        return fail(c, LBMBT_EINVAL, "bulk-copy adjoint needs nx %% 16 == 0 and nx <= %d", adj_tma_max_sites(1));
     const long long n_gslots = adj_tma ? c->n_adj_units * adj_tma_slots_per_unit() : c->n_tiles;
     if (!rc) rc = grow(c, &c->d_gacc, &c->cap_gacc, sizeof(double) * NGACC * n_gslots);
     if (!rc) rc = grow(c, &c->d_gout, &c->cap_gout, sizeof(double) * NGACC * n);
@@ -1397,7 +1402,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     const int adj_stages = 3;
     if (adj_tma) {
         int per_sm = 0;
-        CU(c, adj_tma_prepare(c->adj_cap, adj_stages, c->adj_shape, &per_sm));
+        CU(c, adj_tma_prepare(c->adj_cap, adj_stages, c->adj_shape_used, &per_sm));
         if (per_sm < 1) return fail(c, LBMBT_EINVAL, "bulk-copy adjoint does not fit on an SM");
         if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
         adj_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_adj_units);
@@ -1440,7 +1445,8 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
             aa.lam_parity = parity;
             aa.fprev = (float)c->f[k - 1];
             if (adj_tma)
-                CU(c, launch_adjoint_tma(aa, c->n_adj_units, c->adj_cap, adj_stages, c->adj_shape, adj_grid, c->stream));
+                CU(c, launch_adjoint_tma(aa, c->n_adj_units, c->adj_cap, adj_stages, c->adj_shape_used, adj_grid,
+                                         c->stream));
             else CU(c, launch_adjoint(aa, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
             c->launches++;
             parity ^= 1;

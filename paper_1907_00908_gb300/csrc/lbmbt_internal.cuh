@@ -165,7 +165,7 @@ cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, 
                                cudaStream_t st);
 // bulk-copy adjoint (adjoint_tma.cu)
 int adj_tma_slots_per_unit();
-int adj_tma_max_sites();
+int adj_tma_max_sites(int shape);
 cudaError_t adj_tma_prepare(int cap, int nst, int shape, int* ctas_per_sm);
 cudaError_t launch_adjoint_tma(const AdjointArgs& a, long long n_units, int cap, int nst, int shape, int grid,
                                cudaStream_t st);

@@ -177,13 +177,13 @@ def test_bulk_copy_adjoint_matches_register_adjoint(lb, name):
     gG, f = oracle.pgse(c["b"], c["delta"], c["Delta"], c["dt"], c["d"])
     s = _setup(lb, geom, c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, gG)
     out = {}
-    for kern, shape in ((1, 0), (2, 0), (2, 1)):
+    for kern, shape in ((1, 0), (2, 0), (2, 1), (2, 2)):
         s.set_option(lb.OPT_ADJOINT_KERNEL, kern)
         s.set_option(lb.OPT_ADJOINT_SHAPE, shape)
         out[(kern, shape)] = s.grad(checkpoint_every=16)
     s.close()
     a = _logvec(out[(1, 0)], c["D"], c["T2"], c["kap"])
-    for key in ((2, 0), (2, 1)):
+    for key in ((2, 0), (2, 1), (2, 2)):
         b = _logvec(out[key], c["D"], c["T2"], c["kap"])
         assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max(), key
         assert out[(1, 0)]["S"] == out[key]["S"]
@@ -215,3 +215,23 @@ def test_adjoint_d2q5_matches_oracle_finite_differences(lb, bc, d):
     err = np.abs(a - b).max() / np.abs(b).max()
     assert err < 1e-3, (a, b, err)
     assert abs(g["S"] - S(D, T2, kap)) < 1e-5 * g["S"]
+
+
+def test_bulk_copy_adjoint_shape_falls_back_for_wide_rows(lb):
+    """The default bulk-copy adjoint shape takes units of <= 480 sites; a grid
+    with nx = 496 runs on the 512-site shape instead, and its gradients equal
+    the register adjoint's."""
+    rng = np.random.default_rng(31)
+    lab = rng.integers(0, 2, size=(3, 4, 496)).astype(np.int32)
+    geom = synth.Geometry(lab, np.array([0, 1], np.uint8), 0.5)
+    gG, f = oracle.pgse(1500.0, 0.4, 0.8, 0.02, (1.0, 0.0, 0.0))
+    s = _setup(lb, geom, (0, 0, 0), [2.0, 1.0], [80.0, 50.0], 0.05, 0.02, f, gG)
+    out = {}
+    for kern in (1, 2):
+        s.set_option(lb.OPT_ADJOINT_KERNEL, kern)
+        out[kern] = s.grad(checkpoint_every=8)
+    assert s.get_option(lb.OPT_ADJOINT_SHAPE) == 2
+    s.close()
+    a = _logvec(out[1], [2.0, 1.0], [80.0, 50.0], 0.05)
+    b = _logvec(out[2], [2.0, 1.0], [80.0, 50.0], 0.05)
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
