@@ -235,3 +235,29 @@ def test_device_inputs_equal_host_inputs(lb):
         outs.append((r["S"], fld.cpu().numpy()))
     assert outs[0][0] == outs[1][0]
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_removing_angles_keeps_positions(lb):
+    """set_link_angles(None) returns to the theta = 0 rule with the same
+    positions: the run equals a positions-only run bit for bit."""
+    g = synth.disks(32, 0.5, [[7.3, 8.1]], [4.4])
+    dl, th = synth.link_distances(g, (0, 0, 0)), synth.link_angles(g, (0, 0, 0))
+    gG, f = oracle.pgse(1500.0, 0.5, 1.0, DT, (1.0, 0.0, 0.0))
+    res = []
+    for drop in (True, False):
+        s = lb.Solver(0)
+        s.set_option(lb.OPT_LATTICE, 1)
+        s.set_geometry(g.labels, g.phase_of_label, g.dx, (0, 0, 0))
+        s.set_link_distances(dl)
+        if drop:
+            s.set_link_angles(th)
+            s.set_link_angles(None)
+        s.set_phases([2.0, 1.0], [80.0, 50.0])
+        s.set_permeability(0.03)
+        s.set_sequence(DT, f, gG)
+        fld = torch.zeros(g.n_sites, dtype=torch.complex64, device="cuda")
+        s.run(field=fld)
+        torch.cuda.synchronize()
+        s.close()
+        res.append(fld.cpu().numpy())
+    assert np.array_equal(res[0], res[1])
