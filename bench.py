@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import statistics
@@ -71,18 +72,24 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def sweep_source_hash():
+def _code_hash(files):
+    """Hash of the sources' code: comments, blank lines and trailing blanks
+    left out, so an edit of a comment keeps a capture valid."""
     h = hashlib.sha256()
-    for f in ("sweep_tma.cu", "sweep_common.cuh", "tma_common.cuh", "lbmbt_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f), "rb").read())
+    for f in files:
+        text = open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
+
+
+def sweep_source_hash():
+    return _code_hash(("sweep_tma.cu", "sweep_common.cuh", "tma_common.cuh", "lbmbt_internal.cuh"))
 
 
 def links_source_hash():
-    h = hashlib.sha256()
-    for f in ("sweep.cu", "links.cuh", "sweep_common.cuh", "lbmbt_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1907_00908_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
+    return _code_hash(("sweep.cu", "links.cuh", "sweep_common.cuh", "lbmbt_internal.cuh"))
 
 
 def links_traffic_per_launch(n):
@@ -263,6 +270,7 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     cyl, packs, members, f = batch_workload()
     s = lbmbt.Solver(0, stream)
+    s.set_option(lbmbt.OPT_STAGE_OWN_Z, args.stage_own_z)
     s.set_geometry(cyl.labels, cyl.phase_of_label, 0.5)
     for g in packs:
         s.add_geometry(g.labels, g.phase_of_label, 0.5)
@@ -631,6 +639,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--adj-shape", type=int, default=2, help="bulk-copy adjoint consumer shape (0, 1 or 2)")
+    ap.add_argument("--stage-own-z", type=int, default=0, choices=[0, 1, 2],
+                    help="bulk-copy sweep: own z rows 0 auto, 1 prefetched into registers, 2 staged")
     ap.add_argument("--members", type=int, default=60, help="adjoint workload: number of members (<= 60)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
@@ -681,6 +691,7 @@ def main():
     nm = len(seqs)
 
     s = lbmbt.Solver(local, stream)
+    s.set_option(lbmbt.OPT_STAGE_OWN_Z, args.stage_own_z)
     if not args.no_autotune:
         s.set_option(lbmbt.OPT_AUTOTUNE, 1)
     if args.block:
@@ -709,6 +720,7 @@ def main():
     shape = {"kernel": "bulk-copy" if s.get_option(lbmbt.OPT_KERNEL_USED) == 2 else "register",
              "tma_shape": s.get_option(lbmbt.OPT_TMA_SHAPE), "stages": s.get_option(lbmbt.OPT_STAGES),
              "block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT),
+             "own_z": {0: None, 1: "prefetched", 2: "staged"}[s.get_option(lbmbt.OPT_STAGE_OWN_Z_USED)],
              "autotuned": not args.no_autotune}
     from paper_1907_00908_gb300 import shard
     ms = shard.max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)

@@ -290,13 +290,22 @@ enum {
                                 0 = 256 x 2, 1 = 512 x 1, 2 = 480 x 1 (default;
                                 units of <= 480 sites, so a run with an
                                 nx > 480 takes shape 1)                        */
-    LBMBT_OPT_LATTICE = 11   /* 0 (default) D3Q7; 1 the 2-D D2Q5 lattice of
+    LBMBT_OPT_LATTICE = 11,  /* 0 (default) D3Q7; 1 the 2-D D2Q5 lattice of
                                 Sec. 2.3 (eps_D = 1/3, omega_0 = 1/3,
                                 omega_1..4 = 1/6; tau, P and the membrane
                                 coefficients use eps_D = 1/3) on geometries of
                                 one z plane, register sweep and register
                                 adjoint only (a forced bulk-copy adjoint
                                 returns EUNSUPPORTED)                          */
+    LBMBT_OPT_STAGE_OWN_Z = 12, /* bulk-copy sweep, geometries with membranes:
+                                where the own-site values of the z populations
+                                come from.  0 (default) auto: staged with the
+                                unit when some member with membranes has a
+                                plane of >= 2^17 sites, else prefetched into
+                                registers; 1 always prefetched; 2 always
+                                staged (2 more rows per stage slot)            */
+    LBMBT_OPT_STAGE_OWN_Z_USED = 13 /* read-only: 1 prefetched or 2 staged for a
+                                prepared bulk-copy run, else 0                 */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

@@ -92,6 +92,8 @@ struct lbmbt_ctx {
     int tma_capx = 0;
     int tma_stages = 3;
     int tma_variant = 3;
+    bool tma_oz = false;          // own z rows staged (a member with membranes and a large plane)
+    int oz_opt = 0;               // 0 auto, 1 prefetch, 2 stage
     int tuned_kernel = 0;         // 0: untuned, 1 register, 2 bulk copy (auto follows it)
     struct Tuned { int kernel, block, spt, variant, stages; };
     std::map<std::string, Tuned> tune_cache;
@@ -628,6 +630,11 @@ extern "C" int lbmbt_pgse(double b, double delta, double Delta, double dt, const
 // aligned rows and mask bytes) and a unit fits the shared-memory stages.
 static constexpr int TMA_TARGET_SITES = 1024;
 static constexpr int TMA_MAX_CAP = 1024;
+// Planes from this many sites on: the own z rows of a membrane geometry are
+// staged with the unit (a register prefetch of them would wait on DRAM, the
+// rows being next touched a plane later); below it the register prefetch is
+// faster (the rows are still in L2, and the smaller stage leaves more L1).
+static constexpr long long TMA_OZ_PLANE = 1LL << 17;
 
 static bool tma_eligible(const lbmbt_ctx* c)
 {
@@ -680,12 +687,17 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     if (tma) {
         c->tma_cap = (cap + 15) / 16 * 16;
         c->tma_capx = (capx + 15) / 16 * 16;
+        c->tma_oz = c->oz_opt == 2;
+        if (c->oz_opt == 0)
+            for (auto& d : c->descs)
+                if (d.memb && (long long)d.nx * d.ny >= TMA_OZ_PLANE) c->tma_oz = true;
         int per_sm = 0;
-        const cudaError_t pe = tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, &per_sm);
+        const cudaError_t pe = tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_oz,
+                                           &per_sm);
         if (pe == cudaErrorInvalidValue) {   // more shared memory than a block may have
             cudaGetLastError();
             return fail(c, LBMBT_EINVAL, "%d bulk-copy stages of %d sites (%zu bytes) do not fit in shared memory",
-                        c->tma_stages, c->tma_cap, tma_smem_bytes(c->tma_cap, c->tma_capx, c->tma_stages));
+                        c->tma_stages, c->tma_cap, tma_smem_bytes(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_oz));
         }
         CU(c, pe);
         if (per_sm < 1) return fail(c, LBMBT_EINVAL, "bulk-copy sweep does not fit on an SM");
@@ -784,8 +796,8 @@ static int issue_step(lbmbt_ctx* c)
     SweepArgs a = sweep_args(c);
     if (c->use_tma) {
         a.tile_start = c->d_unit_start;
-        CU(c, launch_sweep_tma(a, c->n_units, c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_grid,
-                               c->stream));
+        CU(c, launch_sweep_tma(a, c->n_units, c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_oz,
+                               c->tma_grid, c->stream));
     } else {
         CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
     }
@@ -1277,6 +1289,10 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         invalidate_run(c);
         c->lattice = (int)v;
         break;
+    case LBMBT_OPT_STAGE_OWN_Z:
+        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "own-z staging must be 0 (auto), 1 or 2");
+        c->oz_opt = (int)v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -1297,6 +1313,8 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_ADJOINT_KERNEL: *v = c->adjoint_opt; break;
     case LBMBT_OPT_ADJOINT_SHAPE: *v = c->adj_shape; break;
     case LBMBT_OPT_LATTICE: *v = c->lattice; break;
+    case LBMBT_OPT_STAGE_OWN_Z: *v = c->oz_opt; break;
+    case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? (c->tma_oz ? 2 : 1) : 0; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }

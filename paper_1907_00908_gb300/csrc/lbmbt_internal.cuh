@@ -130,11 +130,14 @@ cudaError_t launch_reduce(const double2* partial, const long long* tile_start, i
                           const StepCtl* ctl, cudaStream_t st);
 
 // ---- bulk-copy sweep (sweep_tma.cu) --------------------------------------
-size_t tma_smem_bytes(int cap, int capx, int nst);
+// oz: the own rows of planes 5 and 6 go through the stage (wanted where
+// planes are large, so those rows would otherwise come from DRAM a plane
+// later); without it they are prefetched into registers with planes 3 and 4.
+size_t tma_smem_bytes(int cap, int capx, int nst, bool oz);
 int tma_partials_per_unit(int variant);
-cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int* ctas_per_sm);
-cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
-                             cudaStream_t st);
+cudaError_t tma_prepare(int cap, int capx, int nst, int variant, bool oz, int* ctas_per_sm);
+cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, bool oz,
+                             int grid, cudaStream_t st);
 
 // ---- adjoint (adjoint.cu) -------------------------------------------------
 // Per-tile gradient accumulators: [0..3] sum <lambda, w M - g> per phase

@@ -13,9 +13,12 @@
 // collides and stores them with no branch between sites (phase 2), so the
 // arithmetic of several sites interleaves.  The own-site values of planes
 // 3 and 4 (membrane links in y) are prefetched into registers one unit
-// ahead; the own rows of planes 5 and 6 (membrane links in z) are staged
-// with the unit, since those rows are otherwise first touched a whole plane
-// later, and a load at a membrane lane waited on DRAM.
+// ahead.  Those of planes 5 and 6 (membrane links in z) come in one of two
+// forms, chosen per run (template flag OZ): staged with the unit (large
+// planes: the rows are otherwise first touched a whole plane later, and a
+// load at a membrane lane waited on DRAM), or prefetched like planes 3 and 4
+// (small planes: the rows are still in L2, and the smaller stage leaves more
+// of the SM's memory to L1).
 //
 // Source row-blocks of a unit starting at site s0 (all 16-byte aligned when
 // nx is even; the mask copy needs nx % 16 == 0):
@@ -27,7 +30,7 @@
 //   plane 4 (-y) rows y+1 (last row: wrapped row, or own row of plane 3)
 //   plane 5 (+z) plane z-1 (z = 0: wrapped plane, or own rows of plane 6)
 //   plane 6 (-z) plane z+1 (last plane: wrapped, or own rows of plane 5)
-//   own rows of planes 5 and 6 [s0, s0+L) (geometries with membranes only)
+//   own rows of planes 5 and 6 [s0, s0+L) (OZ and geometries with membranes)
 // The boundary factors (periodic phase, mirror conjugation and rewind) are
 // applied per element after the copy, exactly as in the register kernel.
 //
@@ -44,22 +47,24 @@ namespace {
 constexpr int TMA_MAX_STAGES = 6;
 
 // Shared-memory stage (all parts 16-byte aligned): 7 pull rows of (cap + 2)
-// complex values (the sources listed above), the own rows of planes 5 and 6
-// (slots 7 and 8), capx spare complex values (0 in use), then cap mask bytes.
-__host__ __device__ __forceinline__ size_t stage_bytes(int cap, int capx)
+// complex values (the sources listed above), with OZ the own rows of planes
+// 5 and 6 (slots 7 and 8), capx spare complex values (0 in use), then cap
+// mask bytes.
+__host__ __device__ __forceinline__ size_t stage_bytes(int cap, int capx, bool oz)
 {
-    return (((size_t)9 * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
+    return (((size_t)(oz ? 9 : 7) * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
 }
 __device__ __forceinline__ float2* stage_plane(unsigned char* stage, int cap, int i)
 {
     return reinterpret_cast<float2*>(stage) + (size_t)i * (cap + 2);
 }
-__device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, int capx)
+__device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, int capx, bool oz)
 {
-    return stage + ((size_t)9 * (cap + 2) + capx) * sizeof(float2);
+    return stage + ((size_t)(oz ? 9 : 7) * (cap + 2) + capx) * sizeof(float2);
 }
 
 // Thread 0: copies of unit u into `stage`, completion on `bar`.
+template <bool OZ>
 __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, int smod, unsigned char* stage, int cap,
                            int capx, uint64_t* bar, UnitGeo* info)
 {
@@ -75,9 +80,10 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
     auto pl = [&](int i) { return src + (size_t)i * P; };
     const uint32_t rowb = (uint32_t)(nx * sizeof(float2));
     const uint32_t Lb = (uint32_t)(L * sizeof(float2));
-    const uint32_t total = 5 * Lb + 2 * (Lb + 16) + (uint32_t)L + (d.memb ? 2 * Lb : 0u);
+    const bool oz = OZ && d.memb;
+    const uint32_t total = 5 * Lb + 2 * (Lb + 16) + (uint32_t)L + (oz ? 2 * Lb : 0u);
     mbar_arrive_expect_tx(bar, total);
-    if (d.memb) {   // own rows of planes 5 and 6 (membrane links in z)
+    if (oz) {   // own rows of planes 5 and 6 (membrane links in z)
         bulk_g2s(stage_plane(stage, cap, 7), pl(5) + s0, Lb, bar);
         bulk_g2s(stage_plane(stage, cap, 8), pl(6) + s0, Lb, bar);
     }
@@ -122,7 +128,7 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
         else srcz = b1 == BC_PER ? pl(6) + (long long)y0 * nx : pl(5) + s0;
         bulk_g2s(stage_plane(stage, cap, 6), srcz, Lb, bar);
     }
-    bulk_g2s(stage_mask(stage, cap, capx), d.mask + s0, (uint32_t)L, bar);
+    bulk_g2s(stage_mask(stage, cap, capx, OZ), d.mask + s0, (uint32_t)L, bar);
 }
 
 
@@ -133,7 +139,7 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
 // mbarrier (one arrival per consumer warp when it is done with the stage).
 // No block-wide barrier is used after set-up: every wait is an mbarrier wait
 // with a time limit, so a failed wait ends each warp on its own.
-template <int TMA_CONSUMERS, int TMA_SPT>
+template <int TMA_CONSUMERS, int TMA_SPT, bool OZ>
 __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     sweep_tma_kernel(const SweepArgs a, long long n_units, int cap, int capx, int nst)
 {
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     __shared__ UnitGeo infos[TMA_MAX_STAGES];
     __shared__ int s_abort;
 
-    const size_t stb = stage_bytes(cap, capx);
+    const size_t stb = stage_bytes(cap, capx, OZ);
     const int tid = threadIdx.x;
     const int k = __ldcg(&a.ctl->k);
     const int sbase = __ldcg(&a.ctl->slot_base), smod = __ldcg(&a.ctl->slot_mod);
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 break;
             }
             fence_proxy_async_smem();
-            issue_unit(a, u, k, sbase, smod, smem + st * stb, cap, capx, &full[st], &infos[st]);
+            issue_unit<OZ>(a, u, k, sbase, smod, smem + st * stb, cap, capx, &full[st], &infos[st]);
         }
         // wait (bounded) for the copies of the last stages before leaving
         for (long long q = j - 1; q >= 0 && q >= j - nst; --q)
@@ -190,8 +196,8 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 
     // Own-site values of planes 3 and 4 on membrane links in y, prefetched
     // into registers one unit ahead for the lanes whose mask needs them.
-    float2 own[TMA_SPT][2], nown[TMA_SPT][2];
-    auto prefetch = [&](long long j, float2 (&o)[TMA_SPT][2]) -> bool {
+    float2 own[TMA_SPT][4], nown[TMA_SPT][4];
+    auto prefetch = [&](long long j, float2 (&o)[TMA_SPT][4]) -> bool {
         if (unit_of(j) >= n_units) return true;
         const int st = (int)(j % nst);
         if (!mbar_wait(&full[st], (uint32_t)((j / nst) & 1))) return false;
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         const MemberDesc* __restrict__ d = a.members + G.m;
         if (!d->memb) return true;   // geometry without membranes
         unsigned char* sb = smem + st * stb;
-        const uint8_t* __restrict__ mk8 = stage_mask(sb, cap, capx);
+        const uint8_t* __restrict__ mk8 = stage_mask(sb, cap, capx, OZ);
         const unsigned P = (unsigned)d->plane;
         const float2* __restrict__ sp = d->state + (size_t)lsrc * 7 * P;
 #pragma unroll
@@ -210,6 +216,10 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 const unsigned s = G.s0 + (unsigned)l;
                 if (mk & 4u) o[jj][0] = __ldg(sp + (size_t)3 * P + s);
                 if (mk & 8u) o[jj][1] = __ldg(sp + (size_t)4 * P + s);
+                if (!OZ) {
+                    if (mk & 16u) o[jj][2] = __ldg(sp + (size_t)5 * P + s);
+                    if (mk & 32u) o[jj][3] = __ldg(sp + (size_t)6 * P + s);
+                }
 
             }
         }
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         const float2* __restrict__ r4 = stage_plane(sb, cap, 4);
         const float2* __restrict__ r5 = stage_plane(sb, cap, 5);
         const float2* __restrict__ r6 = stage_plane(sb, cap, 6);
-        const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx);
+        const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx, OZ);
         const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + G.m) * 6;
         float2* __restrict__ dst = dstb;
         const bool do_field = field_step && field != nullptr;
@@ -300,8 +310,8 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 if (mk & 1u) g[j][2] = mix(r1[l + 2], g[j][2], sh);      // link to +x: own hat g_1
                 if (mk & 8u) g[j][3] = mix(own[j][1], g[j][3], sh);      // link to -y: own hat g_4
                 if (mk & 4u) g[j][4] = mix(own[j][0], g[j][4], sh);      // link to +y: own hat g_3
-                if (mk & 32u) g[j][5] = mix(stage_plane(sb, cap, 8)[l], g[j][5], sh);   // link to -z: own hat g_6
-                if (mk & 16u) g[j][6] = mix(stage_plane(sb, cap, 7)[l], g[j][6], sh);   // link to +z: own hat g_5
+                if (mk & 32u) g[j][5] = mix(OZ ? stage_plane(sb, cap, 8)[l] : own[j][3], g[j][5], sh);   // -z: own hat g_6
+                if (mk & 16u) g[j][6] = mix(OZ ? stage_plane(sb, cap, 7)[l] : own[j][2], g[j][6], sh);   // +z: own hat g_5
             }
             mks[j] = mk;
             xs[j] = x;
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 #pragma unroll
         for (int j = 0; j < TMA_SPT; ++j)
 #pragma unroll
-            for (int p = 0; p < 2; ++p) own[j][p] = nown[j][p];
+            for (int p = 0; p < 4; ++p) own[j][p] = nown[j][p];
         if (do_sig) {   // grid-uniform; FP64 from the warp level up, one slot per warp
             double dr = zr, di = zi;
             for (int o = 16; o > 0; o >>= 1) {
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 
 }  // namespace
 
-size_t tma_smem_bytes(int cap, int capx, int nst) { return stage_bytes(cap, capx) * nst; }
+size_t tma_smem_bytes(int cap, int capx, int nst, bool oz) { return stage_bytes(cap, capx, oz) * nst; }
 // signal partial slots per unit: one per consumer warp of the variant
 int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2 ? 8 : variant == 3 ? 11 : 16; }
 
@@ -392,40 +402,54 @@ int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2
 // 11 x 3 (units <= 1024 sites).  The register file is split over the SM's 4
 // sub-partitions: with the producer warp, 9 to 12 warps per CTA allow 168
 // registers a thread, 13 to 16 warps 128 and 17 warps 96; the two-phase
-// consumer needs about 150.
-static void* tma_kernel(int variant)
+// consumer needs about 150.  Each in two forms: with the own z rows staged
+// (oz) or prefetched into registers.
+template <bool OZ>
+static void* tma_kernel_oz(int variant)
 {
     switch (variant) {
-    case 1: return (void*)sweep_tma_kernel<384, 3>;
-    case 2: return (void*)sweep_tma_kernel<256, 4>;
-    case 3: return (void*)sweep_tma_kernel<352, 3>;
-    default: return (void*)sweep_tma_kernel<512, 2>;
+    case 1: return (void*)sweep_tma_kernel<384, 3, OZ>;
+    case 2: return (void*)sweep_tma_kernel<256, 4, OZ>;
+    case 3: return (void*)sweep_tma_kernel<352, 3, OZ>;
+    default: return (void*)sweep_tma_kernel<512, 2, OZ>;
     }
 }
+static void* tma_kernel(int variant, bool oz) { return oz ? tma_kernel_oz<true>(variant) : tma_kernel_oz<false>(variant); }
 static int tma_threads(int variant)
 {
     return variant == 1 ? 384 + 32 : variant == 2 ? 256 + 32 : variant == 3 ? 352 + 32 : 512 + 32;
 }
 
-cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int* ctas_per_sm)
+cudaError_t tma_prepare(int cap, int capx, int nst, int variant, bool oz, int* ctas_per_sm)
 {
-    const size_t bytes = tma_smem_bytes(cap, capx, nst);
-    cudaError_t e = cudaFuncSetAttribute(tma_kernel(variant), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const size_t bytes = tma_smem_bytes(cap, capx, nst, oz);
+    void* fn = tma_kernel(variant, oz);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, tma_kernel(variant), tma_threads(variant), bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, tma_threads(variant), bytes);
 }
 
-cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
-                             cudaStream_t st)
+template <bool OZ>
+static void launch_oz(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
+                      size_t sm, cudaStream_t st)
+{
+    switch (variant) {
+    case 1: sweep_tma_kernel<384, 3, OZ><<<grid, 384 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 2: sweep_tma_kernel<256, 4, OZ><<<grid, 256 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 3: sweep_tma_kernel<352, 3, OZ><<<grid, 352 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    default: sweep_tma_kernel<512, 2, OZ><<<grid, 512 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    }
+}
+
+cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, bool oz,
+                             int grid, cudaStream_t st)
 {
     if (nst < 2 || nst > TMA_MAX_STAGES) return cudaErrorInvalidValue;
-    const size_t sm = tma_smem_bytes(cap, capx, nst);
-    switch (variant) {
-    case 1: sweep_tma_kernel<384, 3><<<grid, 384 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    case 2: sweep_tma_kernel<256, 4><<<grid, 256 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    case 3: sweep_tma_kernel<352, 3><<<grid, 352 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    default: sweep_tma_kernel<512, 2><<<grid, 512 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    }
+    const size_t sm = tma_smem_bytes(cap, capx, nst, oz);
+    if (oz)
+        launch_oz<true>(a, n_units, cap, capx, nst, variant, grid, sm, st);
+    else
+        launch_oz<false>(a, n_units, cap, capx, nst, variant, grid, sm, st);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,95 @@
+"""GPU: the two forms of the bulk-copy sweep for geometries with membranes --
+the own-site values of the z populations (needed at membrane links in z,
+Eq. B5) staged with the unit or prefetched into registers.  Both do the same
+arithmetic on the same values, so their fields must agree bit for bit, and
+each must match the FP64 oracle (S within 1e-5, field within 1e-4 of
+max|M|).  The automatic choice stages on large planes with membranes only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INF = math.inf
+
+
+@pytest.fixture(scope="module")
+def lb():
+    from paper_1907_00908_gb300 import lbmbt
+    lbmbt.lib()
+    return lbmbt
+
+
+def _run(lb, labels, pol, bc, D, T2, kap, dt, f, gG, oz):
+    s = lb.Solver(0)
+    s.set_option(lb.OPT_KERNEL, 2)
+    s.set_option(lb.OPT_STAGE_OWN_Z, oz)
+    s.set_geometry(labels, pol, 0.5, bc)
+    s.set_phases(D, T2)
+    s.set_permeability(kap)
+    s.set_sequence(dt, f, gG)
+    fld = torch.zeros(labels.size, dtype=torch.complex64, device="cuda")
+    r = s.run(field=fld)
+    torch.cuda.synchronize()
+    used = (s.get_option(lb.OPT_KERNEL_USED), s.get_option(lb.OPT_STAGE_OWN_Z_USED))
+    s.close()
+    return r, fld.cpu().numpy().reshape(labels.shape), used
+
+
+# a mirror face needs G normal or parallel to it (Sec. 2.4.4)
+@pytest.mark.parametrize("bc,gdir", [((0, 0, 0), (0.3, -0.5, 0.81)), ((1, 1, 1), (0.0, 0.0, 1.0)),
+                                     ((0, 1, 1), (1.0, 0.0, 0.0))])
+def test_forms_agree_and_match_oracle(lb, bc, gdir):
+    rng = np.random.default_rng(21)
+    labels = rng.integers(0, 3, size=(7, 12, 32)).astype(np.int32)
+    pol = np.array([0, 1, 2], np.uint8)
+    D, T2, kap, dt = [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.05, 0.02
+    gG, f = oracle.pgse(1500.0, 0.2, 0.4, dt, gdir)
+    out = {}
+    for oz in (1, 2):
+        r, fld, used = _run(lb, labels, pol, bc, D, T2, kap, dt, f, gG, oz)
+        assert used == (2, oz)
+        out[oz] = (r, fld)
+    assert np.array_equal(out[1][1], out[2][1])
+    assert out[1][0]["S"] == out[2][0]["S"]
+    o = oracle.run(labels, 0.5, pol, bc, D, T2, kap, dt, f, gG, want_field=True)
+    assert abs(out[2][0]["S"] - o["S"]) <= 1e-5 * o["S"]
+    assert np.abs(out[2][1] - o["field"]).max() < 1e-4 * np.abs(o["field"]).max()
+
+
+def test_auto_stages_large_planes_with_membranes(lb):
+    """A 512 x 256 plane (2^17 sites) with membranes: auto stages, and equals
+    the prefetching form bit for bit and the oracle within tolerance; the
+    same plane without membranes and a small plane with them prefetch."""
+    rng = np.random.default_rng(4)
+    nz, ny, nx = 3, 256, 512
+    labels = (rng.random((nz, ny // 8, nx // 8)) < 0.4).astype(np.int32)
+    labels = np.repeat(np.repeat(labels, 8, axis=1), 8, axis=2)
+    pol = np.array([0, 1], np.uint8)
+    D, T2, kap, dt = [2.0, 1.0], [80.0, 50.0], 0.05, 0.02
+    gG, f = oracle.pgse(1500.0, 0.06, 0.1, dt, (0.3, 0.5, 0.81))
+    ra, fa, used = _run(lb, labels, pol, (0, 0, 0), D, T2, kap, dt, f, gG, 0)
+    assert used == (2, 2)
+    rb, fb, used = _run(lb, labels, pol, (0, 0, 0), D, T2, kap, dt, f, gG, 1)
+    assert used == (2, 1)
+    assert np.array_equal(fa, fb)
+    o = oracle.run(labels, 0.5, pol, (0, 0, 0), D, T2, kap, dt, f, gG, want_field=True)
+    assert abs(ra["S"] - o["S"]) <= 1e-5 * o["S"]
+    assert np.abs(fa - o["field"]).max() < 1e-4 * np.abs(o["field"]).max()
+    _, _, used = _run(lb, np.zeros_like(labels), pol, (0, 0, 0), D, T2, kap, dt, f[:4], gG, 0)
+    assert used == (2, 1)
+    _, _, used = _run(lb, labels[:, :128], pol, (0, 0, 0), D, T2, kap, dt, f[:4], gG, 0)
+    assert used == (2, 1)
+
+
+def test_option_range(lb):
+    s = lb.Solver(0)
+    with pytest.raises(lb.LbmbtError):
+        s.set_option(lb.OPT_STAGE_OWN_Z, 3)
+    assert s.get_option(lb.OPT_STAGE_OWN_Z) == 0
+    assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == 0
+    s.close()
