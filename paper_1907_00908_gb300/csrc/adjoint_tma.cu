@@ -148,15 +148,42 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
     // ---------------- consumer warps
     const int warp = tid >> 5, lane = tid & 31;
     const float fk = a.fprev;
+    // Gradient partials stay in registers over the CTA's consecutive units of
+    // one member (a run) and go, warp-reduced, to the slot of (the run's first
+    // unit, warp): the unit-to-CTA map is fixed, so every step adds the same
+    // groups in the same order.
+    float acc[NGACC];
+#pragma unroll
+    for (int q = 0; q < NGACC; ++q) acc[q] = 0.f;
+    long long u_run = -1;
+    int m_run = -1;
+    auto flush = [&]() {
+#pragma unroll
+        for (int q = 0; q < NGACC; ++q)
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+        if (lane == 0) {
+            double* g = a.gacc + ((size_t)u_run * ADJ_SLOTS + warp) * NGACC;
+#pragma unroll
+            for (int q = 0; q < NGACC; ++q) g[q] += (double)acc[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NGACC; ++q) acc[q] = 0.f;
+    };
     for (long long i = 0;; ++i) {
         const long long u = unit_of(i);
         if (u >= n_units) break;
         const int st = (int)(i % nst);
-        if (!mbar_wait(&full[st], (uint32_t)((i / nst) & 1))) {
+        // warp-uniform, so the warp's lanes leave the loop together
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((i / nst) & 1)))) {
             s_abort = 1;
             break;
         }
         const UnitGeo G = infos[st];
+        if (G.m != m_run) {
+            if (m_run >= 0) flush();
+            m_run = G.m;
+            u_run = u;
+        }
         const MemberDesc* __restrict__ sd = a.members + G.m;
         unsigned char* sb = smem + st * stb;
         const float2* __restrict__ U = reinterpret_cast<const float2*>(sb);
@@ -208,9 +235,6 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
             }
         }
 
-        float acc[NGACC];
-#pragma unroll
-        for (int q = 0; q < NGACC; ++q) acc[q] = 0.f;
 #pragma unroll
         for (int j = 0; j < ADJ_SPT; ++j) {
             const int l = tid + j * ADJ_CONSUMERS;
@@ -344,16 +368,8 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
-        // per (unit, warp) slot; the same warp of the same CTA owns it every step
-#pragma unroll
-        for (int q = 0; q < NGACC; ++q)
-            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
-        if (lane == 0) {
-            double* g = a.gacc + ((size_t)u * ADJ_SLOTS + warp) * NGACC;
-#pragma unroll
-            for (int q = 0; q < NGACC; ++q) g[q] += (double)acc[q];
-        }
     }
+    if (m_run >= 0) flush();
     if (s_abort && tid == 0) atomicOr(&a.ctl_err[0], 1);
 }
 
