@@ -157,6 +157,12 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
     for (int q = 0; q < NGACC; ++q) acc[q] = 0.f;
     long long u_run = -1;
     int m_run = -1;
+    // constants of the current member, reloaded only when the member changes
+    const MemberDesc* __restrict__ sd = a.members;
+    int nx = 1, ny = 1, nz = 1, bcx = 0, bcy = 0, bcz = 0, ax = 0, rmode = 0, ds0 = 0;
+    unsigned P = 0, dm0 = 0;
+    float sh = 0.f;
+    float2 sL = make_float2(0.f, 0.f);
     auto flush = [&]() {
 #pragma unroll
         for (int q = 0; q < NGACC; ++q)
@@ -183,40 +189,38 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
             if (m_run >= 0) flush();
             m_run = G.m;
             u_run = u;
+            sd = a.members + G.m;
+            nx = sd->nx; ny = sd->ny; nz = sd->nz;
+            bcx = sd->bc[0]; bcy = sd->bc[1]; bcz = sd->bc[2];
+            P = (unsigned)sd->plane;
+            dm0 = sd->div_m[0]; ds0 = sd->div_s[0];
+            sh = sd->s_share;
+            ax = sd->axes;
+            const bool tab = sd->etab != nullptr && (fk == 1.f || fk == -1.f);
+            rmode = fk == 0.f ? 0 : !tab ? 3 : (ax == 1 || ax == 2 || ax == 4) ? 1 : 2;
+            if (a.first) {
+                const double2 Ld = a.lam_init[G.m];
+                sL = make_float2((float)Ld.x, (float)Ld.y);
+            }
         }
-        const MemberDesc* __restrict__ sd = a.members + G.m;
         unsigned char* sb = smem + st * stb;
         const float2* __restrict__ U = reinterpret_cast<const float2*>(sb);
         const float2* __restrict__ V = U + (size_t)7 * (cap + 2);
         const uint8_t* __restrict__ rm = sb + (size_t)14 * (cap + 2) * sizeof(float2);
         auto Us = [&](int i2) { return U + (size_t)i2 * (cap + 2); };
         auto Vs = [&](int i2) { return V + (size_t)i2 * (cap + 2); };
-        const int nx = sd->nx, ny = sd->ny, nz = sd->nz;
-        const int bcx = sd->bc[0], bcy = sd->bc[1], bcz = sd->bc[2];
-        const unsigned P = (unsigned)sd->plane;
         const float2* __restrict__ ug = sd->state + (size_t)a.fwd_slot * 7 * P;
         const float2* __restrict__ vg = sd->adj + (size_t)a.lam_parity * 7 * P;
         float2* __restrict__ out = sd->adj + (size_t)(a.lam_parity ^ 1) * 7 * P;
         const float2* __restrict__ facP = a.ftab + ((size_t)(a.k - 1) * a.n_members + G.m) * 6;
         const float2* __restrict__ facK = a.ftab + ((size_t)a.k * a.n_members + G.m) * 6;
-        const float sh = sd->s_share;
-        const float ep0 = sd->eps[0], ep1 = sd->eps[1], ep2 = sd->eps[2], ep3 = sd->eps[3];
-        const float om0 = sd->omega[0], om1 = sd->omega[1], om2 = sd->omega[2], om3 = sd->omega[3];
-        // reaction rotation form of this unit (values as rotation_m1): 0 none
-        // (f = 0), 1 one table entry (G on one axis), 2 x and y entries per
-        // site and the z entry per unit, 3 general
         const float2* __restrict__ et = sd->etab;
-        const int ax = sd->axes;
-        const bool tab = et != nullptr && (fk == 1.f || fk == -1.f);
-        const int rmode = fk == 0.f ? 0 : !tab ? 3 : (ax == 1 || ax == 2 || ax == 4) ? 1 : 2;
+        // reaction rotation form of the member (values as rotation_m1): 0
+        // none (f = 0), 1 one table entry (G on one axis), 2 x and y entries
+        // per site and the z entry per unit, 3 general
         const float2* __restrict__ rbase = et + (ax == 1 ? 0 : ax == 2 ? nx : nx + ny + G.z);
         const int rcx = ax == 1, rcy = ax == 2;
         const float2 ez = rmode == 2 ? __ldg(et + nx + ny + G.z) : make_float2(0.f, 0.f);
-        float2 sL = make_float2(0.f, 0.f);
-        if (a.first) {
-            const double2 Ld = a.lam_init[G.m];
-            sL = make_float2((float)Ld.x, (float)Ld.y);
-        }
 
         // own-site values of planes 3..6 for membrane links in y and z
         float2 ou[ADJ_SPT][4], ov[ADJ_SPT][4];
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
         for (int j = 0; j < ADJ_SPT; ++j) {
             const int l = tid + j * ADJ_CONSUMERS;
             if (l >= G.rows * nx) break;
-            const int r = G.rows == 1 ? 0 : (int)fdiv((unsigned)l, sd->div_m[0], sd->div_s[0]);
+            const int r = G.rows == 1 ? 0 : (int)fdiv((unsigned)l, dm0, ds0);
             const int x = l - r * nx, y = G.y0 + r, z = G.z;
             const unsigned s = G.s0 + (unsigned)l;
             const unsigned mk = rm[l];
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
                 if (mk & 32u) gp[5] = mix(own[5], gp[5], sh);
                 if (mk & 16u) gp[6] = mix(own[6], gp[6], sh);
             }
-            const float ep = (ph & 2) ? ((ph & 1) ? ep3 : ep2) : ((ph & 1) ? ep1 : ep0);
+            const float ep = __ldg(sd->eps + ph);   // the member's values, L1-resident
             float2 rot;
             if (rmode == 0) {
                 rot = make_float2(0.f, 0.f);
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
                 lwr += w * lam[i2].x;
                 lwi += w * lam[i2].y;
             }
-            const float om = (ph & 2) ? ((ph & 1) ? om3 : om2) : ((ph & 1) ? om1 : om0);
+            const float om = __ldg(sd->omega + ph);
             const float er = 1.f + rot.x, ei = rot.y;
             float dEp = 0.f;
 #pragma unroll
