@@ -273,6 +273,34 @@ def test_slab_reference_matches_mitra_short_time_limit():
         assert dev == pytest.approx(mitra, rel=3e-3)
 
 
+def test_slab_reference_matches_gaussian_phase_long_pulse_limit():
+    """Pin of the continuum reference in the motional-narrowing regime: pulses
+    much longer than a^2/D, with little phase per correlation time (gG a^3/D
+    small), give a Gaussian phase whose variance follows from the slab's
+    position autocorrelation C(tau) = sum over odd n of 8 a^2/(n pi)^4
+    exp(-(n pi)^2 D tau/a^2), so that int C = a^4/(120 D) and
+    int tau C = 17 a^6/(20160 D^2).  For PGSE with Delta - delta >> a^2/D
+    the two pulses decorrelate and -ln E = 2 gG^2 (delta int C - int tau C).
+    The next cumulant is smaller by (gG a^3/D)^2: the deviation must fall
+    with it."""
+    a, D, dt = 2.0, 2.0, 1.0
+    i0, i1 = a ** 4 / (120 * D), 17 * a ** 6 / (20160 * D ** 2)
+    devs, pars = [], []
+    for delta, gG in ((500.0, 0.06), (2000.0, 0.03), (2000.0, 0.015)):
+        n = int(round(delta / dt))
+        f = np.zeros(3 * n)
+        f[:n] = 1.0
+        f[2 * n:] = -1.0
+        E = refs.slab_signal(a, D, gG, f, dt, n_modes=60)
+        expect = -2 * gG ** 2 * (delta * i0 - i1)
+        devs.append(abs(math.log(E) / expect - 1))
+        pars.append(gG * a ** 3 / D)
+    assert max(devs) < 1e-4
+    for j in (1, 2):   # quadratic fall-off with the narrowing parameter
+        ratio = (devs[0] / devs[j]) / (pars[0] / pars[j]) ** 2
+        assert 0.5 < ratio < 2.0, (devs, pars)
+
+
 def test_exchange_reference_matches_karger_limit():
     """Pin of the exchange reference: for kappa a/D << 1 the compartments are
     well mixed and the Karger two-compartment ODE holds."""
