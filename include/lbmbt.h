@@ -272,7 +272,8 @@ int lbmbt_grad_batch(lbmbt_ctx* ctx, int n_members, const lbmbt_member* members,
 enum {
     LBMBT_OPT_GRAPH = 1,     /* 1 (default): replay step loops as CUDA graphs   */
     LBMBT_OPT_AUTOTUNE = 2,  /* 1: time launch shapes on first use (default 0)  */
-    LBMBT_OPT_BLOCK = 3,     /* threads per block of the sweep (64..1024)       */
+    LBMBT_OPT_BLOCK = 3,     /* threads per block of the register sweep: a
+                                multiple of 32 in 64..512                      */
     LBMBT_OPT_SPT = 4,       /* sites per thread of the sweep (1, 2 or 4)       */
     LBMBT_OPT_KERNEL = 5,    /* 0 (default) auto, 1 register sweep, 2 bulk-copy
                                 (TMA) sweep; auto takes the bulk-copy sweep when

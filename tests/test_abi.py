@@ -28,6 +28,25 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(lbmbt.EXPORTS)
 
 
+def test_binding_constants_match_the_header():
+    """Every status code, face kind, boundary kind and option number of the
+    header has the same value in the Python binding, and the binding names
+    no option the header lacks."""
+    txt = open(os.path.join(ROOT, "include", "lbmbt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\bLBMBT_([A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    assert len(consts) >= 25
+    for name, v in consts.items():
+        if name == "OK":
+            assert lbmbt.LBMBT_OK == v
+        elif name.startswith("E"):
+            assert lbmbt.STATUS[v] == name, name
+        else:
+            assert getattr(lbmbt, name) == v, name
+    opts = {n for n in dir(lbmbt) if n.startswith("OPT_")}
+    assert opts == {n for n in consts if n.startswith("OPT_")}
+
+
 def test_version_string():
     assert b"sm_103a" in lbmbt.lib().lbmbt_version()
 
