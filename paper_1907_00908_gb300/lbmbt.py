@@ -118,6 +118,28 @@ def _p(a):
     raise TypeError(type(a))
 
 
+def _device_tensor(t, dtype, what, numel=None):
+    """Check a torch tensor that the library reads or writes in place through
+    its data pointer alone: on a CUDA device, of the expected dtype
+    (``"int32"``, ``"uint8"``, ``"float32"``, ``"complex64"``), contiguous,
+    and with at least ``numel`` elements when given.  None and raw integer
+    device pointers pass unchecked."""
+    if t is None or isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor, got one on {t.device}")
+    if t.dtype != getattr(torch, dtype):
+        raise TypeError(f"{what}: expected dtype torch.{dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: the tensor must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{what}: {t.numel()} elements, at least {numel} needed")
+    return t
+
+
 def pgse(b_s_mm2, delta, Delta, dt, direction=(1.0, 0.0, 0.0)):
     """``lbmbt_pgse``: returns (gamma_G0[3], f[K])."""
     L = lib()
@@ -139,6 +161,8 @@ def sweep_noalloc(mask_dev, shape, dx, bc, D, T2, kappa, dt, f, gG, state_dev, k
     inside the library.  Returns {Z, S} after step k0 + n_steps."""
     L = lib()
     nz, ny, nx = shape
+    _device_tensor(mask_dev, "uint8", "sweep_noalloc mask")          # sizes: the caller's, checked by the
+    _device_tensor(state_dev, "complex64", "sweep_noalloc state")    # library against its limits only
     bcv = np.ascontiguousarray(bc, np.int32)
     Dv = np.ascontiguousarray(np.atleast_1d(D), np.float64)
     T2v = np.ascontiguousarray(np.atleast_1d(T2), np.float64)
@@ -201,8 +225,7 @@ class Solver:
         """labels: int32 [nz, ny, nx] numpy (host) or torch CUDA tensor (device)."""
         on_dev = hasattr(labels, "is_cuda") and labels.is_cuda
         if on_dev:
-            import torch
-            assert labels.dtype == torch.int32 and labels.is_contiguous()
+            _device_tensor(labels, "int32", "labels")
             nz, ny, nx = labels.shape
         else:
             labels = np.ascontiguousarray(labels, np.int32)
@@ -226,7 +249,9 @@ class Solver:
         """``lbmbt_set_geometry_slab``: labels_ext int32 [nz + 2, ny, nx] (ghost
         plane below, the slab's planes, ghost plane above), numpy or torch CUDA."""
         on_dev = hasattr(labels_ext, "is_cuda") and labels_ext.is_cuda
-        if not on_dev:
+        if on_dev:
+            _device_tensor(labels_ext, "int32", "labels_ext")
+        else:
             labels_ext = np.ascontiguousarray(labels_ext, np.int32)
         nz2, ny, nx = labels_ext.shape
         pol = np.ascontiguousarray(phase_of_label, np.uint8)
@@ -240,11 +265,21 @@ class Solver:
 
     def slab_faces(self, member, lo_out, hi_out):
         """Copy the faces leaving the slab (complex64 [ny, nx] tensors or None)."""
+        n = self._face_sites()
+        _device_tensor(lo_out, "complex64", "slab_faces lo_out", n)
+        _device_tensor(hi_out, "complex64", "slab_faces hi_out", n)
         self._chk(self.L.lbmbt_slab_faces(self.h, int(member), _p(lo_out), _p(hi_out)), "slab_faces")
 
     def slab_set_halos(self, member, lo_in, hi_in):
         """Set the halo planes read by the next step (complex64 [ny, nx] or None)."""
+        n = self._face_sites()
+        _device_tensor(lo_in, "complex64", "slab_set_halos lo_in", n)
+        _device_tensor(hi_in, "complex64", "slab_set_halos hi_in", n)
         self._chk(self.L.lbmbt_slab_set_halos(self.h, int(member), _p(lo_in), _p(hi_in)), "slab_set_halos")
+
+    def _face_sites(self):
+        shape = getattr(self, "shape", None)
+        return None if shape is None else shape[1] * shape[2]
 
     def add_geometry(self, labels, phase_of_label, dx, bc=(0, 0, 0)):
         return self.set_geometry(labels, phase_of_label, dx, bc, add=True)
@@ -256,7 +291,9 @@ class Solver:
             self._chk(self.L.lbmbt_set_link_distances(self.h, int(index), None, 0), "set_link_distances")
             return
         on_dev = hasattr(delta, "is_cuda") and delta.is_cuda
-        if not on_dev:
+        if on_dev:
+            _device_tensor(delta, "float32", "link distances", self._sites(index, 6))
+        else:
             delta = np.ascontiguousarray(delta, np.float32)
         self._chk(self.L.lbmbt_set_link_distances(self.h, int(index), _p(delta), int(on_dev)), "set_link_distances")
 
@@ -267,9 +304,15 @@ class Solver:
             self._chk(self.L.lbmbt_set_link_angles(self.h, int(index), None, 0), "set_link_angles")
             return
         on_dev = hasattr(theta, "is_cuda") and theta.is_cuda
-        if not on_dev:
+        if on_dev:
+            _device_tensor(theta, "float32", "link angles", self._sites(index, 6))
+        else:
             theta = np.ascontiguousarray(theta, np.float32)
         self._chk(self.L.lbmbt_set_link_angles(self.h, int(index), _p(theta), int(on_dev)), "set_link_angles")
+
+    def _sites(self, index=0, per_site=1):
+        """Sites of geometry ``index`` times ``per_site``, None if unknown."""
+        return self.n_sites[index] * per_site if 0 <= index < len(self.n_sites) else None
 
     def get_mask(self, index=0, shape=None):
         n = self.n_sites[index]
@@ -315,6 +358,7 @@ class Solver:
     def run(self, field=None, series=False):
         """Plain run.  ``field``: torch complex64 CUDA tensor [N] (or None).
         Returns dict(Z, S[, series])."""
+        _device_tensor(field, "complex64", "run field", self._sites(0))
         sig = np.zeros(3)
         ser = np.zeros(2 * self.n_steps) if series else None
         self._chk(self.L.lbmbt_run(self.h, _p(sig), _p(field), _p(ser)), "run")
@@ -371,6 +415,7 @@ class Solver:
     # --- timing hooks -------------------------------------------------------
     def set_field(self, field):
         """Field buffer (torch complex64 CUDA [N] or None) for the next prepare()."""
+        _device_tensor(field, "complex64", "set_field", self._sites(0))
         self._field_keep = field
         self._chk(self.L.lbmbt_set_field(self.h, _p(field)), "set_field")
 

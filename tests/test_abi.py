@@ -82,3 +82,15 @@ def test_null_arguments_rejected():
     assert L.lbmbt_create(None, 0, None) == -1
     assert L.lbmbt_destroy(None) == 0
     assert L.lbmbt_run(None, None, None, None) == -1
+
+
+def test_device_tensor_check_rejects_host_data():
+    """Tensors the library reads or writes in place must be CUDA tensors: a
+    host tensor or a numpy array is refused before any library call, and
+    None or a raw device pointer passes through."""
+    torch = pytest.importorskip("torch")
+    for bad in (torch.zeros(4, dtype=torch.complex64), np.zeros(4, np.complex64), [0.0] * 4):
+        with pytest.raises(TypeError):
+            lbmbt._device_tensor(bad, "complex64", "field")
+    assert lbmbt._device_tensor(None, "complex64", "field") is None
+    assert lbmbt._device_tensor(12345, "complex64", "field") == 12345
