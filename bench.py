@@ -50,7 +50,17 @@ def _rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def geometry(n=N_EDGE, seed=2024):
+TISSUE_SEED = 2024
+
+
+def phase_fractions(geom):
+    """Achieved (voxelised) volume fraction of each phase of a geometry."""
+    counts = np.bincount(np.asarray(geom.phase_of_label)[geom.labels.ravel()],
+                         minlength=int(np.max(geom.phase_of_label)) + 1)
+    return [round(float(c) / geom.labels.size, 5) for c in counts]
+
+
+def geometry(n=N_EDGE, seed=TISSUE_SEED):
     from paper_1907_00908_gb300 import synth
     return synth.voronoi_tissue(n, DX, cell_diam=10.0, ecs_fraction=0.2, n_vessels=4, vessel_radius=3.0, seed=seed)
 
@@ -684,6 +694,7 @@ def main():
     t_geo = time.perf_counter()
     geom = geometry(args.n)
     t_geo = time.perf_counter() - t_geo
+    fractions = phase_fractions(geom)
     seqs = sequences()
     K_total = len(seqs[0][1])
     assert args.warmup + args.steps <= K_total
@@ -770,7 +781,8 @@ def main():
             "config": {"workload": WORKLOAD, "grid": [args.n] * 3, "dx_um": DX, "dt_ms": DT, "members": nm,
                        "bc": "mirror", "phases": 3, "kappa_um_ms": KAPPA, "b_s_mm2": B,
                        "l2": "state of 15 GB per direction, far larger than L2; no flush needed",
-                       "sites_per_step": n_sites * nm, "geometry_gen_s": round(t_geo, 1), "launch": shape},
+                       "sites_per_step": n_sites * nm, "geometry_gen_s": round(t_geo, 1), "launch": shape,
+                       "seed": TISSUE_SEED, "phase_fractions": fractions},
             "signal_after_timed_steps": [float(x) for x in sig[:, 2]],
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

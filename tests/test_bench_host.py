@@ -1,9 +1,12 @@
 """Host logic of bench.py that needs no GPU: the kernel-source hash that
 decides whether a committed DRAM-traffic capture still describes the kernel
-(comments and blank lines do not count, code does), and the traffic lookup
-that reports nothing once the hash no longer matches."""
+(comments and blank lines do not count, code does), the traffic lookup
+that reports nothing once the hash no longer matches, and the achieved phase
+fractions reported with the tissue workload."""
 import json
 import os
+
+import numpy as np
 
 import bench
 
@@ -56,3 +59,23 @@ def test_traffic_lookup_follows_the_hash(tmp_path, monkeypatch):
     assert bench.traffic_per_launch() == 120.0 * bench.N_EDGE ** 3 * 3
     (tmp_path / "paper_1907_00908_gb300" / "csrc" / "sweep_tma.cu").write_text(SRC.replace("1.f", "3.f"))
     assert bench.traffic_per_launch() is None
+
+
+def test_phase_fractions_of_a_known_geometry():
+    from paper_1907_00908_gb300 import synth
+    lab = np.zeros((2, 4, 5), np.int32)
+    lab[:, :, :2] = 1                      # label 1: 16 of 40 sites
+    lab[0, 0, 4] = 2                       # label 2: 1 site, same phase as label 0
+    g = synth.Geometry(lab, np.array([0, 1, 0], np.uint8), 0.5)
+    assert bench.phase_fractions(g) == [0.6, 0.4]
+
+
+def test_tissue_fractions_follow_the_recipe():
+    """The tissue's extracellular band (phase 1) is the 0.2 quantile of
+    d2 - d1 over all sites, and the vessel tubes (phase 2) then overwrite
+    sites regardless of the band, so the band keeps about 0.2 of what the
+    vessels leave (128^3, same recipe as the 512^3 workload)."""
+    fr = bench.phase_fractions(bench.geometry(128))
+    assert len(fr) == 3 and abs(sum(fr) - 1.0) < 1e-4, fr
+    assert abs(fr[1] - 0.2 * (1.0 - fr[2])) < 0.01, fr
+    assert 0.0 < fr[2] < 0.2 and fr[0] > 0.6, fr
