@@ -1,0 +1,66 @@
+"""The seeded synthetic geometries behind every workload: each holds the
+recipe it states.
+* Cylinders are z-aligned and non-overlapping (periodic minimum image), fill
+  their area fraction, and take gamma radii of mean 3 um.
+* Sphere packs are non-overlapping, fill their volume fraction, keep radii in
+  [rmin, rmax], and give every sphere at least one site.
+* Gradient directions are unit vectors, isotropic and seeded.
+* Crops keep the label partition and phases.
+* The tissue is reproducible from its seed."""
+import numpy as np
+
+import bench
+from paper_1907_00908_gb300 import synth
+
+
+def _min_gap(centers, radii, box):
+    d = centers[:, None, :] - centers[None, :, :]
+    d -= box * np.round(d / box)
+    gap = np.linalg.norm(d, axis=2) - (radii[:, None] + radii[None, :])
+    np.fill_diagonal(gap, np.inf)
+    return gap.min()
+
+
+def test_cylinder_pack_recipe():
+    g = synth.cylinders(128, 0.5, seed=1)
+    assert all(np.array_equal(g.labels[0], g.labels[z]) for z in range(g.labels.shape[0]))
+    c, r = np.asarray(g.info["centers"]), np.asarray(g.info["radii"])
+    assert _min_gap(c[:, :2], r, 128 * 0.5) > -1e-6
+    assert abs((g.phase_of_label[g.labels] == 1).mean() - 0.6) < 0.02
+    assert len(np.unique(g.labels)) == len(r) + 1
+    assert abs(r.mean() - 3.0) < 0.3 and 0.15 < r.std() / r.mean() < 0.45
+
+
+def test_sphere_pack_recipe():
+    g = synth.spheres(96, 0.5, rmin=2.0, rmax=6.0, fraction=0.5, seed=4)
+    c, r = np.asarray(g.info["centers"]), np.asarray(g.info["radii"])
+    assert r.min() >= 2.0 and r.max() <= 6.0
+    assert _min_gap(c, r, 96 * 0.5) > -1e-6
+    assert abs((g.phase_of_label[g.labels] == 1).mean() - 0.5) < 0.02
+    assert len(np.unique(g.labels)) == len(r) + 1
+
+
+def test_directions_are_unit_isotropic_and_seeded():
+    d = synth.directions_on_sphere(4000, seed=3)
+    assert np.abs(np.linalg.norm(d, axis=1) - 1.0).max() < 1e-12
+    assert np.linalg.norm(d.mean(0)) < 0.05
+    assert np.abs(d.T @ d / len(d) - np.eye(3) / 3).max() < 0.02
+    assert np.array_equal(synth.directions_on_sphere(8, seed=3), d[:8])
+    assert not np.array_equal(synth.directions_on_sphere(8, seed=4), d[:8])
+
+
+def test_crop_keeps_the_label_partition_and_phases():
+    g = bench.geometry(96)
+    cr = synth.crop(g, 40)
+    orig = g.labels[:40, :40, :40]
+    assert np.array_equal(cr.phase_of_label[cr.labels], g.phase_of_label[orig])
+    pairs = np.unique(np.stack([orig.ravel(), cr.labels.ravel()]), axis=1)
+    assert len(np.unique(pairs[0])) == pairs.shape[1] == len(np.unique(pairs[1]))
+    assert cr.labels.max() == pairs.shape[1] - 1
+
+
+def test_tissue_is_reproducible_from_its_seed():
+    a, b = bench.geometry(48), bench.geometry(48)
+    assert np.array_equal(a.labels, b.labels) and np.array_equal(a.phase_of_label, b.phase_of_label)
+    c = bench.geometry(48, seed=bench.TISSUE_SEED + 1)
+    assert not np.array_equal(a.labels, c.labels)
