@@ -118,18 +118,29 @@ def _p(a):
     raise TypeError(type(a))
 
 
-def _device_tensor(t, dtype, what, numel=None):
-    """Check a torch tensor that the library reads or writes in place through
-    its data pointer alone: on a CUDA device, of the expected dtype
-    (``"int32"``, ``"uint8"``, ``"float32"``, ``"complex64"``), contiguous,
-    and with at least ``numel`` elements when given.  None and raw integer
-    device pointers pass unchecked."""
+def _device_tensor(t, dtype, what, numel=None, host_ok=False):
+    """Check a buffer that the library reads or writes in place through its
+    data pointer alone: a torch CUDA tensor (with ``host_ok`` also a host
+    tensor or numpy array, for calls that accept host memory) of the
+    expected dtype (``"int32"``, ``"uint8"``, ``"float32"``,
+    ``"complex64"``), contiguous, and with at least ``numel`` elements when
+    given.  None and raw integer pointers pass unchecked."""
     if t is None or isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        if not host_ok:
+            raise TypeError(f"{what}: expected a torch CUDA tensor, got a numpy array")
+        if t.dtype != np.dtype(dtype):
+            raise TypeError(f"{what}: expected dtype {dtype}, got {t.dtype}")
+        if not t.flags.c_contiguous:
+            raise ValueError(f"{what}: the array must be C-contiguous")
+        if numel is not None and t.size < numel:
+            raise ValueError(f"{what}: {t.size} elements, at least {numel} needed")
         return t
     import torch
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{what}: expected a torch CUDA tensor, got {type(t).__name__}")
-    if not t.is_cuda:
+    if not t.is_cuda and not host_ok:
         raise TypeError(f"{what}: expected a CUDA tensor, got one on {t.device}")
     if t.dtype != getattr(torch, dtype):
         raise TypeError(f"{what}: expected dtype torch.{dtype}, got {t.dtype}")
@@ -264,17 +275,17 @@ class Solver:
         return 0
 
     def slab_faces(self, member, lo_out, hi_out):
-        """Copy the faces leaving the slab (complex64 [ny, nx] tensors or None)."""
+        """Copy the faces leaving the slab (complex64 [ny, nx], host or CUDA, or None)."""
         n = self._face_sites()
-        _device_tensor(lo_out, "complex64", "slab_faces lo_out", n)
-        _device_tensor(hi_out, "complex64", "slab_faces hi_out", n)
+        _device_tensor(lo_out, "complex64", "slab_faces lo_out", n, host_ok=True)
+        _device_tensor(hi_out, "complex64", "slab_faces hi_out", n, host_ok=True)
         self._chk(self.L.lbmbt_slab_faces(self.h, int(member), _p(lo_out), _p(hi_out)), "slab_faces")
 
     def slab_set_halos(self, member, lo_in, hi_in):
-        """Set the halo planes read by the next step (complex64 [ny, nx] or None)."""
+        """Set the halo planes read by the next step (complex64 [ny, nx], host or CUDA, or None)."""
         n = self._face_sites()
-        _device_tensor(lo_in, "complex64", "slab_set_halos lo_in", n)
-        _device_tensor(hi_in, "complex64", "slab_set_halos hi_in", n)
+        _device_tensor(lo_in, "complex64", "slab_set_halos lo_in", n, host_ok=True)
+        _device_tensor(hi_in, "complex64", "slab_set_halos hi_in", n, host_ok=True)
         self._chk(self.L.lbmbt_slab_set_halos(self.h, int(member), _p(lo_in), _p(hi_in)), "slab_set_halos")
 
     def _face_sites(self):

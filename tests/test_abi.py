@@ -94,3 +94,47 @@ def test_device_tensor_check_rejects_host_data():
             lbmbt._device_tensor(bad, "complex64", "field")
     assert lbmbt._device_tensor(None, "complex64", "field") is None
     assert lbmbt._device_tensor(12345, "complex64", "field") == 12345
+
+
+class _FakeLib:
+    """Stands in for the library: every entry point succeeds and records its call."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def fn(*args):
+            self.calls.append(name)
+            return 0
+        return fn
+
+
+def _fake_solver(shape):
+    s = object.__new__(lbmbt.Solver)
+    s.L, s.h, s.shape = _FakeLib(), 1, shape
+    s.n_sites, s.n_steps, s.n_phases = [int(np.prod(shape))], 0, 0
+    return s
+
+
+def test_buffer_checks_follow_each_call_contract():
+    """Slab faces and halos accept host or device buffers (the C calls take
+    either); a field output must be a CUDA tensor. Wrong dtype, layout or
+    size is refused before the library is called."""
+    torch = pytest.importorskip("torch")
+    s = _fake_solver((4, 3, 5))
+    s.slab_faces(0, torch.zeros(15, dtype=torch.complex64), np.zeros((3, 5), np.complex64))
+    s.slab_set_halos(0, None, torch.zeros((3, 5), dtype=torch.complex64))
+    assert s.L.calls == ["lbmbt_slab_faces", "lbmbt_slab_set_halos"]
+    for bad, err in ((torch.zeros(15, dtype=torch.float32), TypeError), (np.zeros(15, np.complex128), TypeError),
+                     (torch.zeros(14, dtype=torch.complex64), ValueError),
+                     (np.zeros((5, 3), np.complex64).T, ValueError)):
+        with pytest.raises(err):
+            s.slab_faces(0, bad, None)
+        with pytest.raises(err):
+            s.slab_set_halos(0, bad, None)
+    with pytest.raises(TypeError):
+        s.run(field=torch.zeros(60, dtype=torch.complex64))
+    with pytest.raises(TypeError):
+        s.set_field(np.zeros(60, np.complex64))
+    assert s.L.calls == ["lbmbt_slab_faces", "lbmbt_slab_set_halos"]
+    s.h = None   # nothing to destroy
