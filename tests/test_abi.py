@@ -138,3 +138,25 @@ def test_buffer_checks_follow_each_call_contract():
         s.set_field(np.zeros(60, np.complex64))
     assert s.L.calls == ["lbmbt_slab_faces", "lbmbt_slab_set_halos"]
     s.h = None   # nothing to destroy
+
+
+def test_member_struct_layout_matches_the_c_compiler(tmp_path):
+    """The binding's lbmbt_member has the size and field offsets that the C
+    compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbmbt.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(lbmbt_member), '
+                   'offsetof(lbmbt_member, gamma_G0), offsetof(lbmbt_member, geometry), '
+                   'offsetof(lbmbt_member, kappa_um_ms)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    size, o_g, o_geo, o_k = map(int, subprocess.run([str(exe)], check=True, capture_output=True,
+                                                     text=True).stdout.split())
+    M = lbmbt.Member
+    assert ctypes.sizeof(M) == size
+    assert (M.gamma_G0.offset, M.geometry.offset, M.kappa_um_ms.offset) == (o_g, o_geo, o_k)
