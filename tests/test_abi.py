@@ -160,3 +160,18 @@ def test_member_struct_layout_matches_the_c_compiler(tmp_path):
     M = lbmbt.Member
     assert ctypes.sizeof(M) == size
     assert (M.gamma_G0.offset, M.geometry.offset, M.kappa_um_ms.offset) == (o_g, o_geo, o_k)
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every entry point's ctypes signature has as many arguments as its
+    prototype in the header (a miscount would shift every later argument)."""
+    txt = open(os.path.join(ROOT, "include", "lbmbt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = dict(re.findall(r"\b(lbmbt_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt))
+    L = lbmbt.lib()
+    assert set(protos) == set(lbmbt.EXPORTS)
+    for name, params in protos.items():
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        argtypes = getattr(L, name).argtypes
+        assert argtypes is not None and len(argtypes) == n, (name, n, argtypes)
