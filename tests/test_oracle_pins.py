@@ -139,6 +139,38 @@ def test_oracle_matches_brute_force_operator(case):
     np.testing.assert_allclose(o["state"], ref, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("seed", range(24))
+def test_oracle_matches_brute_force_operator_on_random_grids(seed):
+    """The same comparison on seeded random tiny grids.
+    * Axes of 1 to 4 nodes, each face periodic or mirror.
+    * 1 to 3 labels with random phases, so membranes fall anywhere, including
+      across a wrap.
+    * kappa of 0, finite or infinite.
+    * Arbitrary waveform values.
+    * A gradient drawn as the mirror rule (Sec. 2.4.4) allows: either along
+      one mirror normal, or anywhere in the periodic axes."""
+    rng = np.random.default_rng(1000 + seed)
+    shape = tuple(int(v) for v in rng.integers(1, 5, size=3))
+    n_lab = int(rng.integers(1, 4)) if seed % 4 == 0 else int(rng.integers(2, 4))
+    lab = rng.integers(0, n_lab, size=shape).astype(np.int32)
+    pol = rng.integers(0, 2, size=n_lab).astype(np.uint8)
+    bc = [int(v) for v in rng.integers(0, 2, size=3)]
+    mirror = [a for a in range(3) if bc[a] == 1]
+    if mirror and rng.random() < 0.5:
+        gG = np.zeros(3)
+        gG[int(rng.choice(mirror))] = rng.uniform(-0.4, 0.4)
+    else:
+        gG = rng.uniform(-0.4, 0.4, size=3)
+        gG[mirror] = 0.0
+    kappa = [0.0, float(rng.uniform(0.05, 1.0)), INF][int(rng.integers(0, 3))]
+    D, T2 = list(rng.uniform(0.3, 2.0, size=2)), [float(rng.uniform(5.0, 50.0)), INF]
+    f = np.round(rng.uniform(-1.5, 1.5, size=int(rng.integers(4, 11))), 2)
+    f[rng.random(f.size) < 0.2] = 0.0
+    o = oracle.run(lab, 0.8, pol, bc, D, T2, kappa, 0.1, f, gG, want_state=True)
+    ref = refs.brute_state(lab, 0.8, pol, bc, D, T2, kappa, 0.1, f, gG)
+    np.testing.assert_allclose(o["state"], ref, rtol=0, atol=1e-13)
+
+
 # ------------------------------------------------------------- invariants
 @pytest.mark.parametrize("bc", [[0, 0, 0], [1, 1, 1], [1, 0, 1]])
 @pytest.mark.parametrize("kappa", [0.0, 0.03, INF])
