@@ -81,20 +81,25 @@ def _site(x, y, z, nx, ny):
     return (z * ny + y) * nx + x
 
 
-def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG):
-    """Final state g_i(x) [nz, ny, nx, 7] from operator matrices (tiny grids).
+def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice="D3Q7"):
+    """Final state g_i(x) [nz, ny, nx, Q] from operator matrices (tiny grids).
 
     Each step: collision block per site; a link map that routes every arriving
     population from its source (neighbour, periodic image with its phase
     factor, or the mirror image) and mixes in the membrane shares; a diagonal
     reaction.  Real-linear maps are kept as (A, B): v -> A v + B conj(v).
+    lattice "D3Q7" (Q = 7) or "D2Q5" (Q = 5, one z plane, eps_D = 1/3).
     """
     labels = np.asarray(labels)
     nz, ny, nx = labels.shape
     dims = (nx, ny, nz)
     N = labels.size
-    Q = 7
-    opp = [0, 2, 1, 4, 3, 6, 5]
+    if lattice == "D2Q5":
+        assert nz == 1
+        Q, vel, wts, eps = 5, E2, WTS2, EPS2
+    else:
+        Q, vel, wts, eps = 7, E, WTS, EPS
+    opp = [0, 2, 1, 4, 3, 6, 5][:Q]
     ph = np.asarray(phase_of_label)[labels].ravel()
     Dv = np.atleast_1d(D)
     T2v = np.atleast_1d(T2)
@@ -103,7 +108,7 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG):
     elif math.isinf(kappa):
         r, s = 0.0, 1.0
     else:
-        P = EPS * dx / (2 * kappa * dt)
+        P = eps * dx / (2 * kappa * dt)
         r, s = P / (1 + P), 1 / (1 + P)
     gG = np.asarray(gG, float)
     conj_axis = [bc[a] == 1 and gG[a] != 0 for a in range(3)]
@@ -111,12 +116,12 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG):
     # collision matrix (real coefficients)
     C = np.zeros((N * Q, N * Q))
     for x in range(N):
-        om = 1.0 / tau(Dv[ph[x]], dt, dx)
-        blk = (1 - om) * np.eye(Q) + om * np.outer(WTS, np.ones(Q))
+        om = 1.0 / tau(Dv[ph[x]], dt, dx, eps)
+        blk = (1 - om) * np.eye(Q) + om * np.outer(wts, np.ones(Q))
         C[x * Q:(x + 1) * Q, x * Q:(x + 1) * Q] = blk
 
     lab = labels.ravel()
-    g = np.tile(WTS.astype(complex), N)
+    g = np.tile(wts.astype(complex), N)
     F = 0.0
     for fk in f:
         A = np.zeros((N * Q, N * Q), complex)
@@ -127,7 +132,7 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG):
                     t = _site(x, y, z, nx, ny)
                     A[t * Q, t * Q] = 1.0
                     for i in range(1, Q):
-                        src = [x - E[i][0], y - E[i][1], z - E[i][2]]
+                        src = [x - vel[i][0], y - vel[i][1], z - vel[i][2]]
                         fac, mirror, mconj = 1.0 + 0j, False, 0j
                         for a in range(3):
                             if src[a] < 0 or src[a] >= dims[a]:

@@ -2,8 +2,9 @@
 eps_D = 1/3, omega_0 = 1/3, omega_1..4 = 1/6): the plane-wave closed form of
 the five-velocity scheme, convergence of free diffusion to exp(-b D) (which
 fails for a wrong eps_D), conservation of the summed magnetisation with
-membranes, and restricted diffusion between impermeable planes converging to
-the continuum Neumann-mode propagator."""
+membranes, restricted diffusion between impermeable planes converging to
+the continuum Neumann-mode propagator, and equality with the five-velocity
+operator assembled link by link on random tiny grids."""
 import math
 
 import numpy as np
@@ -76,3 +77,34 @@ def test_d2q5_needs_one_plane():
     with pytest.raises(ValueError):
         oracle.run(np.zeros((2, 4, 4), np.int32), 1.0, np.zeros(1, np.uint8), (0, 0, 0), [1.0], [INF], INF, 0.05,
                    np.zeros(3), [0, 0, 0], lattice="D2Q5")
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_d2q5_matches_brute_force_operator_on_random_grids(seed):
+    """The oracle's D2Q5 mode equals the five-velocity operator assembled
+    link by link (refs.brute_state with lattice="D2Q5") on seeded random
+    one-plane grids, to 1e-13. The grids have 1 to 5 nodes per in-plane axis,
+    periodic or mirror faces, random labels and phases, and kappa of 0,
+    finite or infinite. Gradients lie in the plane as the mirror rule
+    allows. The oracle's z slots stay exactly zero."""
+    rng = np.random.default_rng(2000 + seed)
+    shape = (1,) + tuple(int(v) for v in rng.integers(1, 6, size=2))
+    n_lab = int(rng.integers(2, 4))
+    lab = rng.integers(0, n_lab, size=shape).astype(np.int32)
+    pol = rng.integers(0, 2, size=n_lab).astype(np.uint8)
+    bc = [int(v) for v in rng.integers(0, 2, size=3)]
+    mirror = [a for a in range(2) if bc[a] == 1]
+    gG = np.zeros(3)
+    if mirror and rng.random() < 0.5:
+        gG[int(rng.choice(mirror))] = rng.uniform(-0.4, 0.4)
+    else:
+        gG[:2] = rng.uniform(-0.4, 0.4, size=2)
+        gG[mirror] = 0.0
+    kappa = [0.0, float(rng.uniform(0.05, 1.0)), INF][int(rng.integers(0, 3))]
+    D, T2 = list(rng.uniform(0.3, 2.0, size=2)), [float(rng.uniform(5.0, 50.0)), INF]
+    f = np.round(rng.uniform(-1.5, 1.5, size=int(rng.integers(4, 11))), 2)
+    f[rng.random(f.size) < 0.2] = 0.0
+    o = oracle.run(lab, 0.8, pol, bc, D, T2, kappa, 0.1, f, gG, want_state=True, lattice="D2Q5")
+    ref = refs.brute_state(lab, 0.8, pol, bc, D, T2, kappa, 0.1, f, gG, lattice="D2Q5")
+    np.testing.assert_allclose(o["state"][..., :5], ref, rtol=0, atol=1e-13)
+    assert not np.any(o["state"][..., 5:])
