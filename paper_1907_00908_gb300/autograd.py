@@ -11,20 +11,32 @@ from __future__ import annotations
 import torch
 
 
+def _like(x):
+    """(device, dtype) a gradient for input x must have."""
+    return (x.device, x.dtype) if isinstance(x, torch.Tensor) else (None, None)
+
+
 class SignalFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, D, T2, kappa, solver, checkpoint_every):
-        solver.set_phases(D.detach().double().cpu().numpy(), T2.detach().double().cpu().numpy())
+        as_np = lambda x: torch.as_tensor(x).detach().double().cpu().numpy()
+        solver.set_phases(as_np(D), as_np(T2))
         solver.set_permeability(float(kappa))
         g = solver.grad(checkpoint_every)
-        ctx.save_for_backward(torch.as_tensor(g["dD"]), torch.as_tensor(g["dT2"]),
+        ctx.save_for_backward(torch.as_tensor(g["dD"], dtype=torch.float64),
+                              torch.as_tensor(g["dT2"], dtype=torch.float64),
                               torch.as_tensor(g["dkappa"], dtype=torch.float64))
+        ctx.like = (_like(D), _like(T2), _like(kappa))
         return torch.as_tensor(g["S"], dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, gout):
-        dD, dT2, dk = ctx.saved_tensors
-        return gout * dD, gout * dT2, gout * dk, None, None
+        # each gradient on its input's device and in its dtype; none for an
+        # input that needs none (a plain number, or requires_grad False)
+        out = []
+        for need, d, (dev, dt) in zip(ctx.needs_input_grad[:3], ctx.saved_tensors, ctx.like):
+            out.append((gout.to(torch.float64).cpu() * d).to(device=dev, dtype=dt) if need else None)
+        return out[0], out[1], out[2], None, None
 
 
 def signal(solver, D, T2, kappa, checkpoint_every=64):
