@@ -313,6 +313,11 @@ def test_error_codes(lb):
         rc = lb.lib().lbmbt_set_geometry(s.h, dims[0], dims[1], dims[2], 1.0, lb._p(tiny), 0, 1, lb._p(pol),
                                          lb._p(bcv))
         assert rc == -1, dims
+    # an empty sequence and a non-finite waveform sample are refused (host checks)
+    for f_bad in (np.zeros(0), np.array([1.0, math.nan])):
+        with pytest.raises(lb.LbmbtError) as e:
+            s.set_sequence(0.05, f_bad, [0.1, 0, 0])
+        assert e.value.code == -1
     s.close()
 
 
