@@ -6,7 +6,9 @@ recipe it states.
   [rmin, rmax], and give every sphere at least one site.
 * Gradient directions are unit vectors, isotropic and seeded.
 * Crops keep the label partition and phases.
-* The tissue is reproducible from its seed."""
+* The tissue is reproducible from its seed.
+* The exact membrane positions on the links of sphere and cylinder packs lie
+  on the bodies' surfaces and agree from both ends of a link."""
 import numpy as np
 
 import bench
@@ -64,3 +66,46 @@ def test_tissue_is_reproducible_from_its_seed():
     assert np.array_equal(a.labels, b.labels) and np.array_equal(a.phase_of_label, b.phase_of_label)
     c = bench.geometry(48, seed=bench.TISSUE_SEED + 1)
     assert not np.array_equal(a.labels, c.labels)
+
+
+_DIRS = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+
+
+def _check_link_positions(g, ndim):
+    """Every membrane position from synth.link_distances lies on the surface
+    of the body its link crosses. The tolerance is the documented clip to
+    [1e-4, 1 - 1e-4] of a link. Both ends of a link see the same cut:
+    Delta_j(s) + Delta_jbar(s + e_j) = 1 exactly."""
+    lab, dx = g.labels, g.dx
+    nz, ny, nx = lab.shape
+    dl = synth.link_distances(g, (0, 0, 0))
+    cen, rad = np.asarray(g.info["centers"]), np.asarray(g.info["radii"])
+    box = np.array([nx, ny, nz]) * dx
+    n = 0
+    for j, e in enumerate(_DIRS):
+        a = j // 2
+        nb = np.roll(lab, -e[a], axis=2 - a)
+        idx = np.nonzero(nb != lab)
+        if len(idx[0]) == 0:
+            continue
+        la, lb = lab[idx], nb[idx]
+        k = np.where((la > 0) & (lb > 0), np.minimum(la, lb), np.where(la > 0, la, lb)) - 1
+        p = np.stack([idx[2], idx[1], idx[0]], 1) * dx + dl[j][idx][:, None] * dx * np.array(e)
+        c = np.zeros((len(k), 3))
+        c[:, :ndim] = cen[k][:, :ndim]
+        dv = p - c
+        dv[:, ndim:] = 0.0
+        dv -= box * np.round(dv / box)
+        assert np.abs(np.linalg.norm(dv, axis=1) - rad[k]).max() <= 1e-4 * dx + 1e-6, j
+        jb = j + 1 if j % 2 == 0 else j - 1
+        assert np.array_equal(dl[j][idx] + np.roll(dl[jb], -e[a], axis=2 - a)[idx], np.ones(len(k), np.float32))
+        n += len(k)
+    assert n > 1000
+
+
+def test_sphere_link_positions_lie_on_the_spheres():
+    _check_link_positions(synth.spheres(48, 0.5, rmin=2.0, rmax=6.0, fraction=0.5, seed=4), 3)
+
+
+def test_cylinder_link_positions_lie_on_the_cylinders():
+    _check_link_positions(synth.cylinders(64, 0.5, seed=1), 2)
