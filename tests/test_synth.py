@@ -109,3 +109,24 @@ def test_sphere_link_positions_lie_on_the_spheres():
 
 def test_cylinder_link_positions_lie_on_the_cylinders():
     _check_link_positions(synth.cylinders(64, 0.5, seed=1), 2)
+
+
+def test_disc_link_angles_are_consistent_and_mirror_antisymmetric():
+    """synth.link_angles on a disc whose centre lies on a node row. The two
+    ends of a link carry opposite angles. Reflecting y about that row maps
+    the disc onto itself: the x links' angles change sign, and the +y and -y
+    links swap with equal angles (the normal's y part flips while e_j does
+    too)."""
+    n, dx = 40, 0.5
+    c = (n // 2) * dx
+    g = synth.disks(n, dx, [[c + 0.137, c]], [6.3])
+    th = synth.link_angles(g, (0, 0, 0))[:, 0]
+    assert np.count_nonzero(th) > 100 and not np.any(th[4:])
+    for j, (ex, ey) in enumerate([(1, 0), (-1, 0), (0, 1), (0, -1)]):
+        jb = j + 1 if j % 2 == 0 else j - 1
+        far = np.roll(np.roll(th[jb], -ey, axis=0), -ex, axis=1)
+        assert np.array_equal(th[j], -far), j
+    refl = lambda a: np.roll(a[::-1], 1, axis=0)
+    assert np.array_equal(refl(g.labels[0]), g.labels[0])
+    assert np.array_equal(refl(th[0]), -th[0]) and np.array_equal(refl(th[1]), -th[1])
+    assert np.array_equal(refl(th[2]), th[3]) and np.array_equal(refl(th[3]), th[2])
