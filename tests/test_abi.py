@@ -175,3 +175,18 @@ def test_binding_signatures_match_the_header_prototypes():
         n = 0 if params in ("", "void") else params.count(",") + 1
         argtypes = getattr(L, name).argtypes
         assert argtypes is not None and len(argtypes) == n, (name, n, argtypes)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++11")])
+def test_header_compiles_cleanly_as_c_and_cxx(tmp_path, lang, std):
+    """include/lbmbt.h is a plain C ABI: it compiles on its own, warning-free
+    under -Wall -Wextra -Wpedantic, as C99 and as C++11."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no compiler")
+    src = tmp_path / ("h.c" if lang == "c" else "h.cpp")
+    src.write_text('#include "lbmbt.h"\nint main(void) { return 0; }\n')
+    subprocess.run([cc, std, "-Wall", "-Wextra", "-Wpedantic", "-Werror", "-fsyntax-only",
+                    "-I", os.path.join(ROOT, "include"), str(src)], check=True)
