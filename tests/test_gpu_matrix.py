@@ -13,7 +13,6 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1907_00908_gb300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
