@@ -349,16 +349,21 @@ int lbmbt_launch_count(lbmbt_ctx* ctx, int64_t* count_out);
  *              call performs steps k0 .. k0 + n_steps - 1 of it;
  *   signal_out[3] (host) = {Re Z, Im Z, |Z|/N} at the end of the last step.
  * Its working data (descriptor, step word, waveform tables, per-tile signal
- * partials) lives in one fixed file-scope device array of 1.25 MiB that every
- * GPU which loads the library holds until the process exits.  Limits:
- * N <= 16,777,216 sites and n_total_steps <= 32,768; larger inputs are
- * rejected with LBMBT_EINVAL and a message in errbuf (errbuf may be NULL).
+ * partials) lives in one fixed file-scope device array of 1,181,184 bytes
+ * (1.13 MiB) that every GPU which loads the library holds until the process
+ * exits.  Limits: N <= 16,777,216 sites and n_total_steps <= 32,768; larger
+ * inputs are rejected with LBMBT_EINVAL and a message in errbuf (errbuf may
+ * be NULL).  Every phase id in the mask (bits 6-7) must be < n_phases, else
+ * LBMBT_ESTATE before the state is touched.  The library cannot see the
+ * sizes of the caller's buffers: they must hold what is stated above.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call outside any stream capture.  All calls share
- * the one array: calls that overlap on the GPU (different streams or host
- * threads without ordering) race and give wrong results.  Work is issued on
- * cuda_stream (NULL = legacy default stream) and the call returns after it
- * finished.
+ * device, cached for the life of the process, so it is stale after a
+ * cudaDeviceReset); make that first call before any stream capture.  Every
+ * call copies the waveform from host memory and waits for its stream.  All
+ * calls share the one array and every call overwrites what it needs of it:
+ * calls that overlap on the GPU (different streams or host threads without
+ * ordering) race and give wrong results.  Work is issued on cuda_stream
+ * (NULL = legacy default stream) and the call returns after it finished.
  */
 int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const uint8_t* mask_dev, const int bc[3],
                         int n_phases, const double* D_um2_ms, const double* T2_ms, double kappa_um_ms,

@@ -12,6 +12,7 @@
 // library holds until the process exits.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -34,6 +35,7 @@ constexpr size_t OFF_CTL = 0;
 constexpr size_t OFF_DESC = 256;
 constexpr size_t OFF_TS = 768;
 constexpr size_t OFF_Z = 1024;
+constexpr size_t OFF_PH = 1056;                      // largest phase id in the caller's mask
 constexpr size_t OFF_FAC = 1088;                     // [2][1][6] boundary factors
 constexpr size_t OFF_F64 = 1280;
 constexpr size_t OFF_F32 = OFF_F64 + NA_MAX_STEPS * sizeof(double);
@@ -43,7 +45,8 @@ constexpr size_t NA_SCRATCH_BYTES = OFF_PART + NA_MAX_TILES * sizeof(double2);
 static_assert(sizeof(StepCtl) <= OFF_DESC - OFF_CTL, "control word does not fit");
 static_assert(sizeof(MemberDesc) <= OFF_TS - OFF_DESC, "descriptor does not fit");
 static_assert(OFF_FAC + 12 * sizeof(float2) <= OFF_F64, "factors do not fit");
-static_assert(NA_SCRATCH_BYTES <= (1u << 21), "scratch larger than stated");
+// 1,181,184 bytes (1.13 MiB), the figure the header states
+static_assert(NA_SCRATCH_BYTES == 1181184, "scratch size differs from the documented figure");
 
 // The scratch.  Host code must not pass `na_scratch` itself to a kernel: on
 // the host it names a stand-in object, not device memory.  Its device address
@@ -63,6 +66,7 @@ __global__ void na_setup_kernel(unsigned char* base, MemberDesc d, long long n_t
     ts[1] = n_tiles;
     // waveform tables from the caller's samples (copied to OFF_F64):
     // f_k as float and F_k = sum_{m<k} f_m dt in FP64, summed in order
+    *reinterpret_cast<int*>(base + OFF_PH) = 0;   // cleared every call
     const double* f64 = reinterpret_cast<const double*>(base + OFF_F64);
     float* f32 = reinterpret_cast<float*>(base + OFF_F32);
     double* F = reinterpret_cast<double*>(base + OFF_FCUM);
@@ -73,6 +77,16 @@ __global__ void na_setup_kernel(unsigned char* base, MemberDesc d, long long n_t
         acc += f64[k] * dt;
     }
     F[K] = acc;
+}
+
+// Largest phase id (mask bits 6..7) over the caller's mask.
+__global__ void na_phase_kernel(const uint8_t* __restrict__ mask, long long N, int* out)
+{
+    unsigned mx = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N; s += (long long)gridDim.x * blockDim.x)
+        mx = max(mx, (unsigned)(mask[s] >> 6));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, (int)mx);
 }
 
 int na_fail(char* errbuf, size_t errlen, int code, const char* msg)
@@ -200,6 +214,22 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     if (e == cudaSuccess) {
         na_setup_kernel<<<1, 1, 0, st>>>(base, d, n_tiles, (int)n_total_steps, dt_ms);
         e = cudaGetLastError();
+    }
+    // every phase id in the mask must name one of the n_phases phases given;
+    // checked before any state is touched
+    int max_ph = 0;
+    if (e == cudaSuccess) {
+        const long long blocks = std::min<long long>((N + 255) / 256, 152LL * 8);
+        na_phase_kernel<<<(unsigned)blocks, 256, 0, st>>>(mask_dev, N, reinterpret_cast<int*>(base + OFF_PH));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&max_ph, base + OFF_PH, sizeof max_ph, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return na_fail(errbuf, errlen, LBMBT_ECUDA, cudaGetErrorString(e));
+    if (max_ph >= n_phases) {
+        char m[128];
+        snprintf(m, sizeof m, "the mask uses phase %d but %d phases are given", max_ph, n_phases);
+        return na_fail(errbuf, errlen, LBMBT_ESTATE, m);
     }
     SweepArgs a;
     a.members = reinterpret_cast<const MemberDesc*>(base + OFF_DESC);

@@ -172,8 +172,23 @@ def sweep_noalloc(mask_dev, shape, dx, bc, D, T2, kappa, dt, f, gG, state_dev, k
     inside the library.  Returns {Z, S} after step k0 + n_steps."""
     L = lib()
     nz, ny, nx = shape
-    _device_tensor(mask_dev, "uint8", "sweep_noalloc mask")          # sizes: the caller's, checked by the
-    _device_tensor(state_dev, "complex64", "sweep_noalloc state")    # library against its limits only
+    # the library cannot see the buffers' sizes: check them here against the
+    # shape (mask N bytes, state 2 x 7 x plane complex64, plane = N rounded
+    # up to 64), before anything is launched, and that both are on the
+    # current device
+    N = int(nx) * int(ny) * int(nz)
+    plane = (N + 63) // 64 * 64
+    for t, need, what in ((mask_dev, N, "mask"), (state_dev, 2 * 7 * plane, "state")):
+        if hasattr(t, "numel") and t.numel() < need:
+            raise ValueError(f"sweep_noalloc {what}: {t.numel()} elements, at least {need} needed for shape "
+                             f"{tuple(shape)}")
+    _device_tensor(mask_dev, "uint8", "sweep_noalloc mask", numel=N)
+    _device_tensor(state_dev, "complex64", "sweep_noalloc state", numel=2 * 7 * plane)
+    import torch
+    cur = torch.cuda.current_device()
+    for t, what in ((mask_dev, "mask"), (state_dev, "state")):
+        if t.device.index != cur:
+            raise ValueError(f"sweep_noalloc {what}: on {t.device}, but the current device is cuda:{cur}")
     bcv = np.ascontiguousarray(bc, np.int32)
     Dv = np.ascontiguousarray(np.atleast_1d(D), np.float64)
     T2v = np.ascontiguousarray(np.atleast_1d(T2), np.float64)

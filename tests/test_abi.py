@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every entry point
 declared in include/lbmbt.h, and its host-only helpers agree with the oracle."""
 import ctypes
+import math
 import os
 import re
 
@@ -138,6 +139,28 @@ def test_buffer_checks_follow_each_call_contract():
         s.set_field(np.zeros(60, np.complex64))
     assert s.L.calls == ["lbmbt_slab_faces", "lbmbt_slab_set_halos"]
     s.h = None   # nothing to destroy
+
+
+def test_noalloc_buffers_are_checked_before_any_launch(monkeypatch):
+    """lbmbt_sweep_noalloc cannot see the sizes of the caller's buffers, so
+    the binding checks them against the shape first: an undersized state
+    (2 x 7 x plane complex64, plane = N rounded up to 64) or mask (N bytes)
+    raises before the library is called; right-sized host tensors are then
+    refused as not being on the GPU, again before any call."""
+    torch = pytest.importorskip("torch")
+    fake = _FakeLib()
+    monkeypatch.setattr(lbmbt, "lib", lambda: fake)
+    shape = (3, 4, 5)   # N = 60, plane = 64
+    args = ((3, 4, 5), 0.5, (0, 0, 0), [2.0], [math.inf], math.inf, 0.01, np.zeros(4), [0.0, 0.0, 0.0])
+    ok_mask, ok_state = torch.zeros(60, dtype=torch.uint8), torch.zeros(2 * 7 * 64, dtype=torch.complex64)
+    for mask, state in ((ok_mask, torch.zeros(2 * 7 * 64 - 1, dtype=torch.complex64)),
+                        (ok_mask, torch.zeros(2 * 7 * 60, dtype=torch.complex64)),
+                        (torch.zeros(59, dtype=torch.uint8), ok_state)):
+        with pytest.raises(ValueError):
+            lbmbt.sweep_noalloc(mask, args[0], *args[1:-1], args[-1], state)
+    with pytest.raises(TypeError):
+        lbmbt.sweep_noalloc(ok_mask, shape, *args[1:-1], args[-1], ok_state)
+    assert fake.calls == []
 
 
 def test_member_struct_layout_matches_the_c_compiler(tmp_path):

@@ -1,5 +1,10 @@
 """GPU adjoint sweep: dS/d(D_p, T2_p, kappa) against central finite
-differences (h = 1e-3 relative) of the FP64 oracle and of the GPU forward."""
+differences (h = 1e-3 relative) of the FP64 oracle and of the GPU forward.
+
+Tolerance against the oracle's differences: 1e-4 of the largest
+log-parameter gradient component (theta dS/dtheta).  The differences' own
+truncation error is O(h^2) ~ 1e-6 of that scale; the rest is the FP32
+forward and adjoint arithmetic."""
 import math
 
 import numpy as np
@@ -12,6 +17,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 INF = math.inf
 H = 1e-3
+ADJ_TOL = 1e-4   # of the largest log-parameter gradient component
 
 
 @pytest.fixture(scope="module")
@@ -95,7 +101,7 @@ def test_adjoint_matches_oracle_finite_differences(lb, name):
     b = _logvec(fd, c["D"], c["T2"], c["kap"])
     err = np.abs(a - b).max() / np.abs(b).max()
     print(name, "adjoint", a, "fd", b, "err", err)
-    assert err < 1e-3
+    assert err < ADJ_TOL
     assert abs(g["S"] - S(c["D"], c["T2"], c["kap"])) < 1e-5 * g["S"]
 
 
@@ -216,7 +222,8 @@ def test_adjoint_d2q5_matches_oracle_finite_differences(lb, bc, d):
     fd = _fd(S, D, T2, kap)
     a, b = _logvec(g, D, T2, kap), _logvec(fd, D, T2, kap)
     err = np.abs(a - b).max() / np.abs(b).max()
-    assert err < 1e-3, (a, b, err)
+    print("d2q5", bc, d, "adjoint", a, "fd", b, "err", err)
+    assert err < ADJ_TOL, (a, b, err)
     assert abs(g["S"] - S(D, T2, kap)) < 1e-5 * g["S"]
 
 
