@@ -16,6 +16,9 @@ arXiv 1907.00908:
                    streaming_LBM, reaction_LBM, permeability_BC/B5,
                    collision_BC (modified periodic) and Sec. 2.4.4 (mirror).
 * ``mask``      -- half-link membrane links on label changes (Sec. 2.4.2).
+* ``run(..., scheme="classical")`` -- the paper's comparison scheme, the
+                   classical LBM with the reaction as a collision source
+                   (Appendix A, Eqs. A2 and A12).
 * ``link_coefficients`` / ``angled_coefficients`` -- the membrane rule with
                    positions (Eqs. B4a-B4c) and its general-angle form
                    (Appendix B, Eqs. B2a, phi_1, phi_2, B1, B1.5).
@@ -75,6 +78,8 @@ def _load():
                 ctypes.c_double, ctypes.c_double, ctypes.c_long, P, P, ctypes.c_int, P, P, ctypes.c_int,
                 ctypes.c_int, P, P, P, P]
             lib.lbm_oracle_run_ex.restype = ctypes.c_int
+            lib.lbm_oracle_run_scheme.argtypes = lib.lbm_oracle_run_ex.argtypes[:21] + [ctypes.c_int] + [P] * 4
+            lib.lbm_oracle_run_scheme.restype = ctypes.c_int
             lib.lbm_oracle_angled_coefficients.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, P, P, P, P]
             lib.lbm_oracle_angled_coefficients.restype = None
             lib.lbm_oracle_link_coefficients.argtypes = [ctypes.c_double] * 4 + [P, P]
@@ -162,7 +167,7 @@ def mask(labels, phase_of_label, bc):
 
 def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
         want_field=False, want_series=False, want_state=False, threads=0, delta=None, substeps=1,
-        lattice="D3Q7", theta=None):
+        lattice="D3Q7", theta=None, scheme="hybrid"):
     """Run the scheme from M = 1 to t = len(f)*dt.
 
     ``labels``: int32 [nz, ny, nx] compartment ids; ``phase_of_label``: phase
@@ -179,6 +184,11 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
     ``theta`` (D2Q5, with ``delta``): [6, 1, ny, nx] signed angles between the
     membrane normal and each link (see ``angled_arrival`` in the C source),
     which selects the general-angle rule of Appendix B.
+    ``scheme`` = "classical": the classical LBM of Appendix A (Eq. A12), the
+    reaction as the collision source dt omega_i R M with R = -i gamma x.G0
+    f(t^k) - 1/T2 and no reaction step (``substeps`` must be 1); the outer
+    faces then take F_(k+1), the phase the source has already given the
+    streamed populations.
     """
     labels = np.ascontiguousarray(labels, dtype=np.int32)
     nz, ny, nx = labels.shape
@@ -200,7 +210,19 @@ def run(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG,
         raise ValueError("lattice must be D3Q7 or D2Q5")
     if theta is not None and (delta is None or lattice != "D2Q5"):
         raise ValueError("membrane angles need positions and the D2Q5 lattice")
-    if substeps != 1 or lattice == "D2Q5":
+    if scheme not in ("hybrid", "classical"):
+        raise ValueError("scheme must be hybrid or classical")
+    if scheme == "classical":
+        if substeps != 1:
+            raise ValueError("the classical scheme has no reaction step to sub-step")
+        dl = None if delta is None else np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(6, N).T)
+        th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(6, N).T)
+        rc = _load().lbm_oracle_run_scheme(
+            nx, ny, nz, float(dx), _ptr(labels), int(pol.size), _ptr(pol), _ptr(bcv),
+            int(Dv.size), _ptr(Dv), _ptr(T2v), float(kappa), float(dt), K, _ptr(fv), _ptr(gv),
+            int(threads), _ptr(dl), _ptr(th), 1, int(lattice == "D2Q5"), 1, _ptr(Z), _ptr(field),
+            _ptr(series), _ptr(state))
+    elif substeps != 1 or lattice == "D2Q5":
         dl = None if delta is None else np.ascontiguousarray(np.asarray(delta, dtype=np.float64).reshape(6, N).T)
         th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(6, N).T)
         rc = _load().lbm_oracle_run_ex(

@@ -11,6 +11,11 @@
  * (Eq. LBM_process_list_2): collision -> boundary/buffer layers -> streaming
  * (with the half-link membrane rule) -> reaction.
  *
+ * The paper's comparison scheme, the classical LBM with the reaction as a
+ * source term in the collision (Appendix A, Eq. A12), is the same loop with
+ * the source added in the collision and no reaction step
+ * (lbm_oracle_run_scheme).
+ *
  * Lattice: D3Q7, directions 0=(0,0,0), 1=+x, 2=-x, 3=+y, 4=-y, 5=+z, 6=-z.
  * Weights: the paper gives D2Q5 only (Sec. 2.3: omega_0 = eps_D, omega_i =
  * eps_D/2, eps_D = 1/3).  For D3Q7 the same pattern with the isotropy
@@ -395,9 +400,11 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     const int* bc, int n_phases, const double* D, const double* T2,
                     double kappa, double dt, long n_steps, const double* f,
                     const double* gG, int n_threads, const double* delta, const double* theta, int substeps,
-                    int d2q5, double* Z_out, double* field_out, double* series_out, double* state_out)
+                    int d2q5, int classical, double* Z_out, double* field_out, double* series_out,
+                    double* state_out)
 {
     if (nx < 1 || ny < 1 || nz < 1 || dx <= 0 || dt <= 0 || n_steps < 0 || substeps < 1) return -1;
+    if (classical && substeps != 1) return -1;   /* no reaction split to sub-step */
     if (d2q5 && nz != 1) return -1;
     if (theta && (!delta || !d2q5)) return -1;   /* the angle rule is the paper's 2-D one */
     const int nq = d2q5 ? 5 : Q;                  /* populations in use */
@@ -491,7 +498,9 @@ static int run_impl(int nx, int ny, int nz, double dx,
 
     double F = 0.0; /* F_k = sum_{m<k} f_m dt */
     for (long k = 0; k < n_steps; ++k) {
-        /* 1. Collision (Eq. collision_LBM), M = sum_i g_i (Eq. M'summation). */
+        /* 1. Collision (Eq. collision_LBM), M = sum_i g_i (Eq. M'summation).
+         *    Classical scheme (Eq. A12): plus the source dt omega_i R M with
+         *    R = -i gamma x.G0 f(t^k) - 1/T2 (Eq. A2), x = n dx. */
 #pragma omp parallel for
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
@@ -500,23 +509,35 @@ static int run_impl(int nx, int ny, int nz, double dx,
                     cplx M = 0;
                     for (int i = 0; i < nq; ++i) M += gs[si * Q + i];
                     double t = tau[ph[si]];
+                    cplx R = 0;
+                    if (classical) {
+                        double xdotG = (x * dx) * gG[0] + (y * dx) * gG[1] + (z * dx) * gG[2];
+                        R = -I * xdotG * f[k] - 1.0 / T2[ph[si]];   /* T2 = inf -> 0 */
+                    }
                     for (int i = 0; i < nq; ++i) {
                         cplx gi = gs[si * Q + i];
                         gh[pi * Q + i] = gi - (gi - w[i] * M) / t;
+                        if (classical) gh[pi * Q + i] += dt * w[i] * R * M;
                     }
                 }
+
+        /* Phase of the outer faces for this step's streaming.  Hybrid: the
+         * streamed populations precede this step's reaction, F_k.  Classical:
+         * the source of step k is already in them (they stand for t^(k+1)),
+         * so F_(k+1) = F_k + f_k dt. */
+        const double Fb = classical ? F + f[k] * dt : F;
 
         /* 2. Buffer layers (Sec. 2.4.3 Eq. collision_BC; Sec. 2.4.4). */
         for (int a = 0; a < 3; ++a) {
             int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
             double L = dims[a] * dx;
-            double phi = gG[a] * L * F; /* Eq. periodic_phi, per axis */
+            double phi = gG[a] * L * Fb; /* Eq. periodic_phi, per axis */
             cplx wrap_lo = cexp(I * phi), wrap_hi = cexp(-I * phi);
             /* mirror, G normal to the face: hat g_i(x_m) =
              * conj( hat g_ibar(x_n) exp(i gamma (x_n + x_m - 2 x_o).G0 F) ),
              * origin x_o = 0 (where G0.x = 0). */
             double xlo = (0 + (-1)) * dx, xhi = ((dims[a] - 1) + dims[a]) * dx;
-            cplx rot_lo = cexp(I * gG[a] * xlo * F), rot_hi = cexp(I * gG[a] * xhi * F);
+            cplx rot_lo = cexp(I * gG[a] * xlo * Fb), rot_hi = cexp(I * gG[a] * xhi * Fb);
             for (int d = 0; d < PAD; ++d)
             for (int u = 0; u < dims[o2]; ++u)
                 for (int v = 0; v < dims[o1]; ++v) {
@@ -553,8 +574,8 @@ static int run_impl(int nx, int ny, int nz, double dx,
          * general-angle rule) */
         cplx wlo[3], whi[3];
         for (int a = 0; a < 3; ++a) {
-            wlo[a] = cexp(I * gG[a] * dims[a] * dx * F);
-            whi[a] = cexp(-I * gG[a] * dims[a] * dx * F);
+            wlo[a] = cexp(I * gG[a] * dims[a] * dx * Fb);
+            whi[a] = cexp(-I * gG[a] * dims[a] * dx * Fb);
         }
 
         /* 3. Streaming (Eq. streaming_LBM), with the half-link membrane rule
@@ -603,7 +624,7 @@ static int run_impl(int nx, int ny, int nz, double dx,
                         }
                     }
                     double xdotG = (x * dx) * gG[0] + (y * dx) * gG[1] + (z * dx) * gG[2];
-                    for (int j = 0; j < substeps; ++j) {
+                    for (int j = 0; j < substeps && !classical; ++j) {   /* 4. (hybrid only) */
                         cplx fac = cexp(-I * xdotG * f[k * substeps + j] * dts) * decay[ph[si]];
                         for (int i = 0; i < nq; ++i) gbar[i] = fac * gbar[i];
                     }
@@ -646,7 +667,7 @@ int lbm_oracle_run(int nx, int ny, int nz, double dx,
                    double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, NULL, NULL, 1, 0, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, NULL, NULL, 1, 0, 0, Z_out, field_out, series_out, state_out);
 }
 
 /*
@@ -665,7 +686,7 @@ int lbm_oracle_run_links(int nx, int ny, int nz, double dx,
 {
     if (!delta) return -1;
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, NULL, 1, 0, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, NULL, 1, 0, 0, Z_out, field_out, series_out, state_out);
 }
 
 /*
@@ -686,5 +707,25 @@ int lbm_oracle_run_ex(int nx, int ny, int nz, double dx,
                       int d2q5, double* Z_out, double* field_out, double* series_out, double* state_out)
 {
     return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
-                    gG, n_threads, delta, theta, substeps, d2q5, Z_out, field_out, series_out, state_out);
+                    gG, n_threads, delta, theta, substeps, d2q5, 0, Z_out, field_out, series_out, state_out);
+}
+
+/*
+ * As lbm_oracle_run_ex, with `classical` != 0 selecting the classical LBM
+ * of Appendix A (Eq. A12): the reaction enters the collision as the source
+ * dt omega_i R M, R = -i gamma x.G0 f(t^k) - 1/T2, and there is no reaction
+ * step (substeps must be 1).  The outer faces take F_(k+1) = sum_{m<=k} f_m dt
+ * (see run_impl).
+ */
+int lbm_oracle_run_scheme(int nx, int ny, int nz, double dx,
+                          const int32_t* labels, int n_labels, const uint8_t* phase_of_label,
+                          const int* bc, int n_phases, const double* D, const double* T2,
+                          double kappa, double dt, long n_steps, const double* f,
+                          const double* gG, int n_threads, const double* delta, const double* theta, int substeps,
+                          int d2q5, int classical, double* Z_out, double* field_out, double* series_out,
+                          double* state_out)
+{
+    return run_impl(nx, ny, nz, dx, labels, n_labels, phase_of_label, bc, n_phases, D, T2, kappa, dt, n_steps, f,
+                    gG, n_threads, delta, theta, substeps, d2q5, classical, Z_out, field_out, series_out,
+                    state_out);
 }

@@ -81,7 +81,7 @@ def _site(x, y, z, nx, ny):
     return (z * ny + y) * nx + x
 
 
-def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice="D3Q7"):
+def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice="D3Q7", scheme="hybrid"):
     """Final state g_i(x) [nz, ny, nx, Q] from operator matrices (tiny grids).
 
     Each step: collision block per site; a link map that routes every arriving
@@ -89,6 +89,10 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice
     factor, or the mirror image) and mixes in the membrane shares; a diagonal
     reaction.  Real-linear maps are kept as (A, B): v -> A v + B conj(v).
     lattice "D3Q7" (Q = 7) or "D2Q5" (Q = 5, one z plane, eps_D = 1/3).
+    scheme "classical" (Appendix A, Eq. A12): the collision block gains the
+    source column dt R(x, t^k) w (a rank-one block, w times the row of ones,
+    scaled by R = -i x.gG f_k - 1/T2), the reaction is the identity, and the
+    face phases use the waveform integral after step k, F + f_k dt.
     """
     labels = np.asarray(labels)
     nz, ny, nx = labels.shape
@@ -123,7 +127,20 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice
     lab = labels.ravel()
     g = np.tile(wts.astype(complex), N)
     F = 0.0
+    classical = scheme == "classical"
+    assert scheme in ("hybrid", "classical")
     for fk in f:
+        if classical:
+            Cs = C.astype(complex)
+            for z in range(nz):
+                for y in range(ny):
+                    for x in range(nx):
+                        t = _site(x, y, z, nx, ny)
+                        Rt = -1j * (x * gG[0] + y * gG[1] + z * gG[2]) * dx * fk - 1.0 / T2v[ph[t]]
+                        Cs[t * Q:(t + 1) * Q, t * Q:(t + 1) * Q] += dt * Rt * np.outer(wts, np.ones(Q))
+            Fl = F + fk * dt   # faces: the source of this step is in the streamed values
+        else:
+            Cs, Fl = C, F
         A = np.zeros((N * Q, N * Q), complex)
         B = np.zeros((N * Q, N * Q), complex)
         for z in range(nz):
@@ -139,13 +156,13 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice
                                 low = src[a] < 0
                                 if bc[a] == 0:
                                     src[a] %= dims[a]
-                                    fac = np.exp((1j if low else -1j) * gG[a] * dims[a] * dx * F)
+                                    fac = np.exp((1j if low else -1j) * gG[a] * dims[a] * dx * Fl)
                                 else:
                                     mirror = True
                                     if conj_axis[a]:
                                         xn = 0 if low else dims[a] - 1
                                         xm = -1 if low else dims[a]
-                                        mconj = np.exp(-1j * gG[a] * (xn + xm) * dx * F)
+                                        mconj = np.exp(-1j * gG[a] * (xn + xm) * dx * Fl)
                         row = t * Q + i
                         if mirror:
                             col = t * Q + opp[i]
@@ -167,8 +184,8 @@ def brute_state(labels, dx, phase_of_label, bc, D, T2, kappa, dt, f, gG, lattice
                 for x in range(nx):
                     t = _site(x, y, z, nx, ny)
                     xg = (x * gG[0] + y * gG[1] + z * gG[2]) * dx
-                    R[t * Q:(t + 1) * Q] = np.exp(-1j * xg * fk * dt) * math.exp(-dt / T2v[ph[t]])
-        h = C @ g
+                    R[t * Q:(t + 1) * Q] = 1.0 if classical else np.exp(-1j * xg * fk * dt) * math.exp(-dt / T2v[ph[t]])
+        h = Cs @ g
         g = R * (A @ h + B @ np.conj(h))
         F += fk * dt
     return g.reshape(nz, ny, nx, Q)
