@@ -578,6 +578,102 @@ def run_variants(args):
     return 0
 
 
+# ---------------------------------------------------------------- classical scheme (Appendix A)
+def run_classical(args):
+    """The paper's comparison scheme, the classical LBM with the reaction as a
+    collision source (Appendix A, Eq. A12), on the GPU.
+
+    Throughput: the 256^3 cylinders (dx 0.25 um, c2 phases, 3 gradient
+    directions, PGSE b = 1000) with the classical pass against the hybrid
+    pass on the same register sweep and on the bulk-copy sweep.
+
+    Accuracy (Sec. 3.2, Fig. 5): a uniform initial field in periodic squares
+    of side L = 20 and 100 um (D2Q5, D = 2.0, T2 = inf, tau = 0.6, PGSE
+    b = 1000, delta 3 / Delta 6 ms, run to the echo), relative L2 error of
+    the field at the echo against the continuum exp(-bD), for dx = 1, 0.5
+    and 0.25 um: the hybrid's does not depend on L, the classical one's does."""
+    import torch
+    from paper_1907_00908_gb300 import lbmbt, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = min(args.n, 256)
+    geom = synth.cylinders(n, 0.25, seed=1)
+    dt = 0.0015625
+    gGs = [lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, dt, d)[0] for d in ((1, 0, 0), (0, 1, 0), (1, 1, 1))]
+    _, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, dt, (1, 0, 0))
+    members = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
+    timing = {}
+    clocks = None
+    for name, scheme, kernel in (("classical_register", 1, 1), ("hybrid_register", 0, 1),
+                                 ("hybrid_bulk_copy", 0, 2)):
+        s = lbmbt.Solver(0, stream)
+        s.set_option(lbmbt.OPT_SCHEME, scheme)
+        s.set_option(lbmbt.OPT_KERNEL, kernel)
+        s.set_option(lbmbt.OPT_AUTOTUNE, 0 if args.no_autotune else 1)
+        s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, (0, 0, 0))
+        s.set_phases(C2_D, C2_T2)
+        s.set_sequence(dt, f, gGs[0])
+        s.prepare(members)
+        s.advance(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(0) as clk:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.advance(args.steps, want_signal=True, n_members=len(gGs))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        timing[name] = {"MLUPS": geom.n_sites * len(gGs) / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                        "launch": {"block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT)}}
+        if scheme == 1:
+            clocks = clk.summary()
+        s.close()
+
+    # Sec. 3.2 / Fig. 5: uniform initial field, L-dependence
+    Dfree, b, delta, Delta, tau = 2.0, 1000.0, 3.0, 6.0, 0.6
+    ex = math.exp(-b * 1e-3 * Dfree)
+    study = {}
+    for L in (20.0, 100.0):
+        for dx in (1.0, 0.5, 0.25):
+            m = math.ceil(delta / ((tau - 0.5) * (1.0 / 3.0) * dx * dx / Dfree))
+            while abs(Delta * m / delta - round(Delta * m / delta)) > 1e-9:
+                m += 1
+            dts = delta / m
+            gG, fs = lbmbt.pgse(b, delta, Delta, dts, (1, 0, 0))
+            nn = int(round(L / dx))
+            lab = np.zeros((1, nn, nn), np.int32)
+            row = {"dt_ms": dts, "steps": len(fs)}
+            for scheme in (0, 1):
+                s = lbmbt.Solver(0, stream)
+                s.set_option(lbmbt.OPT_SCHEME, scheme)
+                s.set_option(lbmbt.OPT_LATTICE, 1)
+                s.set_geometry(lab, [0], dx, (0, 0, 0))
+                s.set_phases([Dfree], [math.inf])
+                s.set_sequence(dts, fs, gG)
+                fld = torch.zeros(lab.size, dtype=torch.complex64, device="cuda")
+                r = s.run(field=fld)
+                torch.cuda.synchronize()
+                err = float(torch.sqrt(torch.mean(torch.abs(fld.to(torch.complex128) - ex) ** 2)) / ex)
+                fin = lambda x: x if math.isfinite(x) else None   # a diverged run has no error to report
+                row["classical" if scheme else "hybrid"] = {"S": fin(r["S"]), "field_L2_rel_err": fin(err)}
+                s.close()
+            study[f"L{int(L)}_dx{dx}"] = row
+    peak, peak_kind = peaks()
+    v = timing["classical_register"]["MLUPS"]
+    achieved = BYTES_PER_SITE * v * 1e6 / 1e9
+    line = {"metric": "MLUPS (classical LBM with reaction source, FP32)", "value": v, "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": timing["classical_register"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"cylinders{n}_dx0.25_classical_3dir", "grid": [n] * 3},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_classical_kernel"},
+            "compare": timing, "uniform_ic_study": study, "exact_exp_minus_bD": ex, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- slabs (strips)
 def run_slab(args):
     """The 512^3 tissue batch cut into z slabs on one GPU (one context per
@@ -658,13 +754,16 @@ def main():
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
     ap.add_argument("--slabs", type=int, default=4, help="slab workload: number of z slabs")
     ap.add_argument("--workload", default="tissue512",
-                    choices=["tissue512", "batch", "adjoint", "slab", "links", "variants", "membrane_study"],
+                    choices=["tissue512", "batch", "adjoint", "slab", "links", "variants", "membrane_study",
+                             "classical"],
                     help="tissue512 (default): the 512^3 tissue batch of 3 directions; batch: 528 members on "
                          "17 geometries; adjoint: gradient of 60 members on a 96^3 sphere pack; slab: the "
                          "tissue batch cut into --slabs z slabs with a face exchange per step; links: membranes at "
                          "their exact positions on the links (256^3 cylinders) against the half-link rule; variants: "
                          "D2Q5 and reaction sub-steps against their plain counterparts; membrane_study: the "
-                         "paper's four membrane-rule variants on a 40 um disc, 100^2 to 800^2")
+                         "paper's four membrane-rule variants on a 40 um disc, 100^2 to 800^2; classical: the "
+                         "classical LBM with a reaction source against the hybrid scheme (throughput on 256^3 "
+                         "cylinders, and the domain-size study of Sec. 3.2)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -680,6 +779,8 @@ def main():
         return run_membrane_study(args)
     if args.workload == "variants":
         return run_variants(args)
+    if args.workload == "classical":
+        return run_classical(args)
 
     import torch
     import torch.distributed as dist

@@ -305,8 +305,22 @@ enum {
                                 plane of >= 2^17 sites, else prefetched into
                                 registers; 1 always prefetched; 2 always
                                 staged (2 more rows per stage slot)            */
-    LBMBT_OPT_STAGE_OWN_Z_USED = 13 /* read-only: 1 prefetched or 2 staged for a
+    LBMBT_OPT_STAGE_OWN_Z_USED = 13, /* read-only: 1 prefetched or 2 staged for a
                                 prepared bulk-copy run, else 0                 */
+    LBMBT_OPT_SCHEME = 14    /* 0 (default) the hybrid scheme (Eq.
+                                LBM_process_list_2); 1 the paper's comparison
+                                scheme, the classical LBM with the reaction as
+                                a source term in the collision (Appendix A,
+                                Eqs. A2 and A12): hat g_i = g_i - (g_i -
+                                omega_i M)/tau + dt omega_i R M, R = -i gamma
+                                x.G0 f(t^k) - 1/T2, no reaction step; the
+                                outer faces then take the waveform integral
+                                after the step, F_(k+1) = sum_{m<=k} f_m dt.
+                                Register sweep only (a forced bulk-copy sweep
+                                returns EINVAL), half-link membranes only
+                                (positions: EUNSUPPORTED), no reaction
+                                sub-steps (EINVAL), no slabs and no adjoint
+                                (EUNSUPPORTED); both lattices              */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

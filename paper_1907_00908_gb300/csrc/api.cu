@@ -85,6 +85,8 @@ struct lbmbt_ctx {
     int adj_cap = 0;
     int adjoint_opt = 0;          // 0 auto, 1 register adjoint, 2 bulk-copy adjoint
     int lattice = 0;              // 0 D3Q7, 1 D2Q5 (Sec. 2.3; grids of one z plane)
+    int scheme = 0;               // 0 hybrid, 1 classical LBM with a reaction source (Eq. A12)
+    int substeps = 1;             // reaction sub-steps folded into the waveform (hybrid only)
     int adj_shape = 2;            // bulk-copy adjoint consumer shape (15 warps x 1 site)
     int adj_shape_used = 2;       // the shape of the prepared run (2 falls back to 1 when an nx > 480)
     bool use_tma = false;
@@ -564,8 +566,11 @@ extern "C" int lbmbt_set_sequence(lbmbt_ctx* c, double dt, int64_t n_steps, cons
     c->n_steps = n_steps;
     c->f.assign(f, f + n_steps);
     for (int a = 0; a < 3; ++a) c->gG[a] = gG[a];
-    std::vector<float> ff(n_steps);
-    std::vector<double> FF(n_steps + 1);
+    c->substeps = 1;
+    // f_k and F_k with one entry past the end (f_K = 0, F_(K+1) = F_K): the
+    // classical scheme's pass k reads them one step ahead
+    std::vector<float> ff(n_steps + 1, 0.f);
+    std::vector<double> FF(n_steps + 2);
     double F = 0.0;
     for (long long k = 0; k < n_steps; ++k) {
         ff[k] = (float)f[k];
@@ -573,12 +578,13 @@ extern "C" int lbmbt_set_sequence(lbmbt_ctx* c, double dt, int64_t n_steps, cons
         F += f[k] * dt;
     }
     FF[n_steps] = F;
+    FF[n_steps + 1] = F;
     cudaFree(c->d_f); cudaFree(c->d_F);
     c->d_f = nullptr; c->d_F = nullptr;
-    CU(c, cudaMalloc(&c->d_f, n_steps * sizeof(float)));
-    CU(c, cudaMalloc(&c->d_F, (n_steps + 1) * sizeof(double)));
-    CU(c, cudaMemcpyAsync(c->d_f, ff.data(), n_steps * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-    CU(c, cudaMemcpyAsync(c->d_F, FF.data(), (n_steps + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMalloc(&c->d_f, (n_steps + 1) * sizeof(float)));
+    CU(c, cudaMalloc(&c->d_F, (n_steps + 2) * sizeof(double)));
+    CU(c, cudaMemcpyAsync(c->d_f, ff.data(), (n_steps + 1) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CU(c, cudaMemcpyAsync(c->d_F, FF.data(), (n_steps + 2) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     return sync(c);
 }
 
@@ -600,7 +606,9 @@ extern "C" int lbmbt_set_sequence_substeps(lbmbt_ctx* c, double dt, int64_t n_st
         for (int j = 0; j < substeps; ++j) acc += f_fine[k * substeps + j];
         fm[k] = acc / substeps;
     }
-    return lbmbt_set_sequence(c, dt, n_steps, fm.data(), gG);
+    const int rc = lbmbt_set_sequence(c, dt, n_steps, fm.data(), gG);
+    if (rc == LBMBT_OK) c->substeps = substeps;
+    return rc;
 }
 
 extern "C" int lbmbt_pgse(double b, double delta, double Delta, double dt, const double dir[3], double gG_out[3],
@@ -639,6 +647,7 @@ static constexpr long long TMA_OZ_PLANE = 1LL << 17;
 static bool tma_eligible(const lbmbt_ctx* c)
 {
     if (c->lattice != 0) return false;   // the bulk-copy sweep has the D3Q7 weights built in
+    if (c->scheme != 0) return false;    // and the hybrid scheme's reaction step
     for (auto& d : c->descs)
         if (d.nx % 16 != 0 || d.nx > TMA_MAX_CAP || d.dlt != nullptr) return false;
     return true;
@@ -659,8 +668,8 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     const bool want = c->kernel_opt == 2 || (c->kernel_opt == 0 && c->tuned_kernel != 1);
     const bool tma = want && tma_eligible(c);
     if (c->kernel_opt == 2 && !tma)
-        return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member and no "
-                                     "membrane positions", TMA_MAX_CAP);
+        return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member, no "
+                                     "membrane positions, the D3Q7 lattice and the hybrid scheme", TMA_MAX_CAP);
     int cap = 16, capx = 0;
     for (int m = 0; m < c->n_members; ++m) {
         MemberDesc& d = c->descs[m];
@@ -744,6 +753,7 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.ctl = c->d_ctl;
     a.f = c->d_f;
     a.F = c->d_F;
+    a.scheme = c->scheme;
     a.partial = c->d_partial;
     a.fac = c->d_fac;
     a.links = 0;
@@ -764,6 +774,11 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     return a;
 }
 
+// F_k table of the control kernel's boundary factors: the hybrid scheme
+// streams before step k's reaction (F_k); the classical scheme's streamed
+// populations already hold step k's source, so its faces take F_(k+1).
+static const double* ctl_F(const lbmbt_ctx* c) { return c->scheme == 1 ? c->d_F + 1 : c->d_F; }
+
 static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base = 0, int slot_mod = 2)
 {
     StepCtl h;
@@ -775,7 +790,7 @@ static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base =
     h.slot_mod = slot_mod;
     h.series = c->series_mode ? 1 : 0;
     h.err = 0;
-    CU(c, launch_ctl(c->d_ctl, h, 1, c->d_desc, c->n_members, c->d_F, c->d_fac, c->stream));
+    CU(c, launch_ctl(c->d_ctl, h, 1, c->d_desc, c->n_members, ctl_F(c), c->d_fac, c->stream));
     c->launches++;
     return LBMBT_OK;
 }
@@ -803,7 +818,7 @@ static int issue_step(lbmbt_ctx* c)
     }
     StepCtl none;
     memset(&none, 0, sizeof none);
-    CU(c, launch_ctl(c->d_ctl, none, 0, c->d_desc, c->n_members, c->d_F, c->d_fac, c->stream));
+    CU(c, launch_ctl(c->d_ctl, none, 0, c->d_desc, c->n_members, ctl_F(c), c->d_fac, c->stream));
     c->launches += 2;
     if (c->series_mode) {
         CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
@@ -881,6 +896,8 @@ static int autotune(lbmbt_ctx* c)
     return LBMBT_OK;
 }
 
+static bool any_slab(const lbmbt_ctx* c);
+
 static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool series, void* field_dev)
 {
     if (c->geoms.empty()) return fail(c, LBMBT_ESTATE, "no geometry set");
@@ -888,6 +905,11 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
     if (c->n_steps == 0) return fail(c, LBMBT_ESTATE, "sequence not set");
     if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
     if (field_dev && n_members != 1) return fail(c, LBMBT_EINVAL, "field output needs a single member");
+    if (c->scheme == 1) {
+        if (any_slab(c)) return fail(c, LBMBT_EUNSUPPORTED, "the classical scheme does not run on slabs");
+        if (c->substeps != 1)
+            return fail(c, LBMBT_EINVAL, "the classical scheme has no reaction step to sub-step");
+    }
     int rc = set_device(c);
     if (rc) return rc;
     std::vector<MemberDesc> descs(n_members);
@@ -939,7 +961,10 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
             if (p < c->n_phases && !(tau > 0.5))
                 return fail(c, LBMBT_EUNSTABLE, "phase %d: tau = %.17g <= 1/2", p, tau);
             d.omega[p] = (float)(1.0 / tau);
-            d.eps[p] = std::isinf(c->T2[p]) ? 0.f : (float)(-std::expm1(-c->dt / c->T2[p]));
+            if (c->scheme == 1)   // the classical source's decay rate: dt/T2 (Eq. A12)
+                d.eps[p] = std::isinf(c->T2[p]) ? 0.f : (float)(c->dt / c->T2[p]);
+            else
+                d.eps[p] = std::isinf(c->T2[p]) ? 0.f : (float)(-std::expm1(-c->dt / c->T2[p]));
         }
         const double kap = mm.kappa_um_ms;
         const double cP = eps * g.dx / (2.0 * c->dt);   // P = cP / kappa  (Eq. P_def)
@@ -950,6 +975,8 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         d.memb = g.has_membranes;
         if (g.d_dlt && !std::isinf(kap)) {
             if (g.slab) return fail(c, LBMBT_EUNSUPPORTED, "membrane positions on a slab are not supported");
+            if (c->scheme == 1)
+                return fail(c, LBMBT_EUNSUPPORTED, "the classical scheme takes the half-link membrane rule only");
             d.dlt = g.d_dlt;
             d.lrho = (float)(kap * c->dt / (eps * g.dx));
             if (g.d_dth) {
@@ -1293,6 +1320,10 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "own-z staging must be 0 (auto), 1 or 2");
         c->oz_opt = (int)v;
         break;
+    case LBMBT_OPT_SCHEME:
+        if (v != 0 && v != 1) return fail(c, LBMBT_EINVAL, "scheme must be 0 (hybrid) or 1 (classical)");
+        c->scheme = (int)v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -1314,6 +1345,7 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_ADJOINT_SHAPE: *v = c->adj_shape; break;
     case LBMBT_OPT_LATTICE: *v = c->lattice; break;
     case LBMBT_OPT_STAGE_OWN_Z: *v = c->oz_opt; break;
+    case LBMBT_OPT_SCHEME: *v = c->scheme; break;
     case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? (c->tma_oz ? 2 : 1) : 0; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
@@ -1511,6 +1543,7 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
     if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
     if (c->geoms.empty() || c->n_phases == 0 || c->n_steps == 0) return fail(c, LBMBT_ESTATE, "set-up incomplete");
     if (any_slab(c)) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not run on slabs");
+    if (c->scheme != 0) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep is of the hybrid scheme only");
     for (auto& g : c->geoms)
         if (g.d_dlt) return fail(c, LBMBT_EUNSUPPORTED, "the adjoint sweep does not take membrane positions");
     if (c->lattice != 0 && c->adjoint_opt == 2)

@@ -51,7 +51,8 @@ struct MemberDesc {
     double dx;            // um
     float ctheta[3];      // -gG_a*dx*dt: reaction angle = f_k * sum_a ctheta_a * n_a
     float omega[4];       // 1/tau_p (Eq. tau_def)
-    float eps[4];         // 1 - exp(-dt/T2_p), from expm1 in FP64
+    float eps[4];         // 1 - exp(-dt/T2_p), from expm1 in FP64; for the
+                          // classical scheme dt/T2_p (its Euler source)
     float s_share;        // 1/(1+P): crossing share of a membrane link (Eq. B5)
     int axes;             // bit a set iff ctheta[a] != 0
     int memb;             // the geometry has at least one membrane link
@@ -107,6 +108,11 @@ struct SweepArgs {
                                   // variant with the Eqs. B4a-B4c rule); 2: and angles
     float w0, wxy, wz;            // equilibrium weights (register sweep, init):
                                   // D3Q7 1/4, 1/8, 1/8; D2Q5 1/3, 1/6, 0 (Sec. 2.3)
+    int scheme;                   // 0 the hybrid scheme; 1 the classical LBM with the
+                                  // reaction as a collision source (Appendix A, Eq. A12),
+                                  // register sweep only: f and F are then read one step
+                                  // ahead (f[k+1], F[k+1]), since the loop state hat g(t^k)
+                                  // already holds step k's source
 };
 
 // ---- launchers (sweep.cu) ------------------------------------------------

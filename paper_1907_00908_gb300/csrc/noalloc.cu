@@ -243,6 +243,7 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.fac = fac;
     a.links = 0;
     a.w0 = W0; a.wxy = WI; a.wz = WI;   // D3Q7
+    a.scheme = 0;                       // the hybrid scheme
     MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
     const double* Fd = reinterpret_cast<const double*>(base + OFF_FCUM);
     // control word (done counter and step start from the values above every

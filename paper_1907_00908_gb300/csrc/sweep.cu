@@ -16,6 +16,9 @@
 //    populations stay exactly 0 and are not touched).
 //  * sweep_links_kernel: the same step with membranes at given positions on
 //        the links (Eqs. B4a-B4c), the rule's links compacted per warp
+//  * sweep_classical_kernel: the same pass for the classical LBM (Appendix A,
+//        Eq. A12): stream + BCs + membrane, M = sum_i g_i, collision with
+//        the reaction as a source term; no reaction step
 //  * ctl_kernel        : sets / advances the step word between sweeps and
 //                        computes the next step's FP64 boundary factors
 //  * reduce_kernel     : fixed-order FP64 sum of the per-tile partials.
@@ -68,8 +71,12 @@ __global__ void build_mask_kernel(const int32_t* __restrict__ labels, const uint
 }
 
 // ---------------------------------------------------------------- init
+// Hybrid scheme: hat g(t^0) = g_eq = omega_i (M = 1).  Classical scheme: the
+// loop state hat g(t^0) is the collision of g_eq with the source of step 0,
+// omega_i (1 + dt R(x, t^0)), R = -i gamma x.G0 f_0 - 1/T2 (Eq. A12).
 __global__ void init_kernel(const MemberDesc* __restrict__ members, const long long* __restrict__ tile_start,
-                            int n_members, int spt, int slot, float w0, float wxy, float wz)
+                            int n_members, int spt, int slot, float w0, float wxy, float wz, int classical,
+                            const float* __restrict__ f)
 {
     __shared__ int sm;
     if (threadIdx.x == 0) sm = find_member(tile_start, n_members, blockIdx.x);
@@ -81,9 +88,19 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
     for (int j = 0; j < spt; ++j) {
         const unsigned s = base + j * blockDim.x + threadIdx.x;
         if (s < (unsigned)d.N) {
-            out[s] = make_float2(w0, 0.f);
+            float2 src = make_float2(0.f, 0.f);   // dt R M with M = 1
+            if (classical) {
+                int x, y, z;
+                coords(&d, s, d.nx, d.ny, x, y, z);
+                const float f0 = __ldg(f);
+                src = source_dtRM(d.eps[d.mask[s] >> 6], f0 != 0.f ? theta_lin(&d, f0, x, y, z) : 0.f, 1.f, 0.f);
+            }
+            out[s] = make_float2(__fmaf_rn(w0, src.x, w0), __fmul_rn(w0, src.y));
 #pragma unroll
-            for (int i = 1; i < Q; ++i) out[(size_t)i * P + s] = make_float2(i < 5 ? wxy : wz, 0.f);
+            for (int i = 1; i < Q; ++i) {
+                const float w = i < 5 ? wxy : wz;
+                out[(size_t)i * P + s] = make_float2(__fmaf_rn(w, src.x, w), __fmul_rn(w, src.y));
+            }
             // slab halo planes start at the neighbours' initial values
             if (s < (unsigned)(d.nx * d.ny))
                 for (int h = 0; h < 2; ++h)
@@ -104,8 +121,9 @@ inline size_t link_smem_bytes(int block, int spt)
     return (size_t)(block / 32) * spt * LINK_SLOTS * (sizeof(float2) + sizeof(uint16_t));
 }
 
-// LINKS: 0 half-link rule only, 1 membrane positions, 2 positions and angles
-template <int SPT, int LINKS>
+// LINKS: 0 half-link rule only, 1 membrane positions, 2 positions and angles.
+// CLS: the classical scheme (Eq. A12) instead of the hybrid one.
+template <int SPT, int LINKS, bool CLS = false>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a)
 {
     __shared__ double2 s_red[32];
@@ -121,7 +139,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const bool do_field = k == __ldcg(&a.ctl->field_step) && field != nullptr;
     const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + m) * 6;
 
-    const float fk = __ldg(a.f + k);
+    // classical: the collision of this pass carries the source of step k+1
+    const float fk = __ldg(a.f + k + (CLS ? 1 : 0));
     const unsigned P = (unsigned)sd->plane;
     const float2* __restrict__ src = sd->state + (size_t)((k - sbase) % smod) * 7 * P;
     float2* __restrict__ dst = sd->state + (size_t)((k + 1 - sbase) % smod) * 7 * P;
@@ -249,11 +268,25 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
         // applied as g + g q with q = exp(i theta)(1 - eps) - 1 (minus-one
         // forms, no O(1) rounding); then M and the BGK collision
         // (Eqs. M'summation, collision_LBM).
-        const float2 q = fk != 0.f ? reaction_q(rotation_m1(sd, fk, x, y, z), sd->eps[ph])
-                                   : make_float2(-sd->eps[ph], 0.f);
         float mr, mi;
-        react(g, q, mr, mi);
-        collide_w(g, sd->omega[ph], mr, mi, a.w0, a.wxy, a.wz);
+        if (CLS) {
+            // Classical scheme (Eq. A12): no reaction step; M(t^(k+1)) =
+            // sum_i g_i, then the collision with the source dt R M of t^(k+1)
+            mr = 0.f;
+            mi = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                mr = __fadd_rn(mr, g[i].x);
+                mi = __fadd_rn(mi, g[i].y);
+            }
+            const float2 src = source_dtRM(sd->eps[ph], fk != 0.f ? theta_lin(sd, fk, x, y, z) : 0.f, mr, mi);
+            collide_source_w(g, sd->omega[ph], mr, mi, src.x, src.y, a.w0, a.wxy, a.wz);
+        } else {
+            const float2 q = fk != 0.f ? reaction_q(rotation_m1(sd, fk, x, y, z), sd->eps[ph])
+                                       : make_float2(-sd->eps[ph], 0.f);
+            react(g, q, mr, mi);
+            collide_w(g, sd->omega[ph], mr, mi, a.w0, a.wxy, a.wz);
+        }
 #pragma unroll
         for (int i = 0; i < Q; ++i)
             if (i < 5 || zpl) __stcs(dst + (size_t)i * P + s, g[i]);
@@ -288,6 +321,12 @@ template <int SPT>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs a)
 {
     sweep_body<SPT, 0>(a);
+}
+
+template <int SPT>
+__global__ void __launch_bounds__(512) sweep_classical_kernel(const SweepArgs a)
+{
+    sweep_body<SPT, 0, true>(a);
 }
 
 // With membrane positions: two blocks of 512 per SM (64 registers), since
@@ -392,7 +431,7 @@ cudaError_t launch_build_mask(const int32_t* labels, const uint8_t* phase_of_lab
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot, cudaStream_t st)
 {
     init_kernel<<<(unsigned)n_tiles, block, 0, st>>>(a.members, a.tile_start, a.n_members, spt, slot, a.w0, a.wxy,
-                                                     a.wz);
+                                                     a.wz, a.scheme, a.f);
     return cudaGetLastError();
 }
 
@@ -413,6 +452,15 @@ cudaError_t links_prepare()
 
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st)
 {
+    if (a.scheme == 1) {   // classical scheme: half-link rule only (positions are refused at set-up)
+        switch (spt) {
+        case 1: sweep_classical_kernel<1><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
+        case 2: sweep_classical_kernel<2><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
+        case 4: sweep_classical_kernel<4><<<(unsigned)n_tiles, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (spt) {
     case 1:
         if (a.links == 2) sweep_links_kernel<1, true><<<(unsigned)n_tiles, block, link_smem_bytes(block, 1), st>>>(a);

@@ -204,6 +204,34 @@ __device__ __forceinline__ void collide_w(float2 (&g)[Q], float om, float mr, fl
     }
 }
 
+// Classical scheme (Appendix A, Eq. A12): collision with the reaction as a
+// source, hat g_i = g_i + omega (w_i M - g_i) + w_i (sr + i si), where
+// (sr, si) = dt R M, R = -i gamma x.G0 f - 1/T2 (Eq. A2), M = sum_i g_i.
+__device__ __forceinline__ void collide_source_w(float2 (&g)[Q], float om, float mr, float mi, float sr, float si,
+                                                 float w0, float wxy, float wz)
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float w = i == 0 ? w0 : i < 5 ? wxy : wz;
+        g[i].x = __fmaf_rn(w, sr, __fmaf_rn(om, __fmaf_rn(w, mr, -g[i].x), g[i].x));
+        g[i].y = __fmaf_rn(w, si, __fmaf_rn(om, __fmaf_rn(w, mi, -g[i].y), g[i].y));
+    }
+}
+
+// The reaction angle itself, theta = f * sum_a ctheta_a n_a = -gamma x.G0 f dt
+// (the classical scheme's source is linear in it).
+__device__ __forceinline__ float theta_lin(const MemberDesc* __restrict__ d, float fk, int x, int y, int z)
+{
+    return __fmul_rn(fk, __fmaf_rn(d->ctheta[2], (float)(z + d->z0),
+                                   __fmaf_rn(d->ctheta[1], (float)y, __fmul_rn(d->ctheta[0], (float)x))));
+}
+
+// dt R M for R = -eps + i theta (eps = dt/T2): (-eps mr - theta mi, -eps mi + theta mr).
+__device__ __forceinline__ float2 source_dtRM(float ep, float th, float mr, float mi)
+{
+    return make_float2(__fmaf_rn(-ep, mr, __fmul_rn(-th, mi)), __fmaf_rn(-ep, mi, __fmul_rn(th, mr)));
+}
+
 // boundary_factors() into a flat [6] array: index 2*axis + (0 low, 1 high).
 __device__ __forceinline__ void boundary_factors6(const MemberDesc& sd, double F, float2* out6)
 {
