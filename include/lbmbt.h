@@ -251,6 +251,38 @@ typedef struct {
 int lbmbt_run_batch(lbmbt_ctx* ctx, int n_members, const lbmbt_member* members,
                     double* signal_out, double* series_out);
 
+/* One member of lbmbt_run_batch_ex: lbmbt_member plus the member's own
+ * gradient waveform and field output.  The dMRI protocols the method serves
+ * (Sec. 2.1, Fig. 2) mix diffusion times (delta, Delta), so a batch can mix
+ * waveforms:
+ *   f        host, the member's waveform f[0 .. n_steps-1] sampled as in
+ *            lbmbt_set_sequence (same dt), or NULL for the set waveform;
+ *   n_steps  length of f, 1 .. the set sequence's n_steps (ignored when f is
+ *            NULL): the member's signal and field are those at t = n_steps*dt
+ *            (its echo); the batch runs to the longest, and a shorter member
+ *            keeps stepping with f = 0 after its end, unobserved;
+ *   field_dev device complex64 [N of its geometry] receiving M(x) at the
+ *            member's end, or NULL. */
+typedef struct {
+    double gamma_G0[3];
+    int geometry;
+    double kappa_um_ms;
+    const double* f;
+    int64_t n_steps;
+    void* field_dev;
+} lbmbt_member_ex;
+
+/*
+ * lbmbt_run_batch with per-member waveforms and field outputs (one launch
+ * per time step, as lbmbt_run_batch).  signal_out[n_members][3] as in
+ * lbmbt_run, each member's at its own end; series_out [n_members][n_steps][2]
+ * or NULL (entries past a member's end are of its continued, unobserved run).
+ * The waveforms and fields are used by this call only.  Errors: EINVAL for a
+ * waveform longer than the set sequence, empty, or not finite.
+ */
+int lbmbt_run_batch_ex(lbmbt_ctx* ctx, int n_members, const lbmbt_member_ex* members,
+                       double* signal_out, double* series_out);
+
 /*
  * Gradient of S = |Z|/N at t_end with respect to the per-phase D_p and T2_p
  * and the permeability kappa, for the plain run (geometry 0, set gradient),

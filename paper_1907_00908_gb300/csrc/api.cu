@@ -143,6 +143,11 @@ struct lbmbt_ctx {
     size_t cap_gout = 0;
     double2* d_laminit = nullptr;
     size_t cap_laminit = 0;
+    // members' own waveforms (lbmbt_run_batch_ex): f [K+1] and F [K+2] per such member
+    float* d_wf = nullptr;
+    size_t cap_wf = 0;
+    double* d_wF = nullptr;
+    size_t cap_wF = 0;
 };
 
 static std::string g_create_error;
@@ -774,10 +779,11 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     return a;
 }
 
-// F_k table of the control kernel's boundary factors: the hybrid scheme
-// streams before step k's reaction (F_k); the classical scheme's streamed
-// populations already hold step k's source, so its faces take F_(k+1).
-static const double* ctl_F(const lbmbt_ctx* c) { return c->scheme == 1 ? c->d_F + 1 : c->d_F; }
+// Offset into the F_k tables of the control kernel's boundary factors: the
+// hybrid scheme streams before step k's reaction (F_k); the classical
+// scheme's streamed populations already hold step k's source, so its faces
+// take F_(k+1).
+static int ctl_F_shift(const lbmbt_ctx* c) { return c->scheme == 1 ? 1 : 0; }
 
 static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base = 0, int slot_mod = 2)
 {
@@ -790,7 +796,7 @@ static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base =
     h.slot_mod = slot_mod;
     h.series = c->series_mode ? 1 : 0;
     h.err = 0;
-    CU(c, launch_ctl(c->d_ctl, h, 1, c->d_desc, c->n_members, ctl_F(c), c->d_fac, c->stream));
+    CU(c, launch_ctl(c->d_ctl, h, 1, c->d_desc, c->n_members, ctl_F_shift(c), c->d_fac, c->stream));
     c->launches++;
     return LBMBT_OK;
 }
@@ -818,7 +824,7 @@ static int issue_step(lbmbt_ctx* c)
     }
     StepCtl none;
     memset(&none, 0, sizeof none);
-    CU(c, launch_ctl(c->d_ctl, none, 0, c->d_desc, c->n_members, ctl_F(c), c->d_fac, c->stream));
+    CU(c, launch_ctl(c->d_ctl, none, 0, c->d_desc, c->n_members, ctl_F_shift(c), c->d_fac, c->stream));
     c->launches += 2;
     if (c->series_mode) {
         CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
@@ -898,7 +904,10 @@ static int autotune(lbmbt_ctx* c)
 
 static bool any_slab(const lbmbt_ctx* c);
 
-static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool series, void* field_dev)
+// ex (optional, [n_members]): each member's own waveform (f, n_steps; f NULL
+// for the run's) and field output.
+static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool series, void* field_dev,
+                   const lbmbt_member_ex* ex = nullptr)
 {
     if (c->geoms.empty()) return fail(c, LBMBT_ESTATE, "no geometry set");
     if (c->n_phases == 0) return fail(c, LBMBT_ESTATE, "phases not set");
@@ -997,6 +1006,18 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         div_magic((unsigned)g.nx, &d.div_m[0], &d.div_s[0]);
         div_magic((unsigned)g.ny, &d.div_m[1], &d.div_s[1]);
         if ((size_t)d.plane > max_plane) max_plane = d.plane;
+        d.fw = c->d_f;
+        d.Fw = c->d_F;
+        d.end_step = -1;
+        if (ex) {
+            if (ex[m].f && (ex[m].n_steps < 1 || ex[m].n_steps > c->n_steps))
+                return fail(c, LBMBT_EINVAL, "member %d: waveform of %lld steps, the run has %lld", m,
+                            (long long)ex[m].n_steps, c->n_steps);
+            if (ex[m].f)
+                for (long long k = 0; k < ex[m].n_steps; ++k)
+                    if (!std::isfinite(ex[m].f[k])) return fail(c, LBMBT_EINVAL, "member %d: f[%lld] not finite", m, k);
+            d.end_step = (int)((ex[m].f ? ex[m].n_steps : c->n_steps) - 1);
+        }
     }
     invalidate_run(c);
     c->n_members = n_members;
@@ -1015,6 +1036,43 @@ static int prepare(lbmbt_ctx* c, int n_members, const lbmbt_member* mem, bool se
         off += (size_t)c->n_slots * 7 * d.plane * sizeof(float2);
     }
     if (field_dev) c->descs[0].field = (float2*)field_dev;
+    if (ex) {
+        // members' own waveforms: f_k (zero past the member's end, one entry
+        // past the run's) and F_k = sum_{m<k} f_m dt, as lbmbt_set_sequence
+        // builds the shared ones
+        const long long K = c->n_steps;
+        int n_own = 0;
+        for (int m = 0; m < n_members; ++m) n_own += ex[m].f != nullptr;
+        if (n_own) {
+            rc = grow(c, &c->d_wf, &c->cap_wf, sizeof(float) * (size_t)n_own * (K + 1));
+            if (!rc) rc = grow(c, &c->d_wF, &c->cap_wF, sizeof(double) * (size_t)n_own * (K + 2));
+            if (rc) return rc;
+            std::vector<float> wf((size_t)n_own * (K + 1), 0.f);
+            std::vector<double> wF((size_t)n_own * (K + 2));
+            int j = 0;
+            for (int m = 0; m < n_members; ++m) {
+                if (!ex[m].f) continue;
+                float* fj = wf.data() + (size_t)j * (K + 1);
+                double* Fj = wF.data() + (size_t)j * (K + 2);
+                double F = 0.0;
+                for (long long k = 0; k < K; ++k) {
+                    const double fk = k < ex[m].n_steps ? ex[m].f[k] : 0.0;
+                    fj[k] = (float)fk;
+                    Fj[k] = F;
+                    F += fk * c->dt;
+                }
+                Fj[K] = F;
+                Fj[K + 1] = F;
+                c->descs[m].fw = c->d_wf + (size_t)j * (K + 1);
+                c->descs[m].Fw = c->d_wF + (size_t)j * (K + 2);
+                ++j;
+            }
+            CU(c, cudaMemcpyAsync(c->d_wf, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice, c->stream));
+            CU(c, cudaMemcpyAsync(c->d_wF, wF.data(), sizeof(double) * wF.size(), cudaMemcpyHostToDevice, c->stream));
+            CU(c, cudaStreamSynchronize(c->stream));
+        }
+        for (int m = 0; m < n_members; ++m) c->descs[m].field = static_cast<float2*>(ex[m].field_dev);
+    }
     {   // slab halo planes: two of nx*ny complex values per slab member
         c->halo_off.assign(n_members, 0);
         size_t hn = 0;
@@ -1168,6 +1226,17 @@ static int fetch_signal(lbmbt_ctx* c, double* signal_out, double* series_out)
     }
     if (series_out && c->series_mode)
         for (size_t i = 0; i < ser.size(); ++i) { series_out[2 * i] = ser[i].x; series_out[2 * i + 1] = ser[i].y; }
+    // series mode reduces every step, so the last reduction is of the last
+    // step: a member that ends earlier takes its signal from its own step
+    if (signal_out && c->series_mode && !ser.empty())
+        for (int m = 0; m < c->n_members; ++m) {
+            const int es = c->descs[m].end_step;
+            if (es < 0 || es == c->n_steps - 1) continue;
+            const double2 z = ser[(size_t)m * c->n_steps + es];
+            signal_out[3 * m] = z.x;
+            signal_out[3 * m + 1] = z.y;
+            signal_out[3 * m + 2] = std::hypot(z.x, z.y) / (double)c->descs[m].N;
+        }
     return LBMBT_OK;
 }
 
@@ -1202,6 +1271,26 @@ extern "C" int lbmbt_run_batch(lbmbt_ctx* c, int n_members, const lbmbt_member* 
     int rc = prepare(c, n_members, members, series_out != nullptr, nullptr);
     if (!rc) rc = advance(c, c->n_steps, true);
     if (!rc) rc = fetch_signal(c, signal_out, series_out);
+    return rc;
+}
+
+extern "C" int lbmbt_run_batch_ex(lbmbt_ctx* c, int n_members, const lbmbt_member_ex* members, double* signal_out,
+                                  double* series_out)
+{
+    if (!c) return LBMBT_EINVAL;
+    if (!members || !signal_out) return fail(c, LBMBT_EINVAL, "members / signal_out is NULL");
+    if (any_slab(c)) return fail(c, LBMBT_ESTATE, "a slab runs with lbmbt_prepare and lbmbt_advance(1) per step");
+    if (n_members < 1) return fail(c, LBMBT_EINVAL, "n_members must be >= 1");
+    std::vector<lbmbt_member> base(n_members);
+    for (int m = 0; m < n_members; ++m) {
+        for (int a = 0; a < 3; ++a) base[m].gamma_G0[a] = members[m].gamma_G0[a];
+        base[m].geometry = members[m].geometry;
+        base[m].kappa_um_ms = members[m].kappa_um_ms;
+    }
+    int rc = prepare(c, n_members, base.data(), series_out != nullptr, nullptr, members);
+    if (!rc) rc = advance(c, c->n_steps, true);
+    if (!rc) rc = fetch_signal(c, signal_out, series_out);
+    // the run stands at its end: no later step writes the members' fields
     return rc;
 }
 

@@ -78,6 +78,14 @@ struct MemberDesc {
     // B): dth[(j-1)*plane + s] = signed angle between the membrane normal and
     // the link from s to s + e_j; nullptr = theta = 0 everywhere
     const float* dth;
+    // the member's waveform: fw[k] = f_k as float (one entry past the end,
+    // 0), Fw[k] = F_k = sum_{m<k} f_m dt (two entries past the end); the
+    // run's shared tables unless the member has a waveform of its own
+    const float* fw;
+    const double* Fw;
+    // step whose end signal partials (and field, if any) are this member's
+    // own: its echo when it is shorter than the run; -1: the step control's
+    int end_step;
 };
 
 // Step control word in device memory.  The sweep reads k here; a one-block
@@ -120,9 +128,10 @@ cudaError_t launch_build_mask(const int32_t* labels, const uint8_t* phase_of_lab
                               int nx, int ny, int nz, const int bc[3], uint8_t* mask, int* err,
                               cudaStream_t st);
 // set != 0: write v to the control word; else advance k by one.  Then compute
-// the boundary factors of the (new) step k for every member into fac[k & 1].
+// the boundary factors of the (new) step k for every member into fac[k & 1],
+// from the member's F table at k + F_shift (1 for the classical scheme).
 cudaError_t launch_ctl(StepCtl* ctl, const StepCtl& v, int set, const MemberDesc* members, int n_members,
-                       const double* F, float2* fac, cudaStream_t st);
+                       int F_shift, float2* fac, cudaStream_t st);
 // Boundary factors of every step 0..K for every member: table[k][m][6].
 cudaError_t launch_factor_table(const MemberDesc* members, int n_members, const double* F, long long K,
                                 float2* table, cudaStream_t st);

@@ -192,6 +192,7 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
         d.div_s[j] = 28 + l;
     }
     const long long n_tiles = (N + NA_TILE - 1) / NA_TILE;
+    d.end_step = -1;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -200,6 +201,8 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     int rc = na_scratch_ptr(dev, &base, errbuf, errlen);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    d.fw = reinterpret_cast<const float*>(base + OFF_F32);      // the waveform tables in the scratch
+    d.Fw = reinterpret_cast<const double*>(base + OFF_FCUM);
 
     StepCtl c;
     c.k = (int)k0;
@@ -245,14 +248,13 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.w0 = W0; a.wxy = WI; a.wz = WI;   // D3Q7
     a.scheme = 0;                       // the hybrid scheme
     MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
-    const double* Fd = reinterpret_cast<const double*>(base + OFF_FCUM);
     // control word (done counter and step start from the values above every
     // call) and the first step's boundary factors
-    if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 1, dd, 1, Fd, fac, st);
+    if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 1, dd, 1, 0, fac, st);
     if (e == cudaSuccess && init) e = launch_init(a, n_tiles, NA_BLOCK, NA_SPT, 0, st);
     for (long long k = 0; e == cudaSuccess && k < n_steps; ++k) {
         e = launch_sweep(a, n_tiles, NA_BLOCK, NA_SPT, st);
-        if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 0, dd, 1, Fd, fac, st);
+        if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 0, dd, 1, 0, fac, st);
     }
     double2* Zd = reinterpret_cast<double2*>(base + OFF_Z);
     if (e == cudaSuccess) e = launch_reduce(a.partial, a.tile_start, 1, 1, Zd, nullptr, 0, a.ctl, st);

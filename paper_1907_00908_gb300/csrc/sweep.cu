@@ -75,8 +75,7 @@ __global__ void build_mask_kernel(const int32_t* __restrict__ labels, const uint
 // loop state hat g(t^0) is the collision of g_eq with the source of step 0,
 // omega_i (1 + dt R(x, t^0)), R = -i gamma x.G0 f_0 - 1/T2 (Eq. A12).
 __global__ void init_kernel(const MemberDesc* __restrict__ members, const long long* __restrict__ tile_start,
-                            int n_members, int spt, int slot, float w0, float wxy, float wz, int classical,
-                            const float* __restrict__ f)
+                            int n_members, int spt, int slot, float w0, float wxy, float wz, int classical)
 {
     __shared__ int sm;
     if (threadIdx.x == 0) sm = find_member(tile_start, n_members, blockIdx.x);
@@ -92,7 +91,7 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
             if (classical) {
                 int x, y, z;
                 coords(&d, s, d.nx, d.ny, x, y, z);
-                const float f0 = __ldg(f);
+                const float f0 = __ldg(d.fw);
                 src = source_dtRM(d.eps[d.mask[s] >> 6], f0 != 0.f ? theta_lin(&d, f0, x, y, z) : 0.f, 1.f, 0.f);
             }
             out[s] = make_float2(__fmaf_rn(w0, src.x, w0), __fmul_rn(w0, src.y));
@@ -134,13 +133,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const MemberDesc* __restrict__ sd = a.members + m;
     const int k = __ldcg(&a.ctl->k);
     const int sbase = __ldcg(&a.ctl->slot_base), smod = __ldcg(&a.ctl->slot_mod);
-    const bool do_sig = __ldcg(&a.ctl->series) || k == __ldcg(&a.ctl->sig_step);
+    // a member with an end step of its own (shorter waveform in a batch)
+    // gives its signal and field there
+    const int es = sd->end_step;
+    const bool do_sig = __ldcg(&a.ctl->series) || k == (es >= 0 ? es : __ldcg(&a.ctl->sig_step));
     float2* const field = sd->field;
-    const bool do_field = k == __ldcg(&a.ctl->field_step) && field != nullptr;
+    const bool do_field = k == (es >= 0 ? es : __ldcg(&a.ctl->field_step)) && field != nullptr;
     const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + m) * 6;
 
     // classical: the collision of this pass carries the source of step k+1
-    const float fk = __ldg(a.f + k + (CLS ? 1 : 0));
+    const float fk = __ldg(sd->fw + k + (CLS ? 1 : 0));
     const unsigned P = (unsigned)sd->plane;
     const float2* __restrict__ src = sd->state + (size_t)((k - sbase) % smod) * 7 * P;
     float2* __restrict__ dst = sd->state + (size_t)((k + 1 - sbase) % smod) * 7 * P;
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(512, ANG ? 1 : 2) sweep_links_kernel(const Swe
 // Control word: set (or advance k), then the boundary factors of the new step
 // for every member, in FP64 (one block; members strided over its threads).
 __global__ void ctl_kernel(StepCtl* ctl, StepCtl v, int set, const MemberDesc* __restrict__ members,
-                           int n_members, const double* __restrict__ F, float2* __restrict__ fac)
+                           int n_members, int F_shift, float2* __restrict__ fac)
 {
     __shared__ int sk;
     if (threadIdx.x == 0) {
@@ -352,9 +354,8 @@ __global__ void ctl_kernel(StepCtl* ctl, StepCtl v, int set, const MemberDesc* _
     }
     __syncthreads();
     const int k = sk;
-    const double Fk = F[k];
     for (int m = threadIdx.x; m < n_members; m += blockDim.x)
-        boundary_factors6(members[m], Fk, fac + ((size_t)(k & 1) * n_members + m) * 6);
+        boundary_factors6(members[m], members[m].Fw[k + F_shift], fac + ((size_t)(k & 1) * n_members + m) * 6);
 }
 
 // Boundary factors of all steps 0..K (adjoint sweep): table[k][m][6].
@@ -400,9 +401,9 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, const long lo
 }  // namespace
 
 cudaError_t launch_ctl(StepCtl* ctl, const StepCtl& v, int set, const MemberDesc* members, int n_members,
-                       const double* F, float2* fac, cudaStream_t st)
+                       int F_shift, float2* fac, cudaStream_t st)
 {
-    ctl_kernel<<<1, 256, 0, st>>>(ctl, v, set, members, n_members, F, fac);
+    ctl_kernel<<<1, 256, 0, st>>>(ctl, v, set, members, n_members, F_shift, fac);
     return cudaGetLastError();
 }
 
@@ -431,7 +432,7 @@ cudaError_t launch_build_mask(const int32_t* labels, const uint8_t* phase_of_lab
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot, cudaStream_t st)
 {
     init_kernel<<<(unsigned)n_tiles, block, 0, st>>>(a.members, a.tile_start, a.n_members, spt, slot, a.w0, a.wxy,
-                                                     a.wz, a.scheme, a.f);
+                                                     a.wz, a.scheme);
     return cudaGetLastError();
 }
 

@@ -188,9 +188,8 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     }
 
     // ---------------- consumer warps
-    const bool do_sig = __ldcg(&a.ctl->series) || k == __ldcg(&a.ctl->sig_step);
-    const bool field_step = k == __ldcg(&a.ctl->field_step);
-    const float fk = __ldg(a.f + k);
+    const bool series = __ldcg(&a.ctl->series);
+    const int sig_step = __ldcg(&a.ctl->sig_step), field_step = __ldcg(&a.ctl->field_step);
     const int lsrc = (k - sbase) % smod, ldst = (k + 1 - sbase) % smod;
     const int warp = tid >> 5, lane = tid & 31;
 
@@ -234,6 +233,8 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     float sh = 0.f, om0 = 0.f, om1 = 0.f, om2 = 0.f, om3 = 0.f, ep0 = 0.f, ep1 = 0.f, ep2 = 0.f, ep3 = 0.f;
     float2* dstb = nullptr;
     float2* field = nullptr;
+    float fk = 0.f;            // the member's f_k
+    bool do_sig = false, do_field = false;
     const MemberDesc* __restrict__ sd = a.members;
 
     for (long long i = 0;; ++i) {
@@ -260,6 +261,11 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             ep0 = sd->eps[0]; ep1 = sd->eps[1]; ep2 = sd->eps[2]; ep3 = sd->eps[3];
             dstb = sd->state + (size_t)ldst * 7 * P;
             field = sd->field;
+            fk = __ldg(sd->fw + k);
+            // a member with an end step of its own gives its signal and field there
+            const int es = sd->end_step;
+            do_sig = series || k == (es >= 0 ? es : sig_step);
+            do_field = field != nullptr && k == (es >= 0 ? es : field_step);
         }
         const float2* __restrict__ r0 = stage_plane(sb, cap, 0);
         const float2* __restrict__ r1 = stage_plane(sb, cap, 1);
@@ -271,7 +277,6 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx, OZ);
         const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + G.m) * 6;
         float2* __restrict__ dst = dstb;
-        const bool do_field = field_step && field != nullptr;
         const int z = G.z;
 
         // Phase 1, every site of this thread: pulls with the face transforms
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         for (int j = 0; j < TMA_SPT; ++j)
 #pragma unroll
             for (int p = 0; p < 4; ++p) own[j][p] = nown[j][p];
-        if (do_sig) {   // grid-uniform; FP64 from the warp level up, one slot per warp
+        if (do_sig) {   // unit-uniform; FP64 from the warp level up, one slot per warp
             double dr = zr, di = zi;
             for (int o = 16; o > 0; o >>= 1) {
                 dr += __shfl_down_sync(0xffffffffu, dr, o);

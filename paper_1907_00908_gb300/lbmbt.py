@@ -35,7 +35,7 @@ EXPORTS = [
     "lbmbt_grad_batch", "lbmbt_set_option", "lbmbt_get_option", "lbmbt_prepare", "lbmbt_advance",
     "lbmbt_launch_count", "lbmbt_sweep_noalloc", "lbmbt_set_geometry_slab", "lbmbt_slab_faces",
     "lbmbt_slab_set_halos", "lbmbt_set_field", "lbmbt_set_link_distances", "lbmbt_set_sequence_substeps",
-    "lbmbt_set_link_angles",
+    "lbmbt_set_link_angles", "lbmbt_run_batch_ex",
 ]
 
 
@@ -48,6 +48,13 @@ class LbmbtError(RuntimeError):
 class Member(ctypes.Structure):
     """``lbmbt_member``: gradient, geometry index, permeability of one batch member."""
     _fields_ = [("gamma_G0", ctypes.c_double * 3), ("geometry", ctypes.c_int), ("kappa_um_ms", ctypes.c_double)]
+
+
+class MemberEx(ctypes.Structure):
+    """``lbmbt_member_ex``: a batch member with its own waveform (f, n_steps)
+    and field output (device pointer), each optional (NULL)."""
+    _fields_ = [("gamma_G0", ctypes.c_double * 3), ("geometry", ctypes.c_int), ("kappa_um_ms", ctypes.c_double),
+                ("f", ctypes.c_void_p), ("n_steps", ctypes.c_int64), ("field_dev", ctypes.c_void_p)]
 
 
 _lib = None
@@ -75,6 +82,7 @@ def lib():
                 "lbmbt_pgse": [D, D, D, D, P, P, ctypes.POINTER(I64), P],
                 "lbmbt_run": [P, P, P, P],
                 "lbmbt_run_batch": [P, I, P, P, P],
+                "lbmbt_run_batch_ex": [P, I, P, P, P],
                 "lbmbt_grad": [P, I, P, P, P, P],
                 "lbmbt_grad_batch": [P, I, P, I, P, P, P, P],
                 "lbmbt_set_option": [P, I, I64],
@@ -406,11 +414,41 @@ class Solver:
             arr[i].kappa_um_ms = float(kap[i])
         return arr
 
-    def run_batch(self, members, series=False):
+    def run_batch(self, members, series=False, waveforms=None, fields=None):
+        """Batched run.  ``waveforms`` (optional, one per member): the
+        member's own waveform (1-D array, at most the set sequence's length;
+        its signal is taken at its end) or None for the set one.  ``fields``
+        (optional, one per member): torch complex64 CUDA tensor [N of the
+        member's geometry] receiving M(x) at the member's end, or None.
+        Either selects ``lbmbt_run_batch_ex``."""
         n = len(members)
         sig = np.zeros(3 * n)
         ser = np.zeros(2 * n * self.n_steps) if series else None
-        self._chk(self.L.lbmbt_run_batch(self.h, n, members, _p(sig), _p(ser)), "run_batch")
+        if waveforms is None and fields is None:
+            self._chk(self.L.lbmbt_run_batch(self.h, n, members, _p(sig), _p(ser)), "run_batch")
+        else:
+            waveforms = [None] * n if waveforms is None else list(waveforms)
+            fields = [None] * n if fields is None else list(fields)
+            if len(waveforms) != n or len(fields) != n:
+                raise ValueError("one waveform and one field entry per member")
+            ex = (MemberEx * n)()
+            keep = []
+            for i in range(n):
+                m = members[i]
+                ex[i].gamma_G0[:] = list(m.gamma_G0)
+                ex[i].geometry = m.geometry
+                ex[i].kappa_um_ms = m.kappa_um_ms
+                if waveforms[i] is not None:
+                    w = np.ascontiguousarray(waveforms[i], np.float64)
+                    if w.ndim != 1 or w.size < 1:
+                        raise ValueError(f"member {i}: waveform must be a non-empty 1-D array")
+                    keep.append(w)
+                    ex[i].f = w.ctypes.data
+                    ex[i].n_steps = w.size
+                fl = _device_tensor(fields[i], "complex64", f"member {i} field", self._sites(m.geometry))
+                ex[i].field_dev = None if fl is None else (fl if isinstance(fl, int) else fl.data_ptr())
+            self._chk(self.L.lbmbt_run_batch_ex(self.h, n, ex, _p(sig), _p(ser)), "run_batch_ex")
+            del keep
         sig = sig.reshape(n, 3)
         out = {"Z": sig[:, 0] + 1j * sig[:, 1], "S": sig[:, 2].copy()}
         if series:

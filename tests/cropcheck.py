@@ -4,12 +4,15 @@ After k steps the value at a site depends only on sites within distance k
 (D3Q7 moves one site per step).  A crop of edge w around the site, with its
 far edges more than k away, therefore gives the same value, up to the global
 phase exp(-i gamma x0.G F_k) of the crop offset x0 (the reaction uses
-absolute positions).  On a periodic axis the crop is centred on the sample
-with wrapped indices (the offset may be negative: the modified periodic
-condition is exactly that quasi-periodic extension).  On a mirror axis a
-crop that reaches the low face starts there and keeps the mirror; samples
-must stay more than k sites from a high mirror face.  The crop's own edges
-are periodic and never influence the sample.
+absolute positions; the mirror rule with G normal to the face keeps that
+relation, its rewind being conjugated with the field).  On a periodic axis
+the crop is centred on the sample with wrapped indices (the offset may be
+negative: the modified periodic condition is exactly that quasi-periodic
+extension).  On a mirror axis a crop that reaches the low face starts
+there, one that reaches the high face ends there, and either keeps the
+mirror on both of its ends (the far one lies more than k sites from the
+sample).  Elsewhere the crop's own edges are periodic; they never
+influence the sample.
 """
 import numpy as np
 
@@ -31,10 +34,13 @@ def sample_values(labels, pol, bc, dx, D, T2, kappa, dt, f, gG, sites, k_steps):
                 s0 = c - h
                 cbc.append(0)
             elif c - h <= 0:
-                s0 = 0            # mirror face inside the crop
+                s0 = 0            # low mirror face inside the crop
+                cbc.append(1)
+            elif c + h >= n:
+                assert n >= w, "axis shorter than the crop"
+                s0 = n - w        # high mirror face inside the crop
                 cbc.append(1)
             else:
-                assert c + h < n, "sample too close to a high mirror face"
                 s0 = c - h
                 cbc.append(0)
             start.append(s0)

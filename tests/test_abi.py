@@ -213,3 +213,24 @@ def test_header_compiles_cleanly_as_c_and_cxx(tmp_path, lang, std):
     src.write_text('#include "lbmbt.h"\nint main(void) { return 0; }\n')
     subprocess.run([cc, std, "-Wall", "-Wextra", "-Wpedantic", "-Werror", "-fsyntax-only",
                     "-I", os.path.join(ROOT, "include"), str(src)], check=True)
+
+
+def test_member_ex_struct_layout_matches_the_c_compiler(tmp_path):
+    """The binding's lbmbt_member_ex (per-member waveform and field) has the
+    size and field offsets that the C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = ["gamma_G0", "geometry", "kappa_um_ms", "f", "n_steps", "field_dev"]
+    src = tmp_path / "layout_ex.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbmbt.h"\n'
+                   'int main(void) { printf("%zu' + ' %zu' * len(names) + '\\n", sizeof(lbmbt_member_ex)' +
+                   "".join(f", offsetof(lbmbt_member_ex, {n})" for n in names) + "); return 0; }\n")
+    exe = tmp_path / "layout_ex"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = list(map(int, subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()))
+    M = lbmbt.MemberEx
+    assert ctypes.sizeof(M) == vals[0]
+    assert [getattr(M, n).offset for n in names] == vals[1:]

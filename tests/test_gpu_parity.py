@@ -397,8 +397,9 @@ def test_signal_partials_do_not_leak_between_runs(lb):
 def test_full_size_tissue_sampled_parity(lb):
     """The benchmark workload at full size (512^3 tissue, mirror faces, three
     directions, default launch configuration = bulk-copy sweep): the field
-    after 8 steps at sampled interior, face, edge and corner sites equals the
-    oracle (crop method, cropcheck.py, pinned against full oracle runs), and
+    after 8 steps at sampled interior, face, edge and corner sites (at the
+    low and the high faces) equals the oracle (crop method, cropcheck.py,
+    pinned against full oracle runs), and
     the batched signal equals the per-direction runs."""
     import bench
     import cropcheck
@@ -408,6 +409,7 @@ def test_full_size_tissue_sampled_parity(lb):
     rng = np.random.default_rng(5)
     sites = [tuple(int(v) for v in rng.integers(20, 490, size=3)) for _ in range(6)]
     sites += [(0, 0, 0), (0, 250, 17), (300, 0, 0), (77, 1, 400), (5, 480, 0), (0, 3, 255)]
+    sites += [(511, 511, 511), (511, 250, 3), (100, 509, 506), (508, 0, 511), (2, 511, 300), (510, 7, 0)]
     idx = torch.tensor([(z * 512 + y) * 512 + x for (z, y, x) in sites], device="cuda")
     S_plain = []
     for gG, f in seqs:

@@ -397,7 +397,8 @@ def test_crop_sampling_reproduces_full_run(gdir, bc):
     gG, f = oracle.pgse(1500.0, 1.0, 2.0, dt, gdir)
     D, T2, kap = [1.0, 2.5, 3.0], [50.0, 80.0, 80.0], 0.03
     full = oracle.run(geom.labels, geom.dx, geom.phase_of_label, bc, D, T2, kap, dt, f[:k], gG, want_field=True)
-    sites = [(18, 17, 16), (0, 0, 0), (0, 20, 11), (12, 0, 25), (20, 19, 0), (2, 28, 3)]
+    sites = [(18, 17, 16), (0, 0, 0), (0, 20, 11), (12, 0, 25), (20, 19, 0), (2, 28, 3),
+             (35, 35, 35), (35, 10, 0), (4, 34, 17), (0, 35, 33), (30, 2, 35)]
     vals = cropcheck.sample_values(geom.labels, geom.phase_of_label, bc, geom.dx, D, T2, kap, dt, f, gG, sites, k)
     ref = np.array([full["field"][s] for s in sites])
     np.testing.assert_allclose(vals, ref, rtol=0, atol=1e-13)
