@@ -394,10 +394,10 @@ int lbmbt_launch_count(lbmbt_ctx* ctx, int64_t* count_out);
  *   f[n_total_steps] (host) the whole waveform, as in lbmbt_set_sequence; the
  *              call performs steps k0 .. k0 + n_steps - 1 of it;
  *   signal_out[3] (host) = {Re Z, Im Z, |Z|/N} at the end of the last step.
- * Its working data (descriptor, step word, waveform tables, per-tile signal
- * partials) lives in one fixed file-scope device array of 1,181,184 bytes
- * (1.13 MiB) that every GPU which loads the library holds until the process
- * exits.  Limits: N <= 16,777,216 sites and n_total_steps <= 32,768; larger
+ * Its working data (descriptor, step word, waveform and boundary-factor
+ * tables, per-tile signal partials) lives in one fixed file-scope device
+ * array of 2,754,304 bytes (2.63 MiB) that every GPU which loads the library
+ * holds until the process exits.  Limits: N <= 16,777,216 sites and n_total_steps <= 32,768; larger
  * inputs are rejected with LBMBT_EINVAL and a message in errbuf (errbuf may
  * be NULL).  Every phase id in the mask (bits 6-7) must be < n_phases, else
  * LBMBT_ESTATE before the state is touched.  The library cannot see the

@@ -107,10 +107,9 @@ struct lbmbt_ctx {
     size_t cap_desc = 0, cap_ts = 0;
     double2* d_partial = nullptr;
     size_t cap_partial = 0;
-    float2* d_fac = nullptr;      // [2][n_members][6] boundary factors
-    size_t cap_fac = 0;
-    float2* d_ftab = nullptr;     // adjoint: [K+1][n_members][6]
+    float2* d_ftab = nullptr;     // boundary factors of every step, [K+1][n_members][6]
     size_t cap_ftab = 0;
+    bool ftab_valid = false;      // d_ftab holds the prepared members' factors
     float2* d_etab = nullptr;     // per-member rotation tables
     size_t cap_etab = 0;
     float2* d_halo = nullptr;     // slab halo planes, [member][2][nx*ny]
@@ -262,7 +261,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaFree(c->d_f); cudaFree(c->d_F);
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
-    cudaFree(c->d_fac); cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab);
+    cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab);
     cudaFree(c->d_adj_unit_start); cudaFree(c->d_halo);
     cudaFree(c->d_ck); cudaFree(c->d_seg); cudaFree(c->d_gacc); cudaFree(c->d_gout); cudaFree(c->d_laminit);
     if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
@@ -334,6 +333,7 @@ static int make_geom(lbmbt_ctx* c, int nx, int ny, int nz, double dx, const int3
 static void invalidate_run(lbmbt_ctx* c)
 {
     c->prepared = false;
+    c->ftab_valid = false;
     drop_graph(c);
 }
 
@@ -658,6 +658,12 @@ static bool tma_eligible(const lbmbt_ctx* c)
     return true;
 }
 
+// Offset into the F_k tables of the boundary-factor table: the
+// hybrid scheme streams before step k's reaction (F_k); the classical
+// scheme's streamed populations already hold step k's source, so its faces
+// take F_(k+1).
+static int ctl_F_shift(const lbmbt_ctx* c) { return c->scheme == 1 ? 1 : 0; }
+
 static int build_worklist(lbmbt_ctx* c, int block, int spt)
 {
     const long long tile = (long long)block * spt;
@@ -729,10 +735,22 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     if (!rc) rc = grow(c, &c->d_unit_start, &c->cap_us, sizeof(long long) * (c->n_members + 1));
     if (!rc) rc = grow(c, &c->d_adj_unit_start, &c->cap_aus, sizeof(long long) * (c->n_members + 1));
     if (!rc) rc = grow(c, &c->d_partial, &c->cap_partial, sizeof(double2) * n_part);
-    if (!rc) rc = grow(c, &c->d_fac, &c->cap_fac, sizeof(float2) * 12 * c->n_members);
     if (rc) return rc;
     CU(c, cudaMemcpyAsync(c->d_desc, c->descs.data(), sizeof(MemberDesc) * c->n_members, cudaMemcpyHostToDevice,
                           c->stream));
+    if (!c->ftab_valid) {
+        // FP64 boundary factors of every step for every member, once per run
+        // (the sweeps and the adjoint read them by step index)
+        const size_t tb = sizeof(float2) * 6 * (size_t)(c->n_steps + 1) * c->n_members;
+        if (tb > (4ull << 30))
+            return fail(c, LBMBT_ENOMEM, "boundary-factor table of %zu bytes (steps x members too large; split the "
+                                         "batch)", tb);
+        rc = grow(c, &c->d_ftab, &c->cap_ftab, tb);
+        if (rc) return rc;
+        CU(c, launch_factor_table(c->d_desc, c->n_members, ctl_F_shift(c), c->n_steps, c->d_ftab, c->stream));
+        c->launches++;
+        c->ftab_valid = true;
+    }
     CU(c, cudaMemcpyAsync(c->d_tile_start, c->tile_start.data(), sizeof(long long) * (c->n_members + 1),
                           cudaMemcpyHostToDevice, c->stream));
     CU(c, cudaMemcpyAsync(c->d_unit_start, c->unit_start.data(), sizeof(long long) * (c->n_members + 1),
@@ -760,7 +778,7 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.F = c->d_F;
     a.scheme = c->scheme;
     a.partial = c->d_partial;
-    a.fac = c->d_fac;
+    a.fac = c->d_ftab;
     a.links = 0;
     for (auto& d : c->descs) {
         if (d.dth) a.links = 2;
@@ -779,11 +797,6 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     return a;
 }
 
-// Offset into the F_k tables of the control kernel's boundary factors: the
-// hybrid scheme streams before step k's reaction (F_k); the classical
-// scheme's streamed populations already hold step k's source, so its faces
-// take F_(k+1).
-static int ctl_F_shift(const lbmbt_ctx* c) { return c->scheme == 1 ? 1 : 0; }
 
 static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base = 0, int slot_mod = 2)
 {
@@ -796,7 +809,7 @@ static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base =
     h.slot_mod = slot_mod;
     h.series = c->series_mode ? 1 : 0;
     h.err = 0;
-    CU(c, launch_ctl(c->d_ctl, h, 1, c->d_desc, c->n_members, ctl_F_shift(c), c->d_fac, c->stream));
+    CU(c, launch_ctl_set(c->d_ctl, h, c->stream));
     c->launches++;
     return LBMBT_OK;
 }
@@ -810,8 +823,8 @@ static int init_state(lbmbt_ctx* c)
     return LBMBT_OK;
 }
 
-// Issue one step: sweep, then the control kernel (k += 1 and the next step's
-// boundary factors), plus the per-step reduce in series mode.
+// Issue one step: the sweep (its last block advances the step word), plus
+// the per-step reduce in series mode.
 static int issue_step(lbmbt_ctx* c)
 {
     SweepArgs a = sweep_args(c);
@@ -822,10 +835,7 @@ static int issue_step(lbmbt_ctx* c)
     } else {
         CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
     }
-    StepCtl none;
-    memset(&none, 0, sizeof none);
-    CU(c, launch_ctl(c->d_ctl, none, 0, c->d_desc, c->n_members, ctl_F_shift(c), c->d_fac, c->stream));
-    c->launches += 2;
+    c->launches += 1;
     if (c->series_mode) {
         CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
                             c->stream));
@@ -1172,7 +1182,7 @@ static int advance(lbmbt_ctx* c, long long n, bool want_signal)
             rc = capture_graph(c);
             if (rc) return rc;
         }
-        const int per = c->series_mode ? 3 : 2;
+        const int per = c->series_mode ? 2 : 1;
         while (left >= GRAPH_CHUNK) {
             CU(c, cudaGraphLaunch(c->graph, c->stream));
             c->launches += GRAPH_CHUNK * per;
@@ -1546,10 +1556,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
         if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
         adj_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_adj_units);
     }
-    if ((rc = grow(c, &c->d_ftab, &c->cap_ftab, sizeof(float2) * 6 * (size_t)(K + 1) * n))) return rc;
-    CU(c, launch_factor_table(c->d_desc, n, c->d_F, K, c->d_ftab, c->stream));
-    c->launches++;
-    AdjointArgs aa;
+    AdjointArgs aa;   // the boundary factors of every step: the forward's table
     aa.members = c->d_desc;
     aa.tile_start = c->d_tile_start;
     aa.n_members = n;

@@ -88,13 +88,13 @@ struct MemberDesc {
     int end_step;
 };
 
-// Step control word in device memory.  The sweep reads k here; a one-block
-// control kernel between sweeps advances it and prepares the next step's
-// boundary factors, so a captured graph of (sweep, control) pairs replays
-// from any step.  No kernel ever waits on it.
+// Step control word in device memory.  Every block of a sweep reads k at its
+// start; the last block to finish (a ticket on `done`, no waiting) advances
+// k, so a captured graph of sweeps replays from any step.  No kernel ever
+// waits on it.
 struct StepCtl {
     int k;              // step index the next sweep performs
-    unsigned done;      // unused (kept zero)
+    unsigned done;      // blocks of the current sweep that have finished (0 between sweeps)
     int sig_step;       // step whose end signal is reduced (-1: none)
     int field_step;     // step whose end field is written (-1: none)
     int slot_base;      // src slot = (k - slot_base) % slot_mod
@@ -111,7 +111,7 @@ struct SweepArgs {
     const float* f;               // waveform per step
     const double* F;              // F_k = sum_{m<k} f_m dt, per step
     double2* partial;             // per-tile (sum Re M, sum Im M)
-    const float2* fac;            // [2][n_members][6] boundary factors, level k & 1
+    const float2* fac;            // [K+1][n_members][6] boundary factors of every step
     int links;                    // 1: a member has membrane positions (register sweep
                                   // variant with the Eqs. B4a-B4c rule); 2: and angles
     float w0, wxy, wz;            // equilibrium weights (register sweep, init):
@@ -127,13 +127,13 @@ struct SweepArgs {
 cudaError_t launch_build_mask(const int32_t* labels, const uint8_t* phase_of_label, int n_labels,
                               int nx, int ny, int nz, const int bc[3], uint8_t* mask, int* err,
                               cudaStream_t st);
-// set != 0: write v to the control word; else advance k by one.  Then compute
-// the boundary factors of the (new) step k for every member into fac[k & 1],
-// from the member's F table at k + F_shift (1 for the classical scheme).
-cudaError_t launch_ctl(StepCtl* ctl, const StepCtl& v, int set, const MemberDesc* members, int n_members,
-                       int F_shift, float2* fac, cudaStream_t st);
-// Boundary factors of every step 0..K for every member: table[k][m][6].
-cudaError_t launch_factor_table(const MemberDesc* members, int n_members, const double* F, long long K,
+// Writes v to the control word (before a run of sweeps, which then advance
+// it themselves).
+cudaError_t launch_ctl_set(StepCtl* ctl, const StepCtl& v, cudaStream_t st);
+// Boundary factors of every step 0..K for every member, table[k][m][6], from
+// each member's F table at k + F_shift (1 for the classical scheme, whose
+// streamed populations already hold step k's source).
+cudaError_t launch_factor_table(const MemberDesc* members, int n_members, int F_shift, long long K,
                                 float2* table, cudaStream_t st);
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot,
                         cudaStream_t st);

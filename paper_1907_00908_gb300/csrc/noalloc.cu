@@ -7,7 +7,8 @@
 // that forbids allocation after start-up).  This entry point runs the same
 // kernels as lbmbt_run on buffers the caller already owns (mask, state) and
 // keeps its own small working data -- member descriptor, tile prefix, step
-// control word, waveform tables, per-tile signal partials -- in one
+// control word, waveform and boundary-factor tables, per-tile signal
+// partials -- in one
 // file-scope __device__ array of fixed size, which every GPU that loads the
 // library holds until the process exits.
 #include <cmath>
@@ -36,17 +37,17 @@ constexpr size_t OFF_DESC = 256;
 constexpr size_t OFF_TS = 768;
 constexpr size_t OFF_Z = 1024;
 constexpr size_t OFF_PH = 1056;                      // largest phase id in the caller's mask
-constexpr size_t OFF_FAC = 1088;                     // [2][1][6] boundary factors
 constexpr size_t OFF_F64 = 1280;
 constexpr size_t OFF_F32 = OFF_F64 + NA_MAX_STEPS * sizeof(double);
 constexpr size_t OFF_FCUM = OFF_F32 + NA_MAX_STEPS * sizeof(float);
-constexpr size_t OFF_PART = (OFF_FCUM + (NA_MAX_STEPS + 1) * sizeof(double) + 255) / 256 * 256;
+// boundary factors of every step, [K+1][1][6]
+constexpr size_t OFF_FTAB = (OFF_FCUM + (NA_MAX_STEPS + 1) * sizeof(double) + 255) / 256 * 256;
+constexpr size_t OFF_PART = (OFF_FTAB + (NA_MAX_STEPS + 1) * 6 * sizeof(float2) + 255) / 256 * 256;
 constexpr size_t NA_SCRATCH_BYTES = OFF_PART + NA_MAX_TILES * sizeof(double2);
 static_assert(sizeof(StepCtl) <= OFF_DESC - OFF_CTL, "control word does not fit");
 static_assert(sizeof(MemberDesc) <= OFF_TS - OFF_DESC, "descriptor does not fit");
-static_assert(OFF_FAC + 12 * sizeof(float2) <= OFF_F64, "factors do not fit");
-// 1,181,184 bytes (1.13 MiB), the figure the header states
-static_assert(NA_SCRATCH_BYTES == 1181184, "scratch size differs from the documented figure");
+// 2,754,304 bytes (2.63 MiB), the figure the header states
+static_assert(NA_SCRATCH_BYTES == 2754304, "scratch size differs from the documented figure");
 
 // The scratch.  Host code must not pass `na_scratch` itself to a kernel: on
 // the host it names a stand-in object, not device memory.  Its device address
@@ -242,20 +243,19 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.f = reinterpret_cast<const float*>(base + OFF_F32);
     a.F = reinterpret_cast<const double*>(base + OFF_FCUM);
     a.partial = reinterpret_cast<double2*>(base + OFF_PART);
-    float2* fac = reinterpret_cast<float2*>(base + OFF_FAC);
-    a.fac = fac;
+    float2* ftab = reinterpret_cast<float2*>(base + OFF_FTAB);
+    a.fac = ftab;
     a.links = 0;
     a.w0 = W0; a.wxy = WI; a.wz = WI;   // D3Q7
     a.scheme = 0;                       // the hybrid scheme
     MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
     // control word (done counter and step start from the values above every
-    // call) and the first step's boundary factors
-    if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 1, dd, 1, 0, fac, st);
+    // call; each sweep's last block advances the step) and the boundary
+    // factors of every step of the waveform
+    if (e == cudaSuccess) e = launch_ctl_set(a.ctl, c, st);
+    if (e == cudaSuccess) e = launch_factor_table(dd, 1, 0, n_total_steps, ftab, st);
     if (e == cudaSuccess && init) e = launch_init(a, n_tiles, NA_BLOCK, NA_SPT, 0, st);
-    for (long long k = 0; e == cudaSuccess && k < n_steps; ++k) {
-        e = launch_sweep(a, n_tiles, NA_BLOCK, NA_SPT, st);
-        if (e == cudaSuccess) e = launch_ctl(a.ctl, c, 0, dd, 1, 0, fac, st);
-    }
+    for (long long k = 0; e == cudaSuccess && k < n_steps; ++k) e = launch_sweep(a, n_tiles, NA_BLOCK, NA_SPT, st);
     double2* Zd = reinterpret_cast<double2*>(base + OFF_Z);
     if (e == cudaSuccess) e = launch_reduce(a.partial, a.tile_start, 1, 1, Zd, nullptr, 0, a.ctl, st);
     double2 Z = make_double2(0.0, 0.0);

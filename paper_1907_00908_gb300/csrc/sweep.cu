@@ -19,8 +19,9 @@
 //  * sweep_classical_kernel: the same pass for the classical LBM (Appendix A,
 //        Eq. A12): stream + BCs + membrane, M = sum_i g_i, collision with
 //        the reaction as a source term; no reaction step
-//  * ctl_kernel        : sets / advances the step word between sweeps and
-//                        computes the next step's FP64 boundary factors
+//  * ctl_set_kernel    : sets the step word before a run of sweeps (each
+//                        sweep's last block advances it)
+//  * factor_table_kernel: FP64 boundary factors of every step, once per run
 //  * reduce_kernel     : fixed-order FP64 sum of the per-tile partials.
 //
 // The work list of a launch is the concatenation of all members' tiles; a
@@ -139,7 +140,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
     const bool do_sig = __ldcg(&a.ctl->series) || k == (es >= 0 ? es : __ldcg(&a.ctl->sig_step));
     float2* const field = sd->field;
     const bool do_field = k == (es >= 0 ? es : __ldcg(&a.ctl->field_step)) && field != nullptr;
-    const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + m) * 6;
+    const float2* __restrict__ fac = a.fac + ((size_t)k * a.n_members + m) * 6;
 
     // classical: the collision of this pass carries the source of step k+1
     const float fk = __ldg(sd->fw + k + (CLS ? 1 : 0));
@@ -317,6 +318,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
             if (l == 0) a.partial[blockIdx.x] = v;
         }
     }
+    // every thread of the block is past its use of the step word
+    __syncthreads();
+    if (threadIdx.x == 0) step_done(a.ctl, k, gridDim.x);
 }
 
 template <int SPT>
@@ -341,32 +345,19 @@ __global__ void __launch_bounds__(512, ANG ? 1 : 2) sweep_links_kernel(const Swe
     sweep_body<SPT, ANG ? 2 : 1>(a);
 }
 
-// Control word: set (or advance k), then the boundary factors of the new step
-// for every member, in FP64 (one block; members strided over its threads).
-__global__ void ctl_kernel(StepCtl* ctl, StepCtl v, int set, const MemberDesc* __restrict__ members,
-                           int n_members, int F_shift, float2* __restrict__ fac)
-{
-    __shared__ int sk;
-    if (threadIdx.x == 0) {
-        if (set) *ctl = v;
-        else ctl->k = ctl->k + 1;
-        sk = ctl->k;
-    }
-    __syncthreads();
-    const int k = sk;
-    for (int m = threadIdx.x; m < n_members; m += blockDim.x)
-        boundary_factors6(members[m], members[m].Fw[k + F_shift], fac + ((size_t)(k & 1) * n_members + m) * 6);
-}
+// Control word: set before a run of sweeps.
+__global__ void ctl_set_kernel(StepCtl* ctl, StepCtl v) { *ctl = v; }
 
-// Boundary factors of all steps 0..K (adjoint sweep): table[k][m][6].
-__global__ void factor_table_kernel(const MemberDesc* __restrict__ members, int n_members,
-                                    const double* __restrict__ F, long long K, float2* __restrict__ table)
+// Boundary factors of all steps 0..K, in FP64 from each member's F_k:
+// table[k][m][6] (forward sweeps and adjoint sweeps).
+__global__ void factor_table_kernel(const MemberDesc* __restrict__ members, int n_members, int F_shift, long long K,
+                                    float2* __restrict__ table)
 {
     const long long n = (K + 1) * n_members;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const long long k = t / n_members;
         const int m = (int)(t - k * n_members);
-        boundary_factors6(members[m], F[k], table + t * 6);
+        boundary_factors6(members[m], members[m].Fw[k + F_shift], table + t * 6);
     }
 }
 
@@ -400,20 +391,19 @@ __global__ void reduce_kernel(const double2* __restrict__ partial, const long lo
 
 }  // namespace
 
-cudaError_t launch_ctl(StepCtl* ctl, const StepCtl& v, int set, const MemberDesc* members, int n_members,
-                       int F_shift, float2* fac, cudaStream_t st)
+cudaError_t launch_ctl_set(StepCtl* ctl, const StepCtl& v, cudaStream_t st)
 {
-    ctl_kernel<<<1, 256, 0, st>>>(ctl, v, set, members, n_members, F_shift, fac);
+    ctl_set_kernel<<<1, 1, 0, st>>>(ctl, v);
     return cudaGetLastError();
 }
 
-cudaError_t launch_factor_table(const MemberDesc* members, int n_members, const double* F, long long K,
+cudaError_t launch_factor_table(const MemberDesc* members, int n_members, int F_shift, long long K,
                                 float2* table, cudaStream_t st)
 {
     const long long n = (K + 1) * n_members;
     long long grid = (n + 255) / 256;
     if (grid > 152LL * 32) grid = 152LL * 32;
-    factor_table_kernel<<<(unsigned)grid, 256, 0, st>>>(members, n_members, F, K, table);
+    factor_table_kernel<<<(unsigned)grid, 256, 0, st>>>(members, n_members, F_shift, K, table);
     return cudaGetLastError();
 }
 

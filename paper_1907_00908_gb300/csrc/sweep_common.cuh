@@ -232,6 +232,21 @@ __device__ __forceinline__ float2 source_dtRM(float ep, float th, float mr, floa
     return make_float2(__fmaf_rn(-ep, mr, __fmul_rn(-th, mi)), __fmaf_rn(-ep, mi, __fmul_rn(th, mr)));
 }
 
+// End of a sweep for one block (or CTA): take a ticket; the last of the
+// launch's `nblocks` advances the step word and clears the counter for the
+// next sweep.  Every block has read k before it takes its ticket, so no
+// block can see the new value.  The caller has made its own threads finish
+// with the step word before calling (one thread per block calls).
+__device__ __forceinline__ void step_done(StepCtl* ctl, int k, unsigned nblocks)
+{
+    __threadfence();
+    if (atomicAdd(&ctl->done, 1u) == nblocks - 1u) {
+        __threadfence();
+        ctl->done = 0u;
+        ctl->k = k + 1;
+    }
+}
+
 // boundary_factors() into a flat [6] array: index 2*axis + (0 low, 1 high).
 __device__ __forceinline__ void boundary_factors6(const MemberDesc& sd, double F, float2* out6)
 {

@@ -164,6 +164,9 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         s_abort = 0;
     }
     __syncthreads();
+    // every thread of this CTA has read the step word: take the CTA's ticket
+    // (the last CTA of the launch advances it for the next sweep)
+    if (tid == 0) step_done(a.ctl, k, gridDim.x);
 
     if (tid >= TMA_CONSUMERS) {
         // ---------------- producer warp (lane 0 issues)
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         const float2* __restrict__ r5 = stage_plane(sb, cap, 5);
         const float2* __restrict__ r6 = stage_plane(sb, cap, 6);
         const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx, OZ);
-        const float2* __restrict__ fac = a.fac + ((size_t)(k & 1) * a.n_members + G.m) * 6;
+        const float2* __restrict__ fac = a.fac + ((size_t)k * a.n_members + G.m) * 6;
         float2* __restrict__ dst = dstb;
         const int z = G.z;
 
