@@ -12,6 +12,14 @@ A "step" is one time step of the whole batch: every site of the lattice
 updated once for each of the 3 directions.  value = MLUPS = sites x members x
 steps / s.  Inputs (15 GB of state per direction) are far larger than L2.
 
+The same JSON line carries, each timed on its own on the same GPU, the
+forms the metric compares: ``plain_single_direction`` (one member on the
+128^3 permeable cylinders), ``batched`` (528 members on 17 geometries, one
+launch per step), ``adjoint`` (the gradient of S for 60 members of a 96^3
+sphere pack over a 400-step prefix of its schedule, against a forward run)
+and ``adjoint_full_schedule`` (the same over all 6400 steps, with the
+member groups the checkpoints needed).
+
 ``--impl reference`` times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload on the host cores.
 """
@@ -274,107 +282,189 @@ def batch_workload(seed=7):
     return cyl, packs, members, f
 
 
-def run_batch(args):
+def _timed_advance(solver, stream, members, steps, warmup, want_signal=True):
+    """Prepare ``members``, advance ``warmup`` steps, then time ``steps``
+    steps with CUDA events on ``stream`` (nvidia-smi sampling around them).
+    Returns (ms per step, clocks summary, signals)."""
     import torch
+    solver.prepare(members)
+    solver.advance(warmup)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sig = solver.advance(steps, want_signal=want_signal, n_members=len(members))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, clk.summary(), sig
+
+
+def _launch_shape(s, lbmbt):
+    return {"kernel": "bulk-copy" if s.get_option(lbmbt.OPT_KERNEL_USED) == 2 else "register",
+            "tma_shape": s.get_option(lbmbt.OPT_TMA_SHAPE), "stages": s.get_option(lbmbt.OPT_STAGES),
+            "block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT)}
+
+
+def _hbm_roofline(mlups, bytes_per_site, kernel):
+    peak, peak_kind = peaks()
+    achieved = mlups * 1e6 * bytes_per_site / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "bytes_per_site_member": bytes_per_site, "kernel": kernel}
+
+
+PLAIN_C2_STEPS, PLAIN_C2_WARMUP = 4000, 50   # 0.2 s timed: a 56 us step needs many for a stable figure
+
+
+def measure_plain_c2(args, stream):
+    """The plain single-direction sweep on the two-phase permeable-cylinder
+    workload: 128^3 at dx 0.5 um, D 2.0/1.0, T2 80/50, kappa 0.02 um/ms,
+    PGSE b 1000 s/mm^2 along x, delta 10 / Delta 30 ms, one member,
+    autotuned launch, timed over 4000 of its 6400 steps (a step takes
+    about 50 us, so a 20-step region is dominated by fixed costs)."""
+    from paper_1907_00908_gb300 import lbmbt, synth
+    geom = synth.cylinders(128, 0.5, seed=1)
+    gG, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, C2_DT, (1, 0, 0))
+    s = lbmbt.Solver(0, stream)
+    s.set_option(lbmbt.OPT_AUTOTUNE, 0 if args.no_autotune else 1)
+    s.set_geometry(geom.labels, geom.phase_of_label, 0.5)
+    s.set_phases(C2_D, C2_T2)
+    s.set_sequence(C2_DT, f, gG)
+    ms, clk, _ = _timed_advance(s, stream, lbmbt.Solver.members([gG], 0, C2_KAPPA), PLAIN_C2_STEPS,
+                                PLAIN_C2_WARMUP)
+    shape = _launch_shape(s, lbmbt)
+    s.close()
+    v = geom.n_sites / (ms * 1e-3) / 1e6
+    return {"value": v, "unit": "MLUPS", "ms_per_step": ms, "steps": PLAIN_C2_STEPS, "warmup": PLAIN_C2_WARMUP,
+            "workload": "128^3 permeable cylinders, dx 0.5 um, 1 member (PGSE b 1000 along x)",
+            "l2": "state of 235 MB per time level pair, larger than L2; no flush needed",
+            "launch": shape, "roofline": _hbm_roofline(v, BYTES_PER_SITE, "sweep (" + shape["kernel"] + ")"),
+            "clocks": clk}
+
+
+def measure_batch(args, stream):
+    """The batched workload: 64 directions x 8 b-values on the 128^3
+    cylinders plus 16 sphere packs of uneven edges, 528 members in one
+    launch per step, autotuned launch."""
     from paper_1907_00908_gb300 import lbmbt
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
     cyl, packs, members, f = batch_workload()
+    t_gen = time.perf_counter() - t0
     s = lbmbt.Solver(0, stream)
     s.set_option(lbmbt.OPT_STAGE_OWN_Z, args.stage_own_z)
+    s.set_option(lbmbt.OPT_AUTOTUNE, 0 if args.no_autotune else 1)
     s.set_geometry(cyl.labels, cyl.phase_of_label, 0.5)
     for g in packs:
         s.add_geometry(g.labels, g.phase_of_label, 0.5)
     s.set_phases(C2_D, C2_T2)
     s.set_sequence(C2_DT, f, members[0][0])
     mem = lbmbt.Solver.members([m[0] for m in members], [m[1] for m in members], [m[2] for m in members])
-    sites = [cyl.n_sites] * 512 + [g.n_sites for g in packs]
-    total_sites = float(sum(sites))
-
-    def timed(solver, mems, steps, warm):
-        solver.prepare(mems)
-        solver.advance(warm)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        solver.advance(steps, want_signal=True, n_members=len(mems))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
-
-    with Clocks(0) as clk:
-        ms_batch = timed(s, mem, args.steps, args.warmup)
-    kernel = s.get_option(lbmbt.OPT_KERNEL_USED)
-    one = lbmbt.Solver.members([members[5][0]], 0, C2_KAPPA)
-    ms_plain = timed(s, one, args.steps, args.warmup)
+    total_sites = float(cyl.n_sites * 512 + sum(g.n_sites for g in packs))
+    ms, clk, _ = _timed_advance(s, stream, mem, args.steps, args.warmup)
+    shape = _launch_shape(s, lbmbt)
     s.close()
-    peak, peak_kind = peaks()
-    v = total_sites / (ms_batch * 1e-3) / 1e6
-    vp = cyl.n_sites / (ms_plain * 1e-3) / 1e6
-    line = {"metric": "MLUPS (batched sweep, FP32, 528 members)", "value": v, "unit": "MLUPS", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch_c3_128cyl_64dirx8b_plus_16_packs", "members": len(members),
-                       "sites_per_step": total_sites, "pack_edges": [int(g.shape[0]) for g in packs],
-                       "kernel": "bulk-copy" if kernel == 2 else "register"},
-            "plain_single_direction": {"value": vp, "unit": "MLUPS", "ms_per_step": ms_plain,
-                                       "workload": "128^3 cylinders, 1 member"},
-            "batched_over_plain": v / vp,
-            "roofline": {"bound": "hbm", "achieved": v * 1e6 * BYTES_PER_SITE / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": v * 1e6 * BYTES_PER_SITE / 1e9 / peak, "peak_source": peak_kind},
-            "clocks": clk.summary()}
+    v = total_sites / (ms * 1e-3) / 1e6
+    return {"value": v, "unit": "MLUPS", "ms_per_step": ms, "steps": args.steps,
+            "workload": "batch_528: 64 directions x 8 b-values on the 128^3 cylinders + 16 sphere packs "
+                        "(edges 48-160, dx 0.5 um, kappa U(0, 0.05) um/ms)",
+            "members": len(members), "sites_per_step": total_sites,
+            "pack_edges": [int(g.shape[0]) for g in packs], "geometry_gen_s": round(t_gen, 1),
+            "launch": shape, "roofline": _hbm_roofline(v, BYTES_PER_SITE, "sweep (" + shape["kernel"] + ")"),
+            "clocks": clk}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    b = measure_batch(args, stream)
+    p = measure_plain_c2(args, stream)
+    line = {"metric": "MLUPS (batched sweep, FP32, 528 members)", "value": b["value"], "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_c3_128cyl_64dirx8b_plus_16_packs", "members": b["members"],
+                       "sites_per_step": b["sites_per_step"], "pack_edges": b["pack_edges"],
+                       "launch": b["launch"]},
+            "plain_single_direction": p, "batched_over_plain": b["value"] / p["value"],
+            "roofline": b["roofline"], "clocks": b["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ---------------------------------------------------------------- adjoint (c4)
-def run_adjoint(args):
-    import torch
+def adjoint_workload(n_members=60):
+    """96^3 two-phase sphere pack (dx 0.5 um, radii U(2, 6) um, fraction
+    0.5), 30 seeded directions x b in {1000, 2500} s/mm^2, PGSE delta 10 /
+    Delta 30 ms."""
     from paper_1907_00908_gb300 import lbmbt, synth
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
     geom = synth.spheres(96, 0.5, rmin=2.0, rmax=6.0, fraction=0.5, seed=4)
     dirs = synth.directions_on_sphere(30, seed=11)
-    gGs = []
-    for b in (1000.0, 2500.0):
-        for d in dirs:
-            gGs.append(lbmbt.pgse(b, C2_DELTA, C2_BIG_DELTA, C2_DT, d)[0])
-    gGs = gGs[:args.members]
+    gGs = [lbmbt.pgse(b, C2_DELTA, C2_BIG_DELTA, C2_DT, d)[0] for b in (1000.0, 2500.0) for d in dirs]
     _, f = lbmbt.pgse(1000.0, C2_DELTA, C2_BIG_DELTA, C2_DT, (1, 0, 0))
-    K = args.steps
-    f = f[:K]
+    return geom, gGs[:n_members], f
+
+
+def measure_adjoint(args, stream, K=None):
+    """Gradient of S with respect to D, T2 and kappa for every member of the
+    adjoint workload (forward with checkpoints every 64 steps, recomputed
+    segments, reverse sweep), over the first K steps of the 6400-step
+    schedule (all of it when K is None), against a forward run of the same
+    members and steps.  Both timed with CUDA events on ``stream``."""
+    import torch
+    from paper_1907_00908_gb300 import lbmbt
+    geom, gGs, f = adjoint_workload(args.members)
+    if K is not None:
+        f = f[:K]
+    K = len(f)
     s = lbmbt.Solver(0, stream)
     s.set_geometry(geom.labels, geom.phase_of_label, 0.5)
     s.set_phases(C2_D, C2_T2)
     s.set_sequence(C2_DT, f, gGs[0])
     s.set_option(lbmbt.OPT_ADJOINT_SHAPE, args.adj_shape)
     mem = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
-    s.grad_batch(lbmbt.Solver.members(gGs[:2], 0, C2_KAPPA), checkpoint_every=64)  # warm-up
+    s.grad_batch(lbmbt.Solver.members(gGs[:2], 0, C2_KAPPA), checkpoint_every=64)   # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(0) as clk:
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e0.record(stream)
         g = s.grad_batch(mem, checkpoint_every=64)
+        e1.record(stream)
         torch.cuda.synchronize()
-        t_grad = time.perf_counter() - t0
+    t_grad = e0.elapsed_time(e1) * 1e-3
+    groups = s.get_option(lbmbt.OPT_GRAD_GROUPS)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    r = s.run_batch(mem)
+    e0.record(stream)
+    s.run_batch(mem)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
+    t_fwd = e0.elapsed_time(e1) * 1e-3
     s.close()
     work = geom.n_sites * len(gGs) * K
-    line = {"metric": "MLUPS-equivalent (gradient of S wrt D, T2, kappa; forward + checkpointed adjoint)",
-            "value": work / t_grad / 1e6, "unit": "MLUPS", "n_gpus": 1, "steps": K, "warmup": 1,
-            "ms_per_step": 1e3 * t_grad / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "adjoint_c4_96pack_30dirx2b", "members": len(gGs), "checkpoint_every": 64,
-                       "sites": geom.n_sites, "steps_of_schedule": K},
+    return {"value": work / t_grad / 1e6, "unit": "MLUPS-equivalent", "seconds": t_grad, "steps": K,
+            "ms_per_step": 1e3 * t_grad / K,
+            "workload": f"adjoint_60: 96^3 sphere pack, {len(gGs)} members (30 directions x b 1000, 2500), "
+                        "checkpoint every 64 steps",
+            "members": len(gGs), "member_groups": groups,
             "plain_forward": {"value": work / t_fwd / 1e6, "unit": "MLUPS", "seconds": t_fwd},
             "gradient_over_forward_time": t_grad / t_fwd,
             "sample_gradient_member0": {"S": float(g["S"][0]), "dS_dD": g["dD"][0].tolist(),
                                         "dS_dT2": g["dT2"][0].tolist(), "dS_dkappa": float(g["dkappa"][0])},
             "clocks": clk.summary()}
+
+
+def run_adjoint(args):
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    a = measure_adjoint(args, stream, args.adj_steps)
+    line = {"metric": "MLUPS-equivalent (gradient of S wrt D, T2, kappa; forward + checkpointed adjoint)",
+            "value": a["value"], "unit": "MLUPS", "n_gpus": 1, "steps": a["steps"], "warmup": 1,
+            "ms_per_step": a["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "adjoint_c4_96pack_30dirx2b", "members": a["members"], "checkpoint_every": 64,
+                       "steps_of_schedule": a["steps"], "member_groups": a["member_groups"]},
+            "plain_forward": a["plain_forward"], "gradient_over_forward_time": a["gradient_over_forward_time"],
+            "sample_gradient_member0": a["sample_gradient_member0"], "clocks": a["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -749,6 +839,12 @@ def main():
     ap.add_argument("--stage-own-z", type=int, default=0, choices=[0, 1, 2],
                     help="bulk-copy sweep: own z rows 0 auto, 1 prefetched into registers, 2 staged")
     ap.add_argument("--members", type=int, default=60, help="adjoint workload: number of members (<= 60)")
+    ap.add_argument("--adj-steps", type=int, default=400,
+                    help="adjoint workload: steps of the 6400-step schedule timed (the prefix)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the plain 128^3, batched and adjoint figures")
+    ap.add_argument("--no-adjoint-full", action="store_true",
+                    help="skip the full-schedule (6400-step) adjoint figure of the default run")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
@@ -874,6 +970,21 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(geom, seqs)
 
+    # the other forms the metric compares on the same GPU, each timed on its
+    # own: the plain single-direction sweep on the 128^3 cylinders, the
+    # 528-member batch, and the adjoint (a 400-step prefix and the full
+    # 6400-step schedule of its 60 members)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        del geom
+        extras["plain_single_direction"] = measure_plain_c2(args, stream)
+        b = measure_batch(args, stream)
+        b["batched_over_plain"] = b["value"] / extras["plain_single_direction"]["value"]
+        extras["batched"] = b
+        extras["adjoint"] = measure_adjoint(args, stream, args.adj_steps)
+        if not args.no_adjoint_full:
+            extras["adjoint_full_schedule"] = measure_adjoint(args, stream, None)
+
     if rank == 0:
         tr = traffic_per_launch()
         line = {
@@ -894,6 +1005,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -339,7 +339,7 @@ enum {
                                 staged (2 more rows per stage slot)            */
     LBMBT_OPT_STAGE_OWN_Z_USED = 13, /* read-only: 1 prefetched or 2 staged for a
                                 prepared bulk-copy run, else 0                 */
-    LBMBT_OPT_SCHEME = 14    /* 0 (default) the hybrid scheme (Eq.
+    LBMBT_OPT_SCHEME = 14,   /* 0 (default) the hybrid scheme (Eq.
                                 LBM_process_list_2); 1 the paper's comparison
                                 scheme, the classical LBM with the reaction as
                                 a source term in the collision (Appendix A,
@@ -353,6 +353,10 @@ enum {
                                 (positions: EUNSUPPORTED), no reaction
                                 sub-steps (EINVAL), no slabs and no adjoint
                                 (EUNSUPPORTED); both lattices              */
+    LBMBT_OPT_GRAD_GROUPS = 15 /* read-only: the number of groups the last
+                                lbmbt_grad_batch split its members into so
+                                that one group's checkpoints fit in the free
+                                device memory (0 before any)              */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

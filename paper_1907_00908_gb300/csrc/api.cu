@@ -110,6 +110,7 @@ struct lbmbt_ctx {
     float2* d_ftab = nullptr;     // boundary factors of every step, [K+1][n_members][6]
     size_t cap_ftab = 0;
     bool ftab_valid = false;      // d_ftab holds the prepared members' factors
+    int grad_groups = 0;          // member groups of the last lbmbt_grad_batch
     float2* d_etab = nullptr;     // per-member rotation tables
     size_t cap_etab = 0;
     float2* d_halo = nullptr;     // slab halo planes, [member][2][nx*ny]
@@ -1445,6 +1446,7 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_LATTICE: *v = c->lattice; break;
     case LBMBT_OPT_STAGE_OWN_Z: *v = c->oz_opt; break;
     case LBMBT_OPT_SCHEME: *v = c->scheme; break;
+    case LBMBT_OPT_GRAD_GROUPS: *v = c->grad_groups; break;
     case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? (c->tma_oz ? 2 : 1) : 0; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
@@ -1653,6 +1655,7 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
     const size_t held = c->cap_state + c->cap_ck + c->cap_seg;
     const size_t budget = (size_t)((double)(free_b + held) * 0.8);
     int m0 = 0;
+    c->grad_groups = 0;
     while (m0 < n_members) {
         size_t used = 0;
         int m1 = m0;
@@ -1670,6 +1673,7 @@ extern "C" int lbmbt_grad_batch(lbmbt_ctx* c, int n_members, const lbmbt_member*
         rc = grad_group(c, m1 - m0, members + m0, ck, signal_out + 3 * m0, dS_dD + (size_t)m0 * c->n_phases,
                         dS_dT2 + (size_t)m0 * c->n_phases, dS_dkappa + m0);
         if (rc) return rc;
+        ++c->grad_groups;
         m0 = m1;
     }
     return LBMBT_OK;
