@@ -123,16 +123,17 @@ def links_traffic_per_launch(n):
     return j["dram_bytes_read"] + j["dram_bytes_write"]
 
 
-def traffic_per_launch():
-    """DRAM bytes per sweep launch from the committed ncu summary, or None
-    when the kernel source changed since it was captured."""
+def traffic_per_launch(site_updates):
+    """DRAM bytes per sweep launch of `site_updates` site-member updates,
+    from the bytes per update in the committed ncu summary, or None when the
+    kernel source changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
     if j.get("source_hash") != sweep_source_hash():
         return None
-    return float(j["bytes_per_site_member"]) * N_EDGE ** 3 * 3
+    return float(j["bytes_per_site_member"]) * site_updates
 
 
 class Clocks:
@@ -849,6 +850,8 @@ def main():
     ap.add_argument("--spt", type=int, default=0)
     ap.add_argument("--n", type=int, default=N_EDGE, help="lattice edge (default 512)")
     ap.add_argument("--slabs", type=int, default=4, help="slab workload: number of z slabs")
+    ap.add_argument("--nz", type=int, default=0,
+                    help="default workload: run only the tissue's first NZ planes (a small case for counters)")
     ap.add_argument("--workload", default="tissue512",
                     choices=["tissue512", "batch", "adjoint", "slab", "links", "variants", "membrane_study",
                              "classical"],
@@ -891,6 +894,11 @@ def main():
 
     t_geo = time.perf_counter()
     geom = geometry(args.n)
+    if args.nz and args.nz < args.n:
+        # the tissue's first nz planes (same planes, staging form and faces;
+        # a small case for counter captures)
+        from paper_1907_00908_gb300 import synth
+        geom = synth.Geometry(np.ascontiguousarray(geom.labels[:args.nz]), geom.phase_of_label, geom.dx)
     t_geo = time.perf_counter() - t_geo
     fractions = phase_fractions(geom)
     seqs = sequences()
@@ -986,14 +994,17 @@ def main():
             extras["adjoint_full_schedule"] = measure_adjoint(args, stream, None)
 
     if rank == 0:
-        tr = traffic_per_launch()
+        tr = traffic_per_launch(n_sites * nm)
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [args.n] * 3, "dx_um": DX, "dt_ms": DT, "members": nm,
+            "config": {"workload": WORKLOAD if geom.labels.shape[0] == args.n else
+                       f"tissue512_first{geom.labels.shape[0]}planes_voronoi_mirror_3dir",
+                       "grid": [args.n, args.n, int(geom.labels.shape[0])], "dx_um": DX, "dt_ms": DT, "members": nm,
                        "bc": "mirror", "phases": 3, "kappa_um_ms": KAPPA, "b_s_mm2": B,
-                       "l2": "state of 15 GB per direction, far larger than L2; no flush needed",
+                       "l2": f"state of {2 * 7 * 8 * n_sites / 1e9:.2f} GB per direction, larger than L2; "
+                             "no flush needed",
                        "sites_per_step": n_sites * nm, "geometry_gen_s": round(t_geo, 1), "launch": shape,
                        "seed": TISSUE_SEED, "phase_fractions": fractions},
             "signal_after_timed_steps": [float(x) for x in sig[:, 2]],

@@ -56,9 +56,9 @@ def test_traffic_lookup_follows_the_hash(tmp_path, monkeypatch):
     rec = {"source_hash": bench.sweep_source_hash(), "bytes_per_site_member": 120.0}
     with open(os.path.join(root, "profiles", "sweep_traffic.json"), "w") as fh:
         json.dump(rec, fh)
-    assert bench.traffic_per_launch() == 120.0 * bench.N_EDGE ** 3 * 3
+    assert bench.traffic_per_launch(bench.N_EDGE ** 3 * 3) == 120.0 * bench.N_EDGE ** 3 * 3
     (tmp_path / "paper_1907_00908_gb300" / "csrc" / "sweep_tma.cu").write_text(SRC.replace("1.f", "3.f"))
-    assert bench.traffic_per_launch() is None
+    assert bench.traffic_per_launch(1000) is None
 
 
 def test_phase_fractions_of_a_known_geometry():
