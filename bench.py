@@ -1011,6 +1011,9 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr, "peak_source": peak_kind,
+                         "traffic_source": "ncu DRAM bytes on the tissue's first 128 planes, scaled by site updates "
+                                           "(profiles/sweep_traffic.json); bytes per update rise with the planes, so "
+                                           "a lower bound for the full grid" if tr is not None else None,
                          "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_tma_kernel"},
             "e2e": e2e,
             "cpu_baseline": cpu,

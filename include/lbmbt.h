@@ -353,10 +353,21 @@ enum {
                                 (positions: EUNSUPPORTED), no reaction
                                 sub-steps (EINVAL), no slabs and no adjoint
                                 (EUNSUPPORTED); both lattices              */
-    LBMBT_OPT_GRAD_GROUPS = 15 /* read-only: the number of groups the last
+    LBMBT_OPT_GRAD_GROUPS = 15, /* read-only: the number of groups the last
                                 lbmbt_grad_batch split its members into so
                                 that one group's checkpoints fit in the free
                                 device memory (0 before any)              */
+    LBMBT_OPT_TEST_WAIT_NS = 16 /* tests of the timeout path only; 0 (default)
+                                off.  1 .. 1e9: every consumer warp of the
+                                bulk-copy sweep first waits, with this limit
+                                in ns, on a shared-memory barrier that nothing
+                                completes; the wait runs out as a wait for a
+                                lost copy would (every wait of the sweep is
+                                bounded by 2 s), the CTA sets the step
+                                control's error word after its producer has
+                                waited (bounded) for its own copies in
+                                flight, and the call returns LBMBT_EDEVICE.
+                                The context stays usable                  */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

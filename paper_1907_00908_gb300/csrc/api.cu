@@ -111,6 +111,7 @@ struct lbmbt_ctx {
     size_t cap_ftab = 0;
     bool ftab_valid = false;      // d_ftab holds the prepared members' factors
     int grad_groups = 0;          // member groups of the last lbmbt_grad_batch
+    long long test_wait_ns = 0;   // tests of the bulk-copy sweep's timeout path (0: off)
     float2* d_etab = nullptr;     // per-member rotation tables
     size_t cap_etab = 0;
     float2* d_halo = nullptr;     // slab halo planes, [member][2][nx*ny]
@@ -778,6 +779,7 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.f = c->d_f;
     a.F = c->d_F;
     a.scheme = c->scheme;
+    a.test_wait_ns = (unsigned long long)c->test_wait_ns;
     a.partial = c->d_partial;
     a.fac = c->d_ftab;
     a.links = 0;
@@ -1424,6 +1426,10 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         if (v != 0 && v != 1) return fail(c, LBMBT_EINVAL, "scheme must be 0 (hybrid) or 1 (classical)");
         c->scheme = (int)v;
         break;
+    case LBMBT_OPT_TEST_WAIT_NS:
+        if (v < 0 || v > 1000000000LL) return fail(c, LBMBT_EINVAL, "test wait must be 0 (off) .. 1e9 ns");
+        c->test_wait_ns = v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -1447,6 +1453,7 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_STAGE_OWN_Z: *v = c->oz_opt; break;
     case LBMBT_OPT_SCHEME: *v = c->scheme; break;
     case LBMBT_OPT_GRAD_GROUPS: *v = c->grad_groups; break;
+    case LBMBT_OPT_TEST_WAIT_NS: *v = c->test_wait_ns; break;
     case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? (c->tma_oz ? 2 : 1) : 0; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);

@@ -116,6 +116,9 @@ struct SweepArgs {
                                   // variant with the Eqs. B4a-B4c rule); 2: and angles
     float w0, wxy, wz;            // equilibrium weights (register sweep, init):
                                   // D3Q7 1/4, 1/8, 1/8; D2Q5 1/3, 1/6, 0 (Sec. 2.3)
+    unsigned long long test_wait_ns;  // bulk-copy sweep, tests of the timeout path only: > 0
+                                  // makes each consumer warp first wait, with this limit,
+                                  // on a barrier nothing completes (0: off)
     int scheme;                   // 0 the hybrid scheme; 1 the classical LBM with the
                                   // reaction as a collision source (Appendix A, Eq. A12),
                                   // register sweep only: f and F are then read one step

@@ -248,6 +248,7 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.links = 0;
     a.w0 = W0; a.wxy = WI; a.wz = WI;   // D3Q7
     a.scheme = 0;                       // the hybrid scheme
+    a.test_wait_ns = 0;
     MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
     // control word (done counter and step start from the values above every
     // call; each sweep's last block advances the step) and the boundary

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     __shared__ uint64_t full[TMA_MAX_STAGES];
     __shared__ uint64_t empty[TMA_MAX_STAGES];
     __shared__ UnitGeo infos[TMA_MAX_STAGES];
+    __shared__ uint64_t never;   // test of the timeout path: a barrier nothing completes
     __shared__ int s_abort;
 
     const size_t stb = stage_bytes(cap, capx, OZ);
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             mbar_init(&full[st], 1);
             mbar_init(&empty[st], TMA_CONSUMERS / 32);
         }
+        mbar_init(&never, 1);
         fence_mbar_init();
         s_abort = 0;
     }
@@ -227,7 +229,12 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         }
         return true;
     };
-    bool ok = prefetch(0, own);
+    // Test of the timeout path (a test-only option): the first wait is on a
+    // barrier that nothing completes, with a short limit; it runs out like a
+    // lost copy would, and the warp takes the abort path below (the producer
+    // keeps its normal bounds and drains its copies before the CTA exits).
+    bool ok = a.test_wait_ns == 0 || mbar_wait(&never, 0u, a.test_wait_ns);
+    ok = ok && prefetch(0, own);
 
     // constants of the current member, reloaded only when the member changes
     int cm = -1, nx = 1, ny = 1, nz = 1, bcx = 0, bcy = 0, bcz0 = 0, bcz1 = 0;

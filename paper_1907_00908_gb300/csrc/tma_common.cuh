@@ -53,13 +53,13 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Bounded wait for one phase of an mbarrier; false after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Bounded wait for one phase of an mbarrier; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = WAIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(bar, parity))
-        if (globaltimer() - t0 > WAIT_NS) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     return true;
 }
 
