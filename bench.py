@@ -675,8 +675,8 @@ def run_classical(args):
     collision source (Appendix A, Eq. A12), on the GPU.
 
     Throughput: the 256^3 cylinders (dx 0.25 um, c2 phases, 3 gradient
-    directions, PGSE b = 1000) with the classical pass against the hybrid
-    pass on the same register sweep and on the bulk-copy sweep.
+    directions, PGSE b = 1000) with the classical pass (autotuned; and on
+    each sweep) against the hybrid pass on the same sweeps.
 
     Accuracy (Sec. 3.2, Fig. 5): a uniform initial field in periodic squares
     of side L = 20 and 100 um (D2Q5, D = 2.0, T2 = inf, tau = 0.6, PGSE
@@ -695,7 +695,8 @@ def run_classical(args):
     members = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
     timing = {}
     clocks = None
-    for name, scheme, kernel in (("classical_register", 1, 1), ("hybrid_register", 0, 1),
+    for name, scheme, kernel in (("classical", 1, 0), ("classical_register", 1, 1),
+                                 ("classical_bulk_copy", 1, 2), ("hybrid_register", 0, 1),
                                  ("hybrid_bulk_copy", 0, 2)):
         s = lbmbt.Solver(0, stream)
         s.set_option(lbmbt.OPT_SCHEME, scheme)
@@ -715,8 +716,8 @@ def run_classical(args):
             torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         timing[name] = {"MLUPS": geom.n_sites * len(gGs) / (ms * 1e-3) / 1e6, "ms_per_step": ms,
-                        "launch": {"block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT)}}
-        if scheme == 1:
+                        "launch": _launch_shape(s, lbmbt)}
+        if name == "classical":
             clocks = clk.summary()
         s.close()
 
@@ -750,16 +751,17 @@ def run_classical(args):
                 s.close()
             study[f"L{int(L)}_dx{dx}"] = row
     peak, peak_kind = peaks()
-    v = timing["classical_register"]["MLUPS"]
+    v = timing["classical"]["MLUPS"]
     achieved = BYTES_PER_SITE * v * 1e6 / 1e9
     line = {"metric": "MLUPS (classical LBM with reaction source, FP32)", "value": v, "unit": "MLUPS",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": timing["classical_register"]["ms_per_step"], "higher_is_better": True,
+            "ms_per_step": timing["classical"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"cylinders{n}_dx0.25_classical_3dir", "grid": [n] * 3},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                         "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_classical_kernel"},
+                         "bytes_per_site_member": BYTES_PER_SITE,
+                         "kernel": "classical pass, " + timing["classical"]["launch"]["kernel"] + " sweep"},
             "compare": timing, "uniform_ic_study": study, "exact_exp_minus_bD": ex, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
@@ -900,6 +902,7 @@ def main():
         from paper_1907_00908_gb300 import synth
         geom = synth.Geometry(np.ascontiguousarray(geom.labels[:args.nz]), geom.phase_of_label, geom.dx)
     t_geo = time.perf_counter() - t_geo
+    nz_run = int(geom.labels.shape[0])
     fractions = phase_fractions(geom)
     seqs = sequences()
     K_total = len(seqs[0][1])
@@ -999,9 +1002,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if geom.labels.shape[0] == args.n else
-                       f"tissue512_first{geom.labels.shape[0]}planes_voronoi_mirror_3dir",
-                       "grid": [args.n, args.n, int(geom.labels.shape[0])], "dx_um": DX, "dt_ms": DT, "members": nm,
+            "config": {"workload": WORKLOAD if nz_run == args.n else
+                       f"tissue512_first{nz_run}planes_voronoi_mirror_3dir",
+                       "grid": [args.n, args.n, nz_run], "dx_um": DX, "dt_ms": DT, "members": nm,
                        "bc": "mirror", "phases": 3, "kappa_um_ms": KAPPA, "b_s_mm2": B,
                        "l2": f"state of {2 * 7 * 8 * n_sites / 1e9:.2f} GB per direction, larger than L2; "
                              "no flush needed",

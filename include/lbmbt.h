@@ -348,8 +348,8 @@ enum {
                                 x.G0 f(t^k) - 1/T2, no reaction step; the
                                 outer faces then take the waveform integral
                                 after the step, F_(k+1) = sum_{m<=k} f_m dt.
-                                Register sweep only (a forced bulk-copy sweep
-                                returns EINVAL), half-link membranes only
+                                Both sweeps (bit-identical fields), half-link
+                                membranes only
                                 (positions: EUNSUPPORTED), no reaction
                                 sub-steps (EINVAL), no slabs and no adjoint
                                 (EUNSUPPORTED); both lattices              */

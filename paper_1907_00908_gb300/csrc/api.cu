@@ -654,7 +654,6 @@ static constexpr long long TMA_OZ_PLANE = 1LL << 17;
 static bool tma_eligible(const lbmbt_ctx* c)
 {
     if (c->lattice != 0) return false;   // the bulk-copy sweep has the D3Q7 weights built in
-    if (c->scheme != 0) return false;    // and the hybrid scheme's reaction step
     for (auto& d : c->descs)
         if (d.nx % 16 != 0 || d.nx > TMA_MAX_CAP || d.dlt != nullptr) return false;
     return true;
@@ -682,7 +681,7 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     const bool tma = want && tma_eligible(c);
     if (c->kernel_opt == 2 && !tma)
         return fail(c, LBMBT_EINVAL, "bulk-copy sweep needs nx %% 16 == 0 and nx <= %d for every member, no "
-                                     "membrane positions, the D3Q7 lattice and the hybrid scheme", TMA_MAX_CAP);
+                                     "membrane positions and the D3Q7 lattice", TMA_MAX_CAP);
     int cap = 16, capx = 0;
     for (int m = 0; m < c->n_members; ++m) {
         MemberDesc& d = c->descs[m];
@@ -804,6 +803,7 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
 static int write_ctl(lbmbt_ctx* c, int sig_step, int field_step, int slot_base = 0, int slot_mod = 2)
 {
     StepCtl h;
+    memset(&h, 0, sizeof h);   // counters start at zero
     h.k = (int)c->k_cur;
     h.done = 0;
     h.sig_step = sig_step;
@@ -838,7 +838,7 @@ static int issue_step(lbmbt_ctx* c)
     } else {
         CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
     }
-    c->launches += 1;
+    c->launches += c->use_tma ? 1 : 2;   // the register sweep is followed by the step advance
     if (c->series_mode) {
         CU(c, launch_reduce(c->d_partial, part_start(c), part_per(c), c->n_members, c->d_Z, c->d_series, c->n_steps, c->d_ctl,
                             c->stream));
@@ -884,17 +884,28 @@ static int autotune(lbmbt_ctx* c)
                 cudaGetLastError();
                 continue;
             }
+            // one warm step, then batches of steps from k = 0 (never past
+            // the end of the schedule), growing until a batch takes 1 ms
             int rc = init_state(c);
             if (!rc) rc = write_ctl(c, -1, -1);
             if (!rc) rc = issue_step(c);
             if (rc) break;
-            CU(c, cudaEventRecord(e0, c->stream));
-            for (int r = 0; r < 4 && !rc; ++r) rc = issue_step(c);
-            CU(c, cudaEventRecord(e1, c->stream));
-            CU(c, cudaEventSynchronize(e1));
-            float ms = 0;
-            CU(c, cudaEventElapsedTime(&ms, e0, e1));
-            if (!rc && ms < best) { best = ms; win = cd; }
+            const long long r_max = std::min<long long>(c->n_steps, 256);
+            long long r = std::min<long long>(4, r_max);
+            float per_step = 0.f;
+            for (;;) {
+                rc = write_ctl(c, -1, -1);
+                CU(c, cudaEventRecord(e0, c->stream));
+                for (long long q = 0; q < r && !rc; ++q) rc = issue_step(c);
+                CU(c, cudaEventRecord(e1, c->stream));
+                CU(c, cudaEventSynchronize(e1));
+                float ms = 0;
+                CU(c, cudaEventElapsedTime(&ms, e0, e1));
+                per_step = ms / (float)r;
+                if (rc || ms >= 1.f || r >= r_max) break;
+                r = std::min<long long>(r * 4, r_max);
+            }
+            if (!rc && per_step < best) { best = per_step; win = cd; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1185,7 +1196,7 @@ static int advance(lbmbt_ctx* c, long long n, bool want_signal)
             rc = capture_graph(c);
             if (rc) return rc;
         }
-        const int per = c->series_mode ? 2 : 1;
+        const int per = (c->use_tma ? 1 : 2) + (c->series_mode ? 1 : 0);
         while (left >= GRAPH_CHUNK) {
             CU(c, cudaGraphLaunch(c->graph, c->stream));
             c->launches += GRAPH_CHUNK * per;

@@ -89,18 +89,21 @@ struct MemberDesc {
 };
 
 // Step control word in device memory.  Every block of a sweep reads k at its
-// start; the last block to finish (a ticket on `done`, no waiting) advances
-// k, so a captured graph of sweeps replays from any step.  No kernel ever
+// start.  The bulk-copy sweep's last CTA to be done with it (a two-level
+// ticket, no waiting) advances k; after a register sweep a one-thread kernel
+// does.  So a captured graph of steps replays from any step.  No kernel ever
 // waits on it.
+constexpr unsigned CTL_SHARDS = 32;   // first-level ticket counters (same-address atomics serialise)
 struct StepCtl {
     int k;              // step index the next sweep performs
-    unsigned done;      // blocks of the current sweep that have finished (0 between sweeps)
+    unsigned done;      // shards of the current sweep whose blocks are all done (0 between sweeps)
     int sig_step;       // step whose end signal is reduced (-1: none)
     int field_step;     // step whose end field is written (-1: none)
     int slot_base;      // src slot = (k - slot_base) % slot_mod
     int slot_mod;       // dst slot = (k + 1 - slot_base) % slot_mod
     int series;         // 1: reduce the signal after every step
     int err;            // device-side error bits
+    unsigned shard[CTL_SHARDS];   // blocks b % CTL_SHARDS == s of the current sweep that are done
 };
 
 struct SweepArgs {
@@ -140,6 +143,7 @@ cudaError_t launch_factor_table(const MemberDesc* members, int n_members, int F_
                                 float2* table, cudaStream_t st);
 cudaError_t launch_init(const SweepArgs& a, long long n_tiles, int block, int spt, int slot,
                         cudaStream_t st);
+// Register sweep (one block per tile), then the one-thread step advance.
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
 cudaError_t links_prepare();   // dynamic shared memory of the membrane-position sweeps
 // Sums partial[tile_start[m]*per .. tile_start[m+1]*per) per member.

@@ -206,6 +206,7 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     d.Fw = reinterpret_cast<const double*>(base + OFF_FCUM);
 
     StepCtl c;
+    memset(&c, 0, sizeof c);   // ticket counters start at zero every call
     c.k = (int)k0;
     c.done = 0;                                  // must start at zero every call
     c.sig_step = (int)(k0 + n_steps - 1);

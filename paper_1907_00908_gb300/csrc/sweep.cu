@@ -19,8 +19,9 @@
 //  * sweep_classical_kernel: the same pass for the classical LBM (Appendix A,
 //        Eq. A12): stream + BCs + membrane, M = sum_i g_i, collision with
 //        the reaction as a source term; no reaction step
-//  * ctl_set_kernel    : sets the step word before a run of sweeps (each
-//                        sweep's last block advances it)
+//  * ctl_set_kernel    : sets the step word before a run of sweeps (the
+//                        bulk-copy sweep's last CTA advances it; after a
+//                        register sweep ctl_advance_kernel does)
 //  * factor_table_kernel: FP64 boundary factors of every step, once per run
 //  * reduce_kernel     : fixed-order FP64 sum of the per-tile partials.
 //
@@ -318,9 +319,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a)
             if (l == 0) a.partial[blockIdx.x] = v;
         }
     }
-    // every thread of the block is past its use of the step word
-    __syncthreads();
-    if (threadIdx.x == 0) step_done(a.ctl, k, gridDim.x);
 }
 
 template <int SPT>
@@ -347,6 +345,13 @@ __global__ void __launch_bounds__(512, ANG ? 1 : 2) sweep_links_kernel(const Swe
 
 // Control word: set before a run of sweeps.
 __global__ void ctl_set_kernel(StepCtl* ctl, StepCtl v) { *ctl = v; }
+
+// Step advance after a register sweep.  That sweep has one block per tile
+// (~10^5 a step on large grids); a ticket per block at its end, as the
+// persistent bulk-copy sweep takes one per CTA, made each block wait for its
+// streaming stores before it retired: 25 % slower, measured.  A persistent
+// form of the register sweep was 12 % slower than one block per tile.
+__global__ void ctl_advance_kernel(StepCtl* ctl) { ctl->k = ctl->k + 1; }
 
 // Boundary factors of all steps 0..K, in FP64 from each member's F_k:
 // table[k][m][6] (forward sweeps and adjoint sweeps).
@@ -441,7 +446,17 @@ cudaError_t links_prepare()
     return cudaSuccess;
 }
 
+static cudaError_t launch_sweep_blocks(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
+
 cudaError_t launch_sweep(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st)
+{
+    cudaError_t e = launch_sweep_blocks(a, n_tiles, block, spt, st);
+    if (e != cudaSuccess) return e;
+    ctl_advance_kernel<<<1, 1, 0, st>>>(a.ctl);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_sweep_blocks(const SweepArgs& a, long long n_tiles, int block, int spt, cudaStream_t st)
 {
     if (a.scheme == 1) {   // classical scheme: half-link rule only (positions are refused at set-up)
         switch (spt) {

@@ -232,16 +232,26 @@ __device__ __forceinline__ float2 source_dtRM(float ep, float th, float mr, floa
     return make_float2(__fmaf_rn(-ep, mr, __fmul_rn(-th, mi)), __fmaf_rn(-ep, mi, __fmul_rn(th, mr)));
 }
 
-// End of a sweep for one block (or CTA): take a ticket; the last of the
-// launch's `nblocks` advances the step word and clears the counter for the
-// next sweep.  Every block has read k before it takes its ticket, so no
-// block can see the new value.  The caller has made its own threads finish
-// with the step word before calling (one thread per block calls).
-__device__ __forceinline__ void step_done(StepCtl* ctl, int k, unsigned nblocks)
+// A CTA of a persistent sweep is done with the step word: take a ticket;
+// the last of the launch's `nblocks` advances the word and clears the
+// counters for the next sweep (which sees both at its launch: kernel
+// boundary).  Every CTA has read k before it takes its ticket, so none can
+// see the new value.  One thread per CTA calls, right after a CTA barrier
+// that follows every thread's read of the step control; with `fence` those
+// reads are ordered before the ticket at device scope.
+// The ticket has two levels, since atomics on one address serialise (about
+// 7 ns each, measured: a register sweep has ~10^5 blocks a step): block b
+// counts on shard b % CTL_SHARDS, and the last block of each shard counts on
+// `done`.
+__device__ __forceinline__ void step_done(StepCtl* ctl, int k, unsigned nblocks, bool fence)
 {
-    __threadfence();
-    if (atomicAdd(&ctl->done, 1u) == nblocks - 1u) {
-        __threadfence();
+    if (fence) __threadfence();
+    const unsigned s = blockIdx.x % CTL_SHARDS;
+    const unsigned in_shard = (nblocks - s + CTL_SHARDS - 1u) / CTL_SHARDS;   // blocks b < nblocks, b % S == s
+    if (atomicAdd(&ctl->shard[s], 1u) != in_shard - 1u) return;
+    ctl->shard[s] = 0u;
+    const unsigned shards = nblocks < CTL_SHARDS ? nblocks : CTL_SHARDS;
+    if (atomicAdd(&ctl->done, 1u) == shards - 1u) {
         ctl->done = 0u;
         ctl->k = k + 1;
     }

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     __syncthreads();
     // every thread of this CTA has read the step word: take the CTA's ticket
     // (the last CTA of the launch advances it for the next sweep)
-    if (tid == 0) step_done(a.ctl, k, gridDim.x);
+    if (tid == 0) step_done(a.ctl, k, gridDim.x, true);
 
     if (tid >= TMA_CONSUMERS) {
         // ---------------- producer warp (lane 0 issues)
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             ep0 = sd->eps[0]; ep1 = sd->eps[1]; ep2 = sd->eps[2]; ep3 = sd->eps[3];
             dstb = sd->state + (size_t)ldst * 7 * P;
             field = sd->field;
-            fk = __ldg(sd->fw + k);
+            fk = __ldg(sd->fw + k + a.scheme);   // the classical scheme collides with f_(k+1)
             // a member with an end step of its own gives its signal and field there
             const int es = sd->end_step;
             do_sig = series || k == (es >= 0 ? es : sig_step);
@@ -364,9 +364,39 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 }
             }
         };
+        // Classical scheme (Appendix A, Eq. A12): no reaction step; M = sum_i g_i
+        // and the collision with the source dt R M, as in the register sweep
+        auto phase2_classical = [&]() {
+#pragma unroll
+            for (int j = 0; j < TMA_SPT; ++j) {
+                const int l = tid + j * TMA_CONSUMERS;
+                const bool valid = l < G.L;
+                const int ph = mks[j] >> 6;
+                const float ep = (ph & 2) ? ((ph & 1) ? ep3 : ep2) : ((ph & 1) ? ep1 : ep0);
+                const float om = (ph & 2) ? ((ph & 1) ? om3 : om2) : ((ph & 1) ? om1 : om0);
+                float mr = 0.f, mi = 0.f;
+#pragma unroll
+                for (int i2 = 0; i2 < Q; ++i2) {
+                    mr = __fadd_rn(mr, g[j][i2].x);
+                    mi = __fadd_rn(mi, g[j][i2].y);
+                }
+                const float2 src = source_dtRM(ep, fk != 0.f ? theta_lin(sd, fk, xs[j], ys[j], z) : 0.f, mr, mi);
+                collide_source_w(g[j], om, mr, mi, src.x, src.y, W0, WI, WI);
+                const unsigned s = G.s0 + (unsigned)l;
+                if (valid) {
+#pragma unroll
+                    for (int i2 = 0; i2 < Q; ++i2) __stcs(dst + (size_t)i2 * P + s, g[j][i2]);
+                    zr += mr;
+                    zi += mi;
+                    if (do_field) field[s] = make_float2(mr, mi);
+                }
+            }
+        };
         const int ax = sd->axes;
         const float2* __restrict__ et = sd->etab;
-        if (fk == 0.f) {
+        if (a.scheme == 1) {
+            phase2_classical();
+        } else if (fk == 0.f) {
             phase2([&](int) { return make_float2(0.f, 0.f); });
         } else if (et != nullptr && (fk == 1.f || fk == -1.f) && (ax == 1 || ax == 2 || ax == 4)) {
             // one gradient axis: a single table entry per site

@@ -6,7 +6,8 @@ Tolerances as for the hybrid scheme: S within 1e-5 relative, the field
 within 1e-4 of max|M|.  Cases: both lattices, periodic, mirror (gradient
 normal and parallel to the faces) and mixed faces, membranes with kappa 0,
 finite and infinite, ragged tile tails, several launch shapes, and a
-128^3 cylinder pack on a short schedule.
+128^3 cylinder pack on a short schedule.  Grids the bulk-copy sweep takes
+(nx a multiple of 16) run on both sweeps, whose fields agree bit for bit.
 """
 import math
 
@@ -31,10 +32,11 @@ def lb():
     return lbmbt
 
 
-def _gpu(lb, geom, bc, D, T2, kap, dt, f, gG, lattice=0, block=None, spt=None, series=False):
+def _gpu(lb, geom, bc, D, T2, kap, dt, f, gG, lattice=0, block=None, spt=None, series=False, kernel=1):
     s = lb.Solver(0)
     s.set_option(lb.OPT_SCHEME, 1)
     s.set_option(lb.OPT_LATTICE, lattice)
+    s.set_option(lb.OPT_KERNEL, kernel)
     if block:
         s.set_option(lb.OPT_BLOCK, block)
     if spt:
@@ -46,7 +48,8 @@ def _gpu(lb, geom, bc, D, T2, kap, dt, f, gG, lattice=0, block=None, spt=None, s
     fld = torch.zeros(geom.n_sites, dtype=torch.complex64, device="cuda")
     r = s.run(field=fld, series=series)
     torch.cuda.synchronize()
-    assert s.get_option(lb.OPT_KERNEL_USED) == 1
+    used = s.get_option(lb.OPT_KERNEL_USED)
+    assert used == kernel if kernel else used == (2 if geom.labels.shape[2] % 16 == 0 and lattice == 0 else 1)
     s.close()
     return r, fld.cpu().numpy().reshape(geom.labels.shape)
 
@@ -71,6 +74,12 @@ CASES = [
     (lambda: synth.crop(synth.voronoi_tissue(40, 0.5, cell_diam=6.0, vessel_radius=1.5, seed=2), 22), (1, 1, 1),
      (1, 0, 0), 0.0),
     (lambda: synth.spheres(18, 1.0, rmin=2.0, rmax=3.0, fraction=0.4, seed=9), (1, 0, 0), (0, 0.6, 0.8), INF),
+    # nx a multiple of 16: both sweeps
+    (lambda: synth.cylinders(32, 1.0, fraction=0.5, seed=6), (0, 0, 0), (0.6, -0.48, 0.64), 0.05),
+    (lambda: synth.crop(synth.voronoi_tissue(48, 0.5, cell_diam=6.0, vessel_radius=1.5, seed=8), 32), (1, 1, 1),
+     (0, 0, 1), 0.01),
+    (lambda: synth.crop(synth.voronoi_tissue(48, 0.5, cell_diam=6.0, vessel_radius=1.5, seed=8), 32), (1, 0, 1),
+     (0, 1, 0), 0.02),
 ]
 
 
@@ -84,6 +93,10 @@ def test_classical_matches_oracle_d3q7(lb, case):
     gG, f = oracle.pgse(1500.0, 2.0, 5.0, 0.05, d)
     r, fld = _gpu(lb, geom, bc, D, T2, kap, 0.05, f, gG)
     _check(r, fld, _oracle(geom, bc, D, T2, kap, 0.05, f, gG))
+    if geom.labels.shape[2] % 16 == 0:   # the bulk-copy sweep: the same bits
+        r2, fld2 = _gpu(lb, geom, bc, D, T2, kap, 0.05, f, gG, kernel=2)
+        assert np.array_equal(fld, fld2)
+        assert r2["S"] == pytest.approx(r["S"], rel=1e-7)
 
 
 @pytest.mark.parametrize("bc,d", [((0, 0, 0), (0.6, 0.8, 0.0)), ((1, 1, 0), (1.0, 0.0, 0.0)),
@@ -144,7 +157,7 @@ def test_classical_cylinders_128_short_schedule(lb):
     gG, f = oracle.pgse(3000.0, 10.0, 30.0, dt, (0.6, 0.0, 0.8))
     f = f[:64]
     D, T2, kap = [2.0, 1.0], [80.0, 50.0], 0.02
-    r, fld = _gpu(lb, geom, (0, 0, 0), D, T2, kap, dt, f, gG)
+    r, fld = _gpu(lb, geom, (0, 0, 0), D, T2, kap, dt, f, gG, kernel=0)   # auto: the bulk-copy sweep
     _check(r, fld, _oracle(geom, (0, 0, 0), D, T2, kap, dt, f, gG))
 
 
@@ -157,11 +170,6 @@ def test_classical_refusals(lb):
     s.set_phases([2.0, 1.0], [80.0, 50.0])
     s.set_permeability(0.02)
     s.set_sequence(0.025, f, gG)
-    s.set_option(lb.OPT_KERNEL, 2)                      # bulk-copy sweep: hybrid only
-    with pytest.raises(lb.LbmbtError) as e:
-        s.run()
-    assert e.value.code == -1
-    s.set_option(lb.OPT_KERNEL, 0)
     with pytest.raises(lb.LbmbtError) as e:             # adjoint: hybrid only
         s.grad()
     assert e.value.code == -5
