@@ -4,7 +4,10 @@
 float64 tensor whose backward gives dS/dD_p, dS/dT2_p and dS/dkappa from the
 library's hand-written adjoint sweep (``lbmbt_grad``), for microstructure
 fitting.  The forward and the reverse sweep both run in the CUDA library; the
-Function only moves the parameters in and the gradients out.
+Function only moves the parameters in and the gradients out.  When no
+gradient can be asked for (grad mode off, or no input requires one) the
+signal comes from a plain forward run (``lbmbt_run``), without the ~4x cost
+of the checkpointed adjoint.
 """
 from __future__ import annotations
 
@@ -19,8 +22,7 @@ def _like(x):
 class SignalFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, D, T2, kappa, solver, checkpoint_every):
-        as_np = lambda x: torch.as_tensor(x).detach().double().cpu().numpy()
-        solver.set_phases(as_np(D), as_np(T2))
+        solver.set_phases(_as_np(D), _as_np(T2))
         solver.set_permeability(float(kappa))
         g = solver.grad(checkpoint_every)
         ctx.save_for_backward(torch.as_tensor(g["dD"], dtype=torch.float64),
@@ -39,6 +41,15 @@ class SignalFn(torch.autograd.Function):
         return out[0], out[1], out[2], None, None
 
 
+def _as_np(x):
+    return torch.as_tensor(x).detach().double().cpu().numpy()
+
+
 def signal(solver, D, T2, kappa, checkpoint_every=64):
     """Differentiable dMRI signal of the solver's geometry and sequence."""
+    wants = torch.is_grad_enabled() and any(isinstance(x, torch.Tensor) and x.requires_grad for x in (D, T2, kappa))
+    if not wants:   # forward only
+        solver.set_phases(_as_np(D), _as_np(T2))
+        solver.set_permeability(float(kappa))
+        return torch.as_tensor(solver.run()["S"], dtype=torch.float64)
     return SignalFn.apply(D, T2, kappa, solver, checkpoint_every)

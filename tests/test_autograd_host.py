@@ -23,7 +23,12 @@ class FakeSolver:
 
     def grad(self, checkpoint_every):
         self.seen["ck"] = checkpoint_every
+        self.seen["called"] = "grad"
         return {"S": 0.75, "dD": np.array([0.5, -2.0]), "dT2": np.array([0.125, 4.0]), "dkappa": -3.0}
+
+    def run(self):
+        self.seen["called"] = "run"
+        return {"S": 0.75}
 
 
 def test_parameters_in_signal_out_and_gradients_back():
@@ -49,3 +54,19 @@ def test_plain_number_and_frozen_parameters_get_no_gradient():
     S.backward()
     assert torch.equal(D.grad, torch.tensor([0.5, -2.0], dtype=torch.float64))
     assert T2.grad is None
+
+
+def test_no_gradient_wanted_runs_the_forward_only():
+    """Under no_grad, or with no input requiring a gradient, the signal comes
+    from a plain forward run: the adjoint (about 4x the cost) is not run."""
+    s = FakeSolver()
+    D = torch.tensor([2.0, 1.0], dtype=torch.float64, requires_grad=True)
+    with torch.no_grad():
+        S = signal(s, D, [80.0, 50.0], 0.02)
+    assert s.seen["called"] == "run" and float(S) == 0.75 and not S.requires_grad
+    s = FakeSolver()
+    S = signal(s, torch.tensor([2.0, 1.0]), torch.tensor([80.0, 50.0]), 0.02)
+    assert s.seen["called"] == "run"
+    s = FakeSolver()
+    S = signal(s, D, [80.0, 50.0], 0.02)
+    assert s.seen["called"] == "grad" and S.requires_grad
