@@ -149,14 +149,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
         const float ep = sd->eps[ph];
         const float2 rot = fk != 0.f ? rotation_m1(sd, fk, x, y, z) : make_float2(0.f, 0.f);
         const float2 q = fk != 0.f ? reaction_q(rot, ep) : make_float2(-ep, 0.f);
-        const float qr = q.x, qi = q.y;
         const float cm1 = rot.x, sn = rot.y;
-        // g = (1 + q) g' and M = sum g, in the forward sweep's order
-        float2 gg[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) gg[i] = gp[i];
-        float Mr, Mi;
-        react(gg, q, Mr, Mi);
 
         // lambda^k at this site
         float2 lam[Q];
@@ -177,28 +170,38 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const AdjointArgs a)
             }
         }
 
-        // d/d omega: <lambda_i, w_i M - g_i>, g_i = (1 + q) g'_i
-        float dOm = 0.f;
-        float lwr = 0.f, lwi = 0.f;
+        // The reacted populations g_i = (1 + q) g'_i and mu = C^T lambda enter
+        // only through sums over i: Sg = sum g'_i (M = (1 + q) Sg),
+        // D = sum conj(lambda_i) g'_i (sum <lambda_i, g_i> = Re((1 + q) D)) and
+        // lw = sum w_i lambda_i (mu_i = (1 - omega) lambda_i + omega lw).
+        float sgr = 0.f, sgi = 0.f, dr = 0.f, di = 0.f, lwr = 0.f, lwi = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float w = i == 0 ? a.w0 : i < 5 ? a.wxy : a.wz;
-            dOm += lam[i].x * (w * Mr - gg[i].x) + lam[i].y * (w * Mi - gg[i].y);
+            sgr += gp[i].x;
+            sgi += gp[i].y;
+            dr += lam[i].x * gp[i].x + lam[i].y * gp[i].y;
+            di += lam[i].x * gp[i].y - lam[i].y * gp[i].x;
             lwr += w * lam[i].x;
             lwi += w * lam[i].y;
         }
-        // mu = C^T lambda; d/d eps: <mu_i, -exp(i theta) g'_i>; nu = conj(1+q) mu
-        const float om = sd->omega[ph];
-        float dEp = 0.f;
+        const float q1r = 1.f + q.x, q1i = q.y;
+        const float Mr = q1r * sgr - q1i * sgi, Mi = q1r * sgi + q1i * sgr;
+        // d/d omega: sum_i <lambda_i, w_i M - g_i> = Re(conj(lw) M) - Re((1 + q) D)
+        const float dOm = (lwr * Mr + lwi * Mi) - (q1r * dr - q1i * di);
+        const float om = sd->omega[ph], om1 = 1.f - om;
         const float er = 1.f + cm1, ei = sn;
+        // d/d eps: -Re(exp(i theta) c), c = sum_i conj(mu_i) g'_i = (1 - omega) D + omega conj(lw) Sg
+        const float cr = om1 * dr + om * (lwr * sgr + lwi * sgi);
+        const float ci = om1 * di + om * (lwr * sgi - lwi * sgr);
+        const float dEp = -(er * cr - ei * ci);
+        // nu_i = conj(1 + q) mu_i = a lambda_i + b, a = conj(1 + q)(1 - omega), b = conj(1 + q) omega lw
+        const float ar = q1r * om1, ai = -q1i * om1;
+        const float br = om * (q1r * lwr + q1i * lwi), bi = om * (q1r * lwi - q1i * lwr);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float mr = lam[i].x + om * (lwr - lam[i].x);
-            const float mi = lam[i].y + om * (lwi - lam[i].y);
-            dEp -= mr * (er * gp[i].x - ei * gp[i].y) + mi * (er * gp[i].y + ei * gp[i].x);
-            // conj(1 + q) * mu
-            lam[i].x = mr + (mr * qr + mi * qi);
-            lam[i].y = mi + (mi * qr - mr * qi);
+            const float2 l = lam[i];
+            lam[i] = make_float2(ar * l.x - ai * l.y + br, ar * l.y + ai * l.x + bi);
             if (i < 5 || zpl) __stcs(out + (size_t)i * P + s, lam[i]);
         }
         // d/d s on membrane links of step k-1: <nu_i, v_i - o_i>

@@ -296,11 +296,6 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
                 rot = rotation_m1(sd, fk, x, y, z);
             }
             const float2 q = reaction_q(rot, ep);
-            float2 gg[Q];
-#pragma unroll
-            for (int i2 = 0; i2 < Q; ++i2) gg[i2] = gp[i2];
-            float Mr, Mi;
-            react(gg, q, Mr, Mi);
 
             // lambda^k (transposed pattern from nu^k)
             float2 lam[Q];
@@ -333,25 +328,39 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
                 }
             }
 
-            // d/d omega, mu = C^T lambda, d/d eps, nu = conj(1 + q) mu
-            float dOm = 0.f, lwr = 0.f, lwi = 0.f;
+            // The step's reacted populations g_i = (1 + q) g'_i and mu = C^T lambda
+            // enter only through sums over i: Sg = sum g'_i (M = (1 + q) Sg),
+            // D = sum conj(lambda_i) g'_i (sum <lambda_i, g_i> = Re((1 + q) D)) and
+            // lw = sum w_i lambda_i (mu_i = (1 - omega) lambda_i + omega lw).
+            float sgr = 0.f, sgi = 0.f, dr = 0.f, di = 0.f, lwr = 0.f, lwi = 0.f;
 #pragma unroll
             for (int i2 = 0; i2 < Q; ++i2) {
                 const float w = i2 == 0 ? W0 : WI;
-                dOm += lam[i2].x * (w * Mr - gg[i2].x) + lam[i2].y * (w * Mi - gg[i2].y);
+                sgr += gp[i2].x;
+                sgi += gp[i2].y;
+                dr += lam[i2].x * gp[i2].x + lam[i2].y * gp[i2].y;
+                di += lam[i2].x * gp[i2].y - lam[i2].y * gp[i2].x;
                 lwr += w * lam[i2].x;
                 lwi += w * lam[i2].y;
             }
-            const float om = __ldg(sd->omega + ph);
+            const float q1r = 1.f + q.x, q1i = q.y;
+            const float Mr = q1r * sgr - q1i * sgi, Mi = q1r * sgi + q1i * sgr;
+            // d/d omega: sum_i <lambda_i, w_i M - g_i> = Re(conj(lw) M) - Re((1 + q) D)
+            const float dOm = (lwr * Mr + lwi * Mi) - (q1r * dr - q1i * di);
+            const float om = __ldg(sd->omega + ph), om1 = 1.f - om;
             const float er = 1.f + rot.x, ei = rot.y;
-            float dEp = 0.f;
+            // d/d eps: -Re(exp(i theta) c), c = sum_i conj(mu_i) g'_i = (1 - omega) D + omega conj(lw) Sg
+            const float cr = om1 * dr + om * (lwr * sgr + lwi * sgi);
+            const float ci = om1 * di + om * (lwr * sgi - lwi * sgr);
+            const float dEp = -(er * cr - ei * ci);
+            // nu_i = conj(1 + q) mu_i = a lambda_i + b, a = conj(1 + q)(1 - omega),
+            // b = conj(1 + q) omega lw
+            const float ar = q1r * om1, ai = -q1i * om1;
+            const float br = om * (q1r * lwr + q1i * lwi), bi = om * (q1r * lwi - q1i * lwr);
 #pragma unroll
             for (int i2 = 0; i2 < Q; ++i2) {
-                const float mr = lam[i2].x + om * (lwr - lam[i2].x);
-                const float mi = lam[i2].y + om * (lwi - lam[i2].y);
-                dEp -= mr * (er * gp[i2].x - ei * gp[i2].y) + mi * (er * gp[i2].y + ei * gp[i2].x);
-                lam[i2].x = mr + (mr * q.x + mi * q.y);
-                lam[i2].y = mi + (mi * q.x - mr * q.y);
+                const float2 l = lam[i2];
+                lam[i2] = make_float2(ar * l.x - ai * l.y + br, ar * l.y + ai * l.x + bi);
                 __stcs(out + (size_t)i2 * P + s, lam[i2]);
             }
             // d/d s on membrane links of step k-1: <nu_i, v_i - o_i>
