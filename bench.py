@@ -137,12 +137,16 @@ def traffic_per_launch(site_updates):
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler running during the timed region (one file per
+    sampler, so regions timed one after the other keep their own records)."""
+
+    _count = 0
 
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = f"/tmp/lbmbt_clocks_{os.getpid()}.csv"
+        Clocks._count += 1
+        self.path = f"/tmp/lbmbt_clocks_{os.getpid()}_{Clocks._count}.csv"
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -936,6 +940,7 @@ def main():
         sig = s.advance(args.steps, want_signal=True, n_members=nm)
         e1.record(stream)
         torch.cuda.synchronize()
+    clocks_main = clk.summary()
     launches = s.launch_count() - l0
     shape = {"kernel": "bulk-copy" if s.get_option(lbmbt.OPT_KERNEL_USED) == 2 else "register",
              "tma_shape": s.get_option(lbmbt.OPT_TMA_SHAPE), "stages": s.get_option(lbmbt.OPT_STAGES),
@@ -1020,7 +1025,7 @@ def main():
                          "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_tma_kernel"},
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "clocks": clk.summary(),
+            "clocks": clocks_main,
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

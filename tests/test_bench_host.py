@@ -79,3 +79,10 @@ def test_tissue_fractions_follow_the_recipe():
     assert len(fr) == 3 and abs(sum(fr) - 1.0) < 1e-4, fr
     assert abs(fr[1] - 0.2 * (1.0 - fr[2])) < 0.01, fr
     assert 0.0 < fr[2] < 0.2 and fr[0] > 0.6, fr
+
+
+def test_clock_samplers_keep_their_own_records():
+    """Regions timed one after another in one process each get their own
+    nvidia-smi record, so a line's clocks are those of its own region."""
+    a, b = bench.Clocks(0), bench.Clocks(0)
+    assert a.path != b.path
