@@ -4,9 +4,11 @@ ragged grid shapes, periodic / mirror faces per axis, gradient directions
 allowed by the faces, kappa 0, finite or infinite, three compartments, with
 or without membrane positions, both sweeps (the bulk-copy sweep where the
 grid allows it), graphs on or off, launch shapes, 1 or 4 reaction sub-steps,
-and the D2Q5 lattice on one-plane grids; and random batches of members on
-different geometries (some with positions), each member against its own
-oracle run.  Every configuration is a pure function of its seed."""
+and the D2Q5 lattice on one-plane grids; the classical scheme over the same
+kind of configurations; random batches of members on different geometries
+(some with positions), and random batches whose members carry their own
+waveforms and field outputs, each member against its own oracle run.  Every
+configuration is a pure function of its seed."""
 import math
 
 import numpy as np
@@ -158,3 +160,89 @@ def test_random_batch_matches_oracle(lb, seed):
         o = oracle.run(lab, 0.5, pol, bc, [2.0, 1.0], [80.0, 50.0], kap, dt, f, gG,
                        delta=None if dl is None else dl.astype(np.float64))
         assert abs(r["S"][m] - o["S"]) <= S_TOL * o["S"], (seed, m, lab.shape, bc, kap, dl is not None)
+
+
+@pytest.mark.parametrize("seed", list(range(32)))
+def test_random_classical_configuration_matches_oracle(lb, seed):
+    """The classical scheme (Appendix A, Eq. A12) over the same kind of
+    random configurations (no membrane positions and no sub-steps, which it
+    refuses), either sweep, both lattices."""
+    c = _config(700 + seed)
+    rng = np.random.default_rng(9000 + seed)
+    f = rng.choice([-1.0, 0.0, 1.0, 0.5], size=int(rng.integers(5, 30)))
+    s = lb.Solver(0)
+    s.set_option(lb.OPT_SCHEME, 1)
+    s.set_option(lb.OPT_GRAPH, c["opts"]["graph"])
+    s.set_option(lb.OPT_BLOCK, c["opts"]["block"])
+    s.set_option(lb.OPT_SPT, c["opts"]["spt"])
+    if c["d2q5"]:
+        s.set_option(lb.OPT_LATTICE, 1)
+    kernel = c["opts"]["kernel"]
+    if kernel == 2 and not (c["shape"][2] % 16 == 0 and not c["d2q5"]):
+        kernel = 1
+    s.set_option(lb.OPT_KERNEL, kernel)
+    s.set_geometry(c["lab"], c["pol"], 0.5, c["bc"])
+    s.set_phases(c["D"], c["T2"])
+    s.set_permeability(c["kap"])
+    s.set_sequence(c["dt"], f, c["gG"])
+    n = int(np.prod(c["shape"]))
+    fld = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    r = s.run(field=fld)
+    torch.cuda.synchronize()
+    s.close()
+    o = oracle.run(c["lab"], 0.5, c["pol"], c["bc"], c["D"], c["T2"], c["kap"], c["dt"], f, c["gG"],
+                   want_field=True, lattice="D2Q5" if c["d2q5"] else "D3Q7", scheme="classical")
+    assert abs(r["S"] - o["S"]) <= S_TOL * max(o["S"], 1e-30) + 1e-12, (c["shape"], c["bc"], r["S"], o["S"])
+    ref = o["field"]
+    err = np.abs(fld.cpu().numpy().reshape(c["shape"]) - ref).max() / max(np.abs(ref).max(), 1e-30)
+    assert err < FIELD_TOL, (c["shape"], c["bc"], c["opts"], err)
+
+
+@pytest.mark.parametrize("seed", list(range(12)))
+def test_random_batch_with_member_waveforms_matches_oracle(lb, seed):
+    """Random batches through lbmbt_run_batch_ex: each member with its own
+    random waveform of its own length (or the set one) and its own field
+    output, against its own oracle run at its own end."""
+    rng = np.random.default_rng(7000 + seed)
+    bc = tuple(int(v) for v in rng.integers(0, 2, size=3))
+    n_mem = int(rng.integers(2, 5))
+    kernel = int(rng.choice([0, 1, 2]))
+    dt, K = 0.02, int(rng.integers(8, 25))
+    f_set = rng.choice([-1.0, 0.0, 1.0], size=K)
+    cases = []
+    nx_all = []
+    for m in range(n_mem):
+        shape = (int(rng.integers(1, 7)), int(rng.integers(1, 9)), int(rng.choice([16, 32, 7, 12])))
+        nx_all.append(shape[2])
+        lab = rng.integers(0, 3, size=shape).astype(np.int32)
+        kap = float(rng.choice([0.0, 0.05, math.inf]))
+        mir = [a for a in range(3) if bc[a] == 1]
+        g = rng.normal(size=3)
+        if mir and (len(mir) == 3 or rng.random() < 0.5):
+            g = np.zeros(3)
+            g[int(rng.choice(mir))] = 1.0
+        else:
+            g[mir] = 0.0
+        wave = None if rng.random() < 0.3 else rng.choice([-1.0, 0.0, 1.0, 0.5], size=int(rng.integers(1, K + 1)))
+        cases.append((lab, kap, g * 0.08, wave))
+    if kernel == 2 and any(v % 16 for v in nx_all):
+        kernel = 1
+    pol = np.array([0, 1, 1], np.uint8)
+    s = lb.Solver(0)
+    s.set_option(lb.OPT_KERNEL, kernel)
+    s.set_option(lb.OPT_GRAPH, int(rng.integers(0, 2)))
+    for m, (lab, _, _, _) in enumerate(cases):
+        (s.set_geometry if m == 0 else s.add_geometry)(lab, pol, 0.5, bc)
+    s.set_phases([2.0, 1.0], [80.0, 50.0])
+    s.set_sequence(dt, f_set, cases[0][2])
+    mem = lb.Solver.members([c[2] for c in cases], list(range(n_mem)), [c[1] for c in cases])
+    flds = [torch.zeros(c[0].size, dtype=torch.complex64, device="cuda") for c in cases]
+    r = s.run_batch(mem, waveforms=[c[3] for c in cases], fields=flds)
+    torch.cuda.synchronize()
+    s.close()
+    for m, (lab, kap, gG, wave) in enumerate(cases):
+        fm = f_set if wave is None else wave
+        o = oracle.run(lab, 0.5, pol, bc, [2.0, 1.0], [80.0, 50.0], kap, dt, fm, gG, want_field=True)
+        assert abs(r["S"][m] - o["S"]) <= S_TOL * o["S"], (seed, m, lab.shape, bc, kap)
+        err = np.abs(flds[m].cpu().numpy().reshape(lab.shape) - o["field"]).max() / np.abs(o["field"]).max()
+        assert err < FIELD_TOL, (seed, m, err)
