@@ -1019,6 +1019,7 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr, "peak_source": peak_kind,
+                         "traffic_gbs": tr / per_launch_s / 1e9 if tr is not None else None,
                          "traffic_source": "ncu DRAM bytes on the tissue's first 128 planes, scaled by site updates "
                                            "(profiles/sweep_traffic.json); bytes per update rise with the planes, so "
                                            "a lower bound for the full grid" if tr is not None else None,
