@@ -75,10 +75,10 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("shape", [(7, 9, 12), (5, 7, 32)])
 @pytest.mark.parametrize("name", list(CASES))
-def test_random_positions_match_oracle(lb, name):
+def test_random_positions_match_oracle(lb, name, shape):
     c = CASES[name]
-    shape = (7, 9, 12)
     rng = np.random.default_rng(5)
     labels = rng.integers(0, 3, size=shape).astype(np.int32)
     pol = np.array([0, 1, 2], np.uint8)
@@ -87,15 +87,17 @@ def test_random_positions_match_oracle(lb, name):
     _check(lb, labels, pol, 0.5, c["bc"], [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], c["kap"], 0.02, f, gG, dl)
 
 
-def test_sphere_pack_exact_positions(lb):
-    g = synth.spheres(20, 0.5, rmin=1.2, rmax=2.5, fraction=0.35, seed=9)
+@pytest.mark.parametrize("n", [20, 32])
+def test_sphere_pack_exact_positions(lb, n):
+    g = synth.spheres(n, 0.5, rmin=1.2, rmax=2.5, fraction=0.35, seed=9)
     dl = synth.link_distances(g, (0, 0, 0))
     gG, f = oracle.pgse(2000.0, 0.4, 0.8, 0.02, (0.3, 0.5, 0.81))
     _check(lb, g.labels, g.phase_of_label, g.dx, (0, 0, 0), [2.0, 1.0], [80.0, 50.0], 0.03, 0.02, f, gG, dl)
 
 
-def test_walls_exact_positions_mirror(lb):
-    g = synth.walls(24, 0.5, [2.13, 5.61, 9.02], axis=0, cross=(4, 6), periodic=False, phases=[0, 1])
+@pytest.mark.parametrize("n", [24, 32])
+def test_walls_exact_positions_mirror(lb, n):
+    g = synth.walls(n, 0.5, [2.13, 5.61, 9.02], axis=0, cross=(4, 6), periodic=False, phases=[0, 1])
     dl = synth.link_distances(g, (1, 0, 0))
     gG, f = oracle.pgse(1500.0, 0.4, 0.8, 0.02, (1.0, 0.0, 0.0))
     _check(lb, g.labels, g.phase_of_label, g.dx, (1, 0, 0), [2.0, 1.0], [80.0, 50.0], 0.05, 0.02, f, gG, dl)
