@@ -1528,15 +1528,30 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
         CU(c, cudaMemcpyAsync(to, from, lv * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
         return LBMBT_OK;
     };
-    // forward with checkpoints u^0, u^ck, u^2ck, ...
+    // forward with checkpoints u^0, u^ck, u^2ck, ...; from the last
+    // segment's first step on it writes its levels straight into the segment
+    // buffer (slot k - k_last), so that segment is not recomputed
+    const long long k_last = (n_ck - 1) * ck;
     rc = write_ctl(c, (int)(K - 1), -1);
     if (rc) return rc;
-    for (int m = 0; m < n; ++m)
-        if ((rc = copy_level(m, c->descs[m].state, ckb[m]))) return rc;
+    if (n_ck > 1)
+        for (int m = 0; m < n; ++m)
+            if ((rc = copy_level(m, c->descs[m].state, ckb[m]))) return rc;
     for (long long k = 0; k < K; ++k) {
+        if (k == k_last) {
+            std::vector<MemberDesc> fd = c->descs;
+            for (int m = 0; m < n; ++m) {
+                const size_t lv = (size_t)7 * c->descs[m].plane;
+                if ((rc = copy_level(m, c->descs[m].state + (k & 1) * lv, segb[m]))) return rc;
+                fd[m].state = segb[m];
+            }
+            CU(c, cudaMemcpyAsync(c->d_desc, fd.data(), sizeof(MemberDesc) * n, cudaMemcpyHostToDevice, c->stream));
+            c->k_cur = k;
+            if ((rc = write_ctl(c, (int)(K - 1), -1, (int)k, ck + 1))) return rc;
+        }
         if ((rc = issue_step(c))) return rc;
         const long long kn = k + 1;
-        if (kn % ck == 0 && kn < K)
+        if (kn % ck == 0 && kn < k_last)
             for (int m = 0; m < n; ++m) {
                 const size_t lv = (size_t)7 * c->descs[m].plane;
                 if ((rc = copy_level(m, c->descs[m].state + (kn & 1) * lv, ckb[m] + (kn / ck) * lv))) return rc;
@@ -1594,11 +1609,13 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     int parity = 1;
     for (long long seg = n_ck - 1; seg >= 0; --seg) {
         const long long k0 = seg * ck, k1 = std::min(K, k0 + ck);
-        for (int m = 0; m < n; ++m) {
-            const size_t lv = (size_t)7 * c->descs[m].plane;
-            if ((rc = copy_level(m, ckb[m] + seg * lv, segb[m]))) return rc;
+        if (seg < n_ck - 1) {   // the last segment's levels are in place from the forward pass
+            for (int m = 0; m < n; ++m) {
+                const size_t lv = (size_t)7 * c->descs[m].plane;
+                if ((rc = copy_level(m, ckb[m] + seg * lv, segb[m]))) return rc;
+            }
         }
-        if (k1 - k0 - 1 > 0) {
+        if (seg < n_ck - 1 && k1 - k0 - 1 > 0) {
             c->k_cur = k0;
             if ((rc = write_ctl(c, -1, -1, (int)k0, ck + 1))) return rc;
             for (long long k = k0; k < k1 - 1; ++k)
