@@ -848,8 +848,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--adj-shape", type=int, default=2, help="bulk-copy adjoint consumer shape (0, 1 or 2)")
-    ap.add_argument("--stage-own-z", type=int, default=0, choices=[0, 1, 2],
-                    help="bulk-copy sweep: own z rows 0 auto, 1 prefetched into registers, 2 staged")
+    ap.add_argument("--stage-own-z", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="bulk-copy sweep: own z values 0 auto, 1 prefetched into registers, 2 staged, "
+                         "3 z-marching columns")
     ap.add_argument("--members", type=int, default=60, help="adjoint workload: number of members (<= 60)")
     ap.add_argument("--adj-steps", type=int, default=400,
                     help="adjoint workload: steps of the 6400-step schedule timed (the prefix)")
@@ -950,7 +951,7 @@ def main():
     shape = {"kernel": "bulk-copy" if s.get_option(lbmbt.OPT_KERNEL_USED) == 2 else "register",
              "tma_shape": s.get_option(lbmbt.OPT_TMA_SHAPE), "stages": s.get_option(lbmbt.OPT_STAGES),
              "block": s.get_option(lbmbt.OPT_BLOCK), "spt": s.get_option(lbmbt.OPT_SPT),
-             "own_z": {0: None, 1: "prefetched", 2: "staged"}[s.get_option(lbmbt.OPT_STAGE_OWN_Z_USED)],
+             "own_z": {0: None, 1: "prefetched", 2: "staged", 3: "z-marching"}[s.get_option(lbmbt.OPT_STAGE_OWN_Z_USED)],
              "autotuned": not args.no_autotune}
     from paper_1907_00908_gb300 import shard
     ms = shard.max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)

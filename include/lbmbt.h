@@ -332,13 +332,19 @@ enum {
                                 returns EUNSUPPORTED)                          */
     LBMBT_OPT_STAGE_OWN_Z = 12, /* bulk-copy sweep, geometries with membranes:
                                 where the own-site values of the z populations
-                                come from.  0 (default) auto: staged with the
-                                unit when some member with membranes has a
-                                plane of >= 2^17 sites, else prefetched into
-                                registers; 1 always prefetched; 2 always
-                                staged (2 more rows per stage slot)            */
-    LBMBT_OPT_STAGE_OWN_Z_USED = 13, /* read-only: 1 prefetched or 2 staged for a
-                                prepared bulk-copy run, else 0                 */
+                                come from.  0 (default) auto: when some member
+                                with membranes has a plane of >= 2^17 sites,
+                                z-marching if the grid gives at least 32
+                                columns per SM of >= 8 planes (a column length
+                                that divides every member's nz), else staged;
+                                otherwise prefetched.  1 always prefetched into
+                                registers; 2 always staged with the unit (2 more
+                                rows per stage slot); 3 always z-marching: each
+                                CTA walks columns of units (the same rows of
+                                consecutive planes) in z order and carries the
+                                z values from unit to unit                     */
+    LBMBT_OPT_STAGE_OWN_Z_USED = 13, /* read-only: 1 prefetched, 2 staged or 3
+                                z-marching for a prepared bulk-copy run, else 0 */
     LBMBT_OPT_SCHEME = 14,   /* 0 (default) the hybrid scheme (Eq.
                                 LBM_process_list_2); 1 the paper's comparison
                                 scheme, the classical LBM with the reaction as

@@ -116,11 +116,12 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
         // ---------------- producer warp (lane 0 issues)
         if (tid != ADJ_CONSUMERS) return;
         long long j = 0;
-        for (;; ++j) {
+        int st = 0;          // j % nst and (j / nst) & 1, kept by increments (no division per unit)
+        uint32_t ph = 0;
+        for (;; ++j, st = st + 1 == nst ? 0 : st + 1, ph = st == 0 ? ph ^ 1u : ph) {
             const long long u = unit_of(j);
             if (u >= n_units || s_abort) break;
-            const int st = (int)(j % nst);
-            if (j >= nst && !mbar_wait(&empty[st], (uint32_t)(((j / nst) - 1) & 1))) {
+            if (j >= nst && !mbar_wait(&empty[st], ph ^ 1u)) {
                 s_abort = 1;
                 break;
             }
@@ -175,12 +176,13 @@ __global__ void __launch_bounds__(ADJ_CONSUMERS + 32, 1)
 #pragma unroll
         for (int q = 0; q < NGACC; ++q) acc[q] = 0.f;
     };
-    for (long long i = 0;; ++i) {
+    int st = 0;              // i % nst and (i / nst) & 1, kept by increments
+    uint32_t ph = 0;
+    for (long long i = 0;; ++i, st = st + 1 == nst ? 0 : st + 1, ph = st == 0 ? ph ^ 1u : ph) {
         const long long u = unit_of(i);
         if (u >= n_units) break;
-        const int st = (int)(i % nst);
         // warp-uniform, so the warp's lanes leave the loop together
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((i / nst) & 1)))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[st], ph))) {
             s_abort = 1;
             break;
         }

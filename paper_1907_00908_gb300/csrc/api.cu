@@ -13,6 +13,7 @@
 #include <cstring>
 #include <algorithm>
 #include <map>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -94,8 +95,13 @@ struct lbmbt_ctx {
     int tma_capx = 0;
     int tma_stages = 3;
     int tma_variant = 3;
-    bool tma_oz = false;          // own z rows staged (a member with membranes and a large plane)
-    int oz_opt = 0;               // 0 auto, 1 prefetch, 2 stage
+    int tma_form = 0;             // own z values: 0 prefetched, 1 staged, 2 z-marching columns
+    int oz_opt = 0;               // 0 auto, 1 prefetch, 2 stage, 3 z-marching
+    int tma_zc = 0;               // z-marching: units per column
+    long long n_cc = 0;           // z-marching: columns of all members
+    std::vector<long long> cc_start;
+    long long* d_cc_start = nullptr;
+    size_t cap_cc = 0;
     int tuned_kernel = 0;         // 0: untuned, 1 register, 2 bulk copy (auto follows it)
     struct Tuned { int kernel, block, spt, variant, stages; };
     std::map<std::string, Tuned> tune_cache;
@@ -263,7 +269,7 @@ extern "C" int lbmbt_destroy(lbmbt_ctx* c)
     cudaFree(c->d_f); cudaFree(c->d_F);
     cudaFree(c->d_desc); cudaFree(c->d_tile_start); cudaFree(c->d_partial); cudaFree(c->d_Z);
     cudaFree(c->d_series); cudaFree(c->d_state); cudaFree(c->d_ctl); cudaFree(c->d_err);
-    cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab);
+    cudaFree(c->d_ftab); cudaFree(c->d_unit_start); cudaFree(c->d_etab); cudaFree(c->d_cc_start);
     cudaFree(c->d_adj_unit_start); cudaFree(c->d_halo);
     cudaFree(c->d_ck); cudaFree(c->d_seg); cudaFree(c->d_gacc); cudaFree(c->d_gout); cudaFree(c->d_laminit);
     if (c->owned_stream) cudaStreamDestroy(c->owned_stream);
@@ -708,22 +714,52 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     if (tma) {
         c->tma_cap = (cap + 15) / 16 * 16;
         c->tma_capx = (capx + 15) / 16 * 16;
-        c->tma_oz = c->oz_opt == 2;
-        if (c->oz_opt == 0)
-            for (auto& d : c->descs)
-                if (d.memb && (long long)d.nx * d.ny >= TMA_OZ_PLANE) c->tma_oz = true;
+        if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+        // where the own z values of membrane lanes come from: on large planes
+        // with membranes z-marching columns (each row read once, no own value
+        // from global memory) when the grid gives enough columns of >= 8
+        // planes, else staged with the unit; otherwise prefetched
+        bool large = false;
+        for (auto& d : c->descs)
+            if (d.memb && (long long)d.nx * d.ny >= TMA_OZ_PLANE) large = true;
+        int gz = 0;   // column length must divide every member's nz
+        for (auto& d : c->descs) gz = std::gcd(gz, d.nz);
+        auto columns = [&](int zc) {
+            long long n = 0;
+            for (auto& d : c->descs) n += (long long)(d.nz / zc) * ((d.ny + d.rpu - 1) / d.rpu);
+            return n;
+        };
+        int zc = 0;   // the longest column (a power of two <= 32) that leaves >= 32 columns a SM
+        for (int t = 32; t >= 1 && !zc; t >>= 1)
+            if (gz % t == 0 && columns(t) >= 32LL * c->sm_count) zc = t;
+        if (c->oz_opt == 3 && !zc)
+            for (int t = 32; t >= 1 && !zc; t >>= 1)
+                if (gz % t == 0) zc = t;
+        c->tma_form = c->oz_opt == 1 ? 0 : c->oz_opt == 2 ? 1 : c->oz_opt == 3 ? 2
+                      : !large ? 0 : zc >= 8 ? 2 : 1;
+        c->tma_zc = c->tma_form == 2 ? zc : 0;
+        c->n_cc = 0;
+        c->cc_start.assign(c->n_members + 1, 0);
+        if (c->tma_form == 2)
+            for (int m = 0; m < c->n_members; ++m) {
+                MemberDesc& d = c->descs[m];
+                d.cc0 = c->cc_start[m];
+                c->cc_start[m + 1] = d.cc0 + (long long)(d.nz / zc) * ((d.ny + d.rpu - 1) / d.rpu);
+            }
+        c->n_cc = c->cc_start[c->n_members];
         int per_sm = 0;
-        const cudaError_t pe = tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_oz,
+        const cudaError_t pe = tma_prepare(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_form,
                                            &per_sm);
         if (pe == cudaErrorInvalidValue) {   // more shared memory than a block may have
             cudaGetLastError();
             return fail(c, LBMBT_EINVAL, "%d bulk-copy stages of %d sites (%zu bytes) do not fit in shared memory",
-                        c->tma_stages, c->tma_cap, tma_smem_bytes(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_oz));
+                        c->tma_stages, c->tma_cap,
+                        tma_smem_bytes(c->tma_cap, c->tma_capx, c->tma_stages, c->tma_form));
         }
         CU(c, pe);
         if (per_sm < 1) return fail(c, LBMBT_EINVAL, "bulk-copy sweep does not fit on an SM");
-        if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
-        c->tma_grid = (int)std::min<long long>((long long)c->sm_count * per_sm, c->n_units);
+        c->tma_grid = (int)std::min<long long>((long long)c->sm_count * per_sm,
+                                               c->tma_form == 2 ? c->n_cc : c->n_units);
     }
     for (auto& d : c->descs)
         if (d.dlt) {
@@ -736,6 +772,7 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
     if (!rc) rc = grow(c, &c->d_unit_start, &c->cap_us, sizeof(long long) * (c->n_members + 1));
     if (!rc) rc = grow(c, &c->d_adj_unit_start, &c->cap_aus, sizeof(long long) * (c->n_members + 1));
     if (!rc) rc = grow(c, &c->d_partial, &c->cap_partial, sizeof(double2) * n_part);
+    if (!rc) rc = grow(c, &c->d_cc_start, &c->cap_cc, sizeof(long long) * (c->n_members + 1));
     if (rc) return rc;
     CU(c, cudaMemcpyAsync(c->d_desc, c->descs.data(), sizeof(MemberDesc) * c->n_members, cudaMemcpyHostToDevice,
                           c->stream));
@@ -758,6 +795,9 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
                           cudaMemcpyHostToDevice, c->stream));
     CU(c, cudaMemcpyAsync(c->d_adj_unit_start, c->adj_unit_start.data(), sizeof(long long) * (c->n_members + 1),
                           cudaMemcpyHostToDevice, c->stream));
+    if (c->use_tma && c->tma_form == 2)
+        CU(c, cudaMemcpyAsync(c->d_cc_start, c->cc_start.data(), sizeof(long long) * (c->n_members + 1),
+                              cudaMemcpyHostToDevice, c->stream));
     c->tile_block = block;
     c->tile_spt = spt;
     drop_graph(c);
@@ -781,6 +821,12 @@ static SweepArgs sweep_args(lbmbt_ctx* c)
     a.test_wait_ns = (unsigned long long)c->test_wait_ns;
     a.partial = c->d_partial;
     a.fac = c->d_ftab;
+    const bool zm = c->use_tma && c->tma_form == 2;
+    a.zc = zm ? c->tma_zc : 0;
+    a.zc_log2 = 0;
+    while (a.zc > (1 << a.zc_log2)) ++a.zc_log2;
+    a.n_cc = zm ? c->n_cc : 0;
+    a.cc_start = zm ? c->d_cc_start : nullptr;
     a.links = 0;
     for (auto& d : c->descs) {
         if (d.dth) a.links = 2;
@@ -833,7 +879,7 @@ static int issue_step(lbmbt_ctx* c)
     SweepArgs a = sweep_args(c);
     if (c->use_tma) {
         a.tile_start = c->d_unit_start;
-        CU(c, launch_sweep_tma(a, c->n_units, c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_oz,
+        CU(c, launch_sweep_tma(a, c->n_units, c->tma_cap, c->tma_capx, c->tma_stages, c->tma_variant, c->tma_form,
                                c->tma_grid, c->stream));
     } else {
         CU(c, launch_sweep(a, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
@@ -1430,7 +1476,7 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         c->lattice = (int)v;
         break;
     case LBMBT_OPT_STAGE_OWN_Z:
-        if (v < 0 || v > 2) return fail(c, LBMBT_EINVAL, "own-z staging must be 0 (auto), 1 or 2");
+        if (v < 0 || v > 3) return fail(c, LBMBT_EINVAL, "own-z source must be 0 (auto), 1, 2 or 3");
         c->oz_opt = (int)v;
         break;
     case LBMBT_OPT_SCHEME:
@@ -1465,7 +1511,7 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_SCHEME: *v = c->scheme; break;
     case LBMBT_OPT_GRAD_GROUPS: *v = c->grad_groups; break;
     case LBMBT_OPT_TEST_WAIT_NS: *v = c->test_wait_ns; break;
-    case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? (c->tma_oz ? 2 : 1) : 0; break;
+    case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? c->tma_form + 1 : 0; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }

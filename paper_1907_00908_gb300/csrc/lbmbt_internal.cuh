@@ -42,6 +42,7 @@ struct MemberDesc {
     long long plane;      // plane stride in sites
     long long tile0;      // first work-list tile of this member (site tiles)
     long long unit0;      // first row-unit of this member (bulk-copy sweep)
+    long long cc0;        // first unit column of this member (bulk-copy sweep, z-marching form)
     int rpu;              // x-rows per unit of the bulk-copy sweep
     int rpu_adj;          // x-rows per unit of the bulk-copy adjoint sweep
     long long unit0_adj;  // first row-unit of this member (bulk-copy adjoint)
@@ -122,6 +123,12 @@ struct SweepArgs {
     unsigned long long test_wait_ns;  // bulk-copy sweep, tests of the timeout path only: > 0
                                   // makes each consumer warp first wait, with this limit,
                                   // on a barrier nothing completes (0: off)
+    int zc;                       // bulk-copy sweep, z-marching form: units per column
+                                  // (consecutive z-planes of the same rows; a power of two
+                                  // that divides every member's nz), else 0
+    int zc_log2;                  // log2(zc)
+    long long n_cc;               // z-marching: columns of all members
+    const long long* cc_start;    // z-marching: n_members + 1 prefix of columns
     int scheme;                   // 0 the hybrid scheme; 1 the classical LBM with the
                                   // reaction as a collision source (Appendix A, Eq. A12),
                                   // register sweep only: f and F are then read one step
@@ -155,10 +162,10 @@ cudaError_t launch_reduce(const double2* partial, const long long* tile_start, i
 // oz: the own rows of planes 5 and 6 go through the stage (wanted where
 // planes are large, so those rows would otherwise come from DRAM a plane
 // later); without it they are prefetched into registers with planes 3 and 4.
-size_t tma_smem_bytes(int cap, int capx, int nst, bool oz);
+size_t tma_smem_bytes(int cap, int capx, int nst, int form);
 int tma_partials_per_unit(int variant);
-cudaError_t tma_prepare(int cap, int capx, int nst, int variant, bool oz, int* ctas_per_sm);
-cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, bool oz,
+cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int form, int* ctas_per_sm);
+cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int form,
                              int grid, cudaStream_t st);
 
 // ---- adjoint (adjoint.cu) -------------------------------------------------

@@ -250,6 +250,10 @@ extern "C" int lbmbt_sweep_noalloc(int nx, int ny, int nz, double dx_um, const u
     a.w0 = W0; a.wxy = WI; a.wz = WI;   // D3Q7
     a.scheme = 0;                       // the hybrid scheme
     a.test_wait_ns = 0;
+    a.zc = 0;   // the register sweep: no z-marching columns
+    a.zc_log2 = 0;
+    a.n_cc = 0;
+    a.cc_start = nullptr;
     MemberDesc* dd = reinterpret_cast<MemberDesc*>(base + OFF_DESC);
     // control word (done counter and step start from the values above every
     // call; each sweep's last block advances the step) and the boundary

@@ -13,12 +13,19 @@
 // collides and stores them with no branch between sites (phase 2), so the
 // arithmetic of several sites interleaves.  The own-site values of planes
 // 3 and 4 (membrane links in y) are prefetched into registers one unit
-// ahead.  Those of planes 5 and 6 (membrane links in z) come in one of two
-// forms, chosen per run (template flag OZ): staged with the unit (large
-// planes: the rows are otherwise first touched a whole plane later, and a
-// load at a membrane lane waited on DRAM), or prefetched like planes 3 and 4
-// (small planes: the rows are still in L2, and the smaller stage leaves more
-// of the SM's memory to L1).
+// ahead.  Those of planes 5 and 6 (membrane links in z) come in one of three
+// forms, chosen per run (template parameter FORM): 0 prefetched like planes
+// 3 and 4 (small planes: the rows are still in L2, and the smaller stage
+// leaves more of the SM's memory to L1); 1 staged with the unit (the rows
+// are otherwise first touched a whole plane later, and a load at a membrane
+// lane waited on DRAM; they are read again when the neighbouring planes'
+// units pull them); 2 z-marching: each CTA takes columns of zc units (the
+// same rows of zc consecutive z-planes of one member) in z order.  There a
+// unit stages the own rows of plane 5 in place of the rows of plane z-1,
+// and every consumer keeps, per site, the plane-5 own value (the next
+// unit's +z pull) and the plane-6 pull value (the next unit's own value) in
+// registers, so each row is read once and no own value is loaded from
+// global memory; the first unit of a column loads those two values itself.
 //
 // Source row-blocks of a unit starting at site s0 (all 16-byte aligned when
 // nx is even; the mask copy needs nx % 16 == 0):
@@ -28,9 +35,10 @@
 //   plane 3 (+y) rows y-1 (row 0 of the grid: wrapped row, or the mirror
 //                source: own row of plane 4)
 //   plane 4 (-y) rows y+1 (last row: wrapped row, or own row of plane 3)
-//   plane 5 (+z) plane z-1 (z = 0: wrapped plane, or own rows of plane 6)
+//   plane 5 (+z) plane z-1 (z = 0: wrapped plane, or own rows of plane 6);
+//                z-marching: own rows of plane 5
 //   plane 6 (-z) plane z+1 (last plane: wrapped, or own rows of plane 5)
-//   own rows of planes 5 and 6 [s0, s0+L) (OZ and geometries with membranes)
+//   own rows of planes 5 and 6 [s0, s0+L) (FORM 1 and geometries with membranes)
 // The boundary factors (periodic phase, mirror conjugation and rewind) are
 // applied per element after the copy, exactly as in the register kernel.
 //
@@ -47,29 +55,66 @@ namespace {
 constexpr int TMA_MAX_STAGES = 6;
 
 // Shared-memory stage (all parts 16-byte aligned): 7 pull rows of (cap + 2)
-// complex values (the sources listed above), with OZ the own rows of planes
+// complex values (the sources listed above), with FORM 1 the own rows of planes
 // 5 and 6 (slots 7 and 8), capx spare complex values (0 in use), then cap
 // mask bytes.
-__host__ __device__ __forceinline__ size_t stage_bytes(int cap, int capx, bool oz)
+__host__ __device__ __forceinline__ size_t stage_bytes(int cap, int capx, int form)
 {
-    return (((size_t)(oz ? 9 : 7) * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
+    return (((size_t)(form == 1 ? 9 : 7) * (cap + 2) + capx) * sizeof(float2) + cap + 127) / 128 * 128;
 }
 __device__ __forceinline__ float2* stage_plane(unsigned char* stage, int cap, int i)
 {
     return reinterpret_cast<float2*>(stage) + (size_t)i * (cap + 2);
 }
-__device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, int capx, bool oz)
+__device__ __forceinline__ uint8_t* stage_mask(unsigned char* stage, int cap, int capx, int form)
 {
-    return stage + ((size_t)(oz ? 9 : 7) * (cap + 2) + capx) * sizeof(float2);
+    return stage + ((size_t)(form == 1 ? 9 : 7) * (cap + 2) + capx) * sizeof(float2);
+}
+
+// Z-marching (FORM 2): the j-th unit of this CTA.  Columns cc = blockIdx +
+// q gridDim (q = j / zc) of all members in order; unit index within the
+// member cc_local * zc + zi.  n_units past the last column.  zc is a power
+// of two (shifts and masks: no division in the unit loops).
+__device__ __forceinline__ long long zm_unit(const SweepArgs& a, long long n_units, long long j)
+{
+    const long long cc = blockIdx.x + (j >> a.zc_log2) * (long long)gridDim.x;
+    if (cc >= a.n_cc) return n_units;
+    const int m = a.n_members == 1 ? 0 : find_member(a.cc_start, a.n_members, cc);
+    const MemberDesc* __restrict__ d = a.members + m;
+    return d->unit0 + ((cc - d->cc0) << a.zc_log2) + (j & (a.zc - 1));
+}
+
+// Where z-marching unit u lies; us is the index of the same rows in the
+// plane-by-plane order, whose signal slots it fills.
+__device__ __forceinline__ UnitGeo unit_geo_zm(const SweepArgs& a, long long u, long long* us)
+{
+    UnitGeo G;
+    G.m = a.n_members == 1 ? 0 : find_member(a.tile_start, a.n_members, u);
+    const MemberDesc* __restrict__ d = a.members + G.m;
+    const int ny = d->ny, nx = d->nx, rpu = d->rpu;
+    const int lu = (int)(u - d->unit0);
+    const int upz = (ny + rpu - 1) / rpu;
+    const int ccl = lu >> a.zc_log2, zi = lu & (a.zc - 1);
+    const int yb = ccl % upz;
+    G.z = (ccl / upz) * a.zc + zi;
+    G.y0 = yb * rpu;
+    G.rows = min(rpu, ny - G.y0);
+    G.L = G.rows * nx;
+    G.s0 = (unsigned)G.z * ((unsigned)nx * ny) + (unsigned)G.y0 * nx;
+    *us = d->unit0 + (long long)G.z * upz + yb;
+    return G;
 }
 
 // Thread 0: copies of unit u into `stage`, completion on `bar`.
-template <bool OZ>
+template <int FORM>
 __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, int smod, unsigned char* stage, int cap,
-                           int capx, uint64_t* bar, UnitGeo* info)
+                           int capx, uint64_t* bar, UnitGeo* info, long long* info_us)
 {
-    const UnitGeo G = unit_geo(a.members, a.tile_start, a.n_members, u);
+    constexpr bool OZ = FORM == 1;
+    long long us = u;
+    const UnitGeo G = FORM == 2 ? unit_geo_zm(a, u, &us) : unit_geo(a.members, a.tile_start, a.n_members, u);
     *info = G;   // published to the consumers by the mbarrier (release/acquire)
+    *info_us = us;
     const int m = G.m, z = G.z, y0 = G.y0, rows = G.rows;
     const MemberDesc& d = a.members[m];
     const long long nx = d.nx, sxy = (long long)d.nx * d.ny;
@@ -119,7 +164,8 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
     {
         const float2* srcz;
         const int b0 = d.zbc[0], b1 = d.zbc[1];
-        if (z >= 1) srcz = pl(5) + s0 - sxy;
+        if (FORM == 2) srcz = pl(5) + s0;   // z-marching: the own rows (the next unit's pull rows)
+        else if (z >= 1) srcz = pl(5) + s0 - sxy;
         else if (b0 == BC_HALO || b0 == BC_HALO_PER) srcz = d.halo[0] + (long long)y0 * nx;
         else srcz = b0 == BC_PER ? pl(5) + s0 + (long long)(d.nz - 1) * sxy : pl(6) + s0;
         bulk_g2s(stage_plane(stage, cap, 5), srcz, Lb, bar);
@@ -128,7 +174,7 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
         else srcz = b1 == BC_PER ? pl(6) + (long long)y0 * nx : pl(5) + s0;
         bulk_g2s(stage_plane(stage, cap, 6), srcz, Lb, bar);
     }
-    bulk_g2s(stage_mask(stage, cap, capx, OZ), d.mask + s0, (uint32_t)L, bar);
+    bulk_g2s(stage_mask(stage, cap, capx, FORM), d.mask + s0, (uint32_t)L, bar);
 }
 
 
@@ -139,22 +185,31 @@ __device__ void issue_unit(const SweepArgs& a, long long u, int k, int sbase, in
 // mbarrier (one arrival per consumer warp when it is done with the stage).
 // No block-wide barrier is used after set-up: every wait is an mbarrier wait
 // with a time limit, so a failed wait ends each warp on its own.
-template <int TMA_CONSUMERS, int TMA_SPT, bool OZ>
+template <int TMA_CONSUMERS, int TMA_SPT, int FORM>
 __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     sweep_tma_kernel(const SweepArgs a, long long n_units, int cap, int capx, int nst)
 {
+    constexpr bool OZ = FORM == 1;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t full[TMA_MAX_STAGES];
     __shared__ uint64_t empty[TMA_MAX_STAGES];
     __shared__ UnitGeo infos[TMA_MAX_STAGES];
+    __shared__ long long infos_us[TMA_MAX_STAGES];   // signal slot index of the unit
     __shared__ uint64_t never;   // test of the timeout path: a barrier nothing completes
     __shared__ int s_abort;
 
-    const size_t stb = stage_bytes(cap, capx, OZ);
+    const size_t stb = stage_bytes(cap, capx, FORM);
     const int tid = threadIdx.x;
     const int k = __ldcg(&a.ctl->k);
     const int sbase = __ldcg(&a.ctl->slot_base), smod = __ldcg(&a.ctl->slot_mod);
-    auto unit_of = [&](long long j) { return blockIdx.x + j * (long long)gridDim.x; };
+    auto unit_of = [&](long long j) {
+        return FORM == 2 ? zm_unit(a, n_units, j) : blockIdx.x + j * (long long)gridDim.x;
+    };
+    // z-marching: this CTA's units (its columns x zc); the consumers test
+    // only this count, the producer walks the columns
+    const long long n_mine = FORM == 2 && blockIdx.x < a.n_cc
+                                 ? ((a.n_cc - 1 - blockIdx.x) / gridDim.x + 1) << a.zc_log2 : 0;
+    auto has_unit = [&](long long j) { return FORM == 2 ? j < n_mine : unit_of(j) < n_units; };
 
     if (tid == 0) {
         for (int st = 0; st < nst; ++st) {
@@ -174,16 +229,17 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         // ---------------- producer warp (lane 0 issues)
         if (tid != TMA_CONSUMERS) return;
         long long j = 0;
-        for (;; ++j) {
+        int st = 0;          // j % nst and (j / nst) & 1, kept by increments (no division per unit)
+        uint32_t ph = 0;
+        for (;; ++j, st = st + 1 == nst ? 0 : st + 1, ph = st == 0 ? ph ^ 1u : ph) {
             const long long u = unit_of(j);
             if (u >= n_units || s_abort) break;
-            const int st = (int)(j % nst);
-            if (j >= nst && !mbar_wait(&empty[st], (uint32_t)(((j / nst) - 1) & 1))) {
+            if (j >= nst && !mbar_wait(&empty[st], ph ^ 1u)) {
                 s_abort = 1;
                 break;
             }
             fence_proxy_async_smem();
-            issue_unit<OZ>(a, u, k, sbase, smod, smem + st * stb, cap, capx, &full[st], &infos[st]);
+            issue_unit<FORM>(a, u, k, sbase, smod, smem + st * stb, cap, capx, &full[st], &infos[st], &infos_us[st]);
         }
         // wait (bounded) for the copies of the last stages before leaving
         for (long long q = j - 1; q >= 0 && q >= j - nst; --q)
@@ -201,15 +257,15 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     // Own-site values of planes 3 and 4 on membrane links in y, prefetched
     // into registers one unit ahead for the lanes whose mask needs them.
     float2 own[TMA_SPT][4], nown[TMA_SPT][4];
-    auto prefetch = [&](long long j, float2 (&o)[TMA_SPT][4]) -> bool {
-        if (unit_of(j) >= n_units) return true;
-        const int st = (int)(j % nst);
-        if (!mbar_wait(&full[st], (uint32_t)((j / nst) & 1))) return false;
+    // (st, ph): unit j's stage and the parity of its fill
+    auto prefetch = [&](long long j, int st, uint32_t ph, float2 (&o)[TMA_SPT][4]) -> bool {
+        if (!has_unit(j)) return true;
+        if (!mbar_wait(&full[st], ph)) return false;
         const UnitGeo G = infos[st];
         const MemberDesc* __restrict__ d = a.members + G.m;
         if (!d->memb) return true;   // geometry without membranes
         unsigned char* sb = smem + st * stb;
-        const uint8_t* __restrict__ mk8 = stage_mask(sb, cap, capx, OZ);
+        const uint8_t* __restrict__ mk8 = stage_mask(sb, cap, capx, FORM);
         const unsigned P = (unsigned)d->plane;
         const float2* __restrict__ sp = d->state + (size_t)lsrc * 7 * P;
 #pragma unroll
@@ -220,7 +276,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 const unsigned s = G.s0 + (unsigned)l;
                 if (mk & 4u) o[jj][0] = __ldg(sp + (size_t)3 * P + s);
                 if (mk & 8u) o[jj][1] = __ldg(sp + (size_t)4 * P + s);
-                if (!OZ) {
+                if (FORM == 0) {
                     if (mk & 16u) o[jj][2] = __ldg(sp + (size_t)5 * P + s);
                     if (mk & 32u) o[jj][3] = __ldg(sp + (size_t)6 * P + s);
                 }
@@ -234,7 +290,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     // lost copy would, and the warp takes the abort path below (the producer
     // keeps its normal bounds and drains its copies before the CTA exits).
     bool ok = a.test_wait_ns == 0 || mbar_wait(&never, 0u, a.test_wait_ns);
-    ok = ok && prefetch(0, own);
+    ok = ok && prefetch(0, 0, 0u, own);
 
     // constants of the current member, reloaded only when the member changes
     int cm = -1, nx = 1, ny = 1, nz = 1, bcx = 0, bcy = 0, bcz0 = 0, bcz1 = 0;
@@ -246,18 +302,25 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
     float fk = 0.f;            // the member's f_k
     bool do_sig = false, do_field = false;
     const MemberDesc* __restrict__ sd = a.members;
+    // z-marching: per site, this unit's +z pull value and own plane-6 value,
+    // carried from the previous unit of the column
+    float2 c5[TMA_SPT], c6[TMA_SPT];
 
-    for (long long i = 0;; ++i) {
-        const long long u = unit_of(i);
-        if (u >= n_units) break;
-        const int st = (int)(i % nst);
-        ok = ok && prefetch(i + 1, nown);
-        ok = ok && mbar_wait(&full[st], (uint32_t)((i / nst) & 1));
+    int st = 0, stn = 0;     // stage of unit i and of unit i + 1, and their fill parities
+    uint32_t ph = 0, phn = 0;
+    for (long long i = 0;; ++i, st = stn, ph = phn) {
+        if (!has_unit(i)) break;
+        const long long u = FORM == 2 ? 0 : unit_of(i);
+        stn = st + 1 == nst ? 0 : st + 1;
+        phn = stn == 0 ? ph ^ 1u : ph;
+        ok = ok && prefetch(i + 1, stn, phn, nown);
+        ok = ok && mbar_wait(&full[st], ph);
         if (!ok) {
             s_abort = 1;
             break;
         }
         const UnitGeo G = infos[st];
+        const long long uslot = FORM == 2 ? infos_us[st] : u;   // the unit's signal slots
         unsigned char* sb = smem + st * stb;
         if (G.m != cm) {
             cm = G.m;
@@ -284,10 +347,28 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
         const float2* __restrict__ r4 = stage_plane(sb, cap, 4);
         const float2* __restrict__ r5 = stage_plane(sb, cap, 5);
         const float2* __restrict__ r6 = stage_plane(sb, cap, 6);
-        const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx, OZ);
+        const uint8_t* __restrict__ rm = stage_mask(sb, cap, capx, FORM);
         const float2* __restrict__ fac = a.fac + ((size_t)k * a.n_members + G.m) * 6;
         float2* __restrict__ dst = dstb;
         const int z = G.z;
+        if (FORM == 2 && (z & (a.zc - 1)) == 0) {
+            // first unit of a column: the carried values from memory (the
+            // +z pull source as the other forms stage it, the own plane-6 value)
+            const float2* __restrict__ sp = sd->state + (size_t)lsrc * 7 * P;
+            const unsigned sxy = (unsigned)nx * ny;
+#pragma unroll
+            for (int j = 0; j < TMA_SPT; ++j) {
+                const int l0 = tid + j * TMA_CONSUMERS;
+                const int l = l0 < G.L ? l0 : 0;
+                const unsigned s = G.s0 + (unsigned)l;
+                const float2* p5;
+                if (z >= 1) p5 = sp + (size_t)5 * P + (s - sxy);
+                else if (bcz0 == BC_HALO || bcz0 == BC_HALO_PER) p5 = sd->halo[0] + (size_t)G.y0 * nx + l;
+                else p5 = bcz0 == BC_PER ? sp + (size_t)5 * P + s + (size_t)(nz - 1) * sxy : sp + (size_t)6 * P + s;
+                c5[j] = __ldg(p5);
+                c6[j] = __ldg(sp + (size_t)6 * P + s);
+            }
+        }
 
         // Phase 1, every site of this thread: pulls with the face transforms
         // and the half-link membrane rule.  Lanes past the unit's end work on
@@ -313,7 +394,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
             if (y == 0) g[j][3] = face_fix(g[j][3], bcy, __ldg(fac + 2));
             g[j][4] = r4[l];
             if (y == ny - 1) g[j][4] = face_fix(g[j][4], bcy, __ldg(fac + 3));
-            g[j][5] = r5[l];
+            g[j][5] = FORM == 2 ? c5[j] : r5[l];
             if (z == 0) g[j][5] = face_fix(g[j][5], bcz0, __ldg(fac + 4));
             g[j][6] = r6[l];
             if (z == nz - 1) g[j][6] = face_fix(g[j][6], bcz1, __ldg(fac + 5));
@@ -325,8 +406,14 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 if (mk & 1u) g[j][2] = mix(r1[l + 2], g[j][2], sh);      // link to +x: own hat g_1
                 if (mk & 8u) g[j][3] = mix(own[j][1], g[j][3], sh);      // link to -y: own hat g_4
                 if (mk & 4u) g[j][4] = mix(own[j][0], g[j][4], sh);      // link to +y: own hat g_3
-                if (mk & 32u) g[j][5] = mix(OZ ? stage_plane(sb, cap, 8)[l] : own[j][3], g[j][5], sh);   // -z: own hat g_6
-                if (mk & 16u) g[j][6] = mix(OZ ? stage_plane(sb, cap, 7)[l] : own[j][2], g[j][6], sh);   // +z: own hat g_5
+                if (mk & 32u)   // -z: own hat g_6
+                    g[j][5] = mix(FORM == 2 ? c6[j] : OZ ? stage_plane(sb, cap, 8)[l] : own[j][3], g[j][5], sh);
+                if (mk & 16u)   // +z: own hat g_5
+                    g[j][6] = mix(FORM == 2 ? r5[l] : OZ ? stage_plane(sb, cap, 7)[l] : own[j][2], g[j][6], sh);
+            }
+            if (FORM == 2) {   // carried to the next unit of the column (same rows, plane z + 1)
+                c5[j] = r5[l];
+                c6[j] = r6[l];
             }
             mks[j] = mk;
             xs[j] = x;
@@ -431,7 +518,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
                 dr += __shfl_down_sync(0xffffffffu, dr, o);
                 di += __shfl_down_sync(0xffffffffu, di, o);
             }
-            if (lane == 0) a.partial[u * (TMA_CONSUMERS / 32) + warp] = make_double2(dr, di);
+            if (lane == 0) a.partial[uslot * (TMA_CONSUMERS / 32) + warp] = make_double2(dr, di);
         }
     }
     if (s_abort && tid == 0) atomicOr(&a.ctl->err, 1);
@@ -439,7 +526,7 @@ __global__ void __launch_bounds__(TMA_CONSUMERS + 32, 1)
 
 }  // namespace
 
-size_t tma_smem_bytes(int cap, int capx, int nst, bool oz) { return stage_bytes(cap, capx, oz) * nst; }
+size_t tma_smem_bytes(int cap, int capx, int nst, int form) { return stage_bytes(cap, capx, form) * nst; }
 // signal partial slots per unit: one per consumer warp of the variant
 int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2 ? 8 : variant == 3 ? 11 : 16; }
 
@@ -448,53 +535,59 @@ int tma_partials_per_unit(int variant) { return variant == 1 ? 12 : variant == 2
 // sub-partitions: with the producer warp, 9 to 12 warps per CTA allow 168
 // registers a thread, 13 to 16 warps 128 and 17 warps 96; the two-phase
 // consumer needs about 150.  Each in two forms: with the own z rows staged
-// (oz) or prefetched into registers.
-template <bool OZ>
-static void* tma_kernel_oz(int variant)
+// (form 1), prefetched into registers (form 0), or z-marching (form 2).
+template <int FORM>
+static void* tma_kernel_form(int variant)
 {
     switch (variant) {
-    case 1: return (void*)sweep_tma_kernel<384, 3, OZ>;
-    case 2: return (void*)sweep_tma_kernel<256, 4, OZ>;
-    case 3: return (void*)sweep_tma_kernel<352, 3, OZ>;
-    default: return (void*)sweep_tma_kernel<512, 2, OZ>;
+    case 1: return (void*)sweep_tma_kernel<384, 3, FORM>;
+    case 2: return (void*)sweep_tma_kernel<256, 4, FORM>;
+    case 3: return (void*)sweep_tma_kernel<352, 3, FORM>;
+    default: return (void*)sweep_tma_kernel<512, 2, FORM>;
     }
 }
-static void* tma_kernel(int variant, bool oz) { return oz ? tma_kernel_oz<true>(variant) : tma_kernel_oz<false>(variant); }
+static void* tma_kernel(int variant, int form)
+{
+    return form == 2 ? tma_kernel_form<2>(variant) : form == 1 ? tma_kernel_form<1>(variant) : tma_kernel_form<0>(variant);
+}
 static int tma_threads(int variant)
 {
     return variant == 1 ? 384 + 32 : variant == 2 ? 256 + 32 : variant == 3 ? 352 + 32 : 512 + 32;
 }
 
-cudaError_t tma_prepare(int cap, int capx, int nst, int variant, bool oz, int* ctas_per_sm)
+cudaError_t tma_prepare(int cap, int capx, int nst, int variant, int form, int* ctas_per_sm)
 {
-    const size_t bytes = tma_smem_bytes(cap, capx, nst, oz);
-    void* fn = tma_kernel(variant, oz);
+    const size_t bytes = tma_smem_bytes(cap, capx, nst, form);
+    void* fn = tma_kernel(variant, form);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, tma_threads(variant), bytes);
 }
 
-template <bool OZ>
-static void launch_oz(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
-                      size_t sm, cudaStream_t st)
+template <int FORM>
+static void launch_form(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int grid,
+                        size_t sm, cudaStream_t st)
 {
     switch (variant) {
-    case 1: sweep_tma_kernel<384, 3, OZ><<<grid, 384 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    case 2: sweep_tma_kernel<256, 4, OZ><<<grid, 256 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    case 3: sweep_tma_kernel<352, 3, OZ><<<grid, 352 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
-    default: sweep_tma_kernel<512, 2, OZ><<<grid, 512 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 1: sweep_tma_kernel<384, 3, FORM><<<grid, 384 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 2: sweep_tma_kernel<256, 4, FORM><<<grid, 256 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    case 3: sweep_tma_kernel<352, 3, FORM><<<grid, 352 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
+    default: sweep_tma_kernel<512, 2, FORM><<<grid, 512 + 32, sm, st>>>(a, n_units, cap, capx, nst); break;
     }
 }
 
-cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, bool oz,
+cudaError_t launch_sweep_tma(const SweepArgs& a, long long n_units, int cap, int capx, int nst, int variant, int form,
                              int grid, cudaStream_t st)
 {
     if (nst < 2 || nst > TMA_MAX_STAGES) return cudaErrorInvalidValue;
-    const size_t sm = tma_smem_bytes(cap, capx, nst, oz);
-    if (oz)
-        launch_oz<true>(a, n_units, cap, capx, nst, variant, grid, sm, st);
+    if (form == 2 && (a.zc < 1 || a.cc_start == nullptr)) return cudaErrorInvalidValue;
+    const size_t sm = tma_smem_bytes(cap, capx, nst, form);
+    if (form == 2)
+        launch_form<2>(a, n_units, cap, capx, nst, variant, grid, sm, st);
+    else if (form == 1)
+        launch_form<1>(a, n_units, cap, capx, nst, variant, grid, sm, st);
     else
-        launch_oz<false>(a, n_units, cap, capx, nst, variant, grid, sm, st);
+        launch_form<0>(a, n_units, cap, capx, nst, variant, grid, sm, st);
     return cudaGetLastError();
 }
 

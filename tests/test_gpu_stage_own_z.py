@@ -1,15 +1,18 @@
-"""GPU: the two forms of the bulk-copy sweep for geometries with membranes --
-the own-site values of the z populations (needed at membrane links in z,
-Eq. B5) staged with the unit or prefetched into registers.  Both do the same
-arithmetic on the same values, so their fields must agree bit for bit, and
-each must match the FP64 oracle (S within 1e-5, field within 1e-4 of
-max|M|).  The automatic choice stages on large planes with membranes only."""
+"""GPU: the three forms of the bulk-copy sweep for geometries with membranes
+-- the own-site values of the z populations (needed at membrane links in z,
+Eq. B5) prefetched into registers (option 1), staged with the unit (2), or
+carried from unit to unit by z-marching columns (3).  All do the same
+arithmetic on the same values, so their fields and signals must agree bit
+for bit, and each must match the FP64 oracle (S within 1e-5, field within
+1e-4 of max|M|).  The automatic choice marches (or, where the grid gives
+too few columns, stages) on large planes with membranes only."""
 import math
 
 import numpy as np
 import pytest
 
 import oracle
+from paper_1907_00908_gb300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,17 +48,18 @@ def _run(lb, labels, pol, bc, D, T2, kap, dt, f, gG, oz):
                                      ((0, 1, 1), (1.0, 0.0, 0.0))])
 def test_forms_agree_and_match_oracle(lb, bc, gdir):
     rng = np.random.default_rng(21)
-    labels = rng.integers(0, 3, size=(7, 12, 32)).astype(np.int32)
+    labels = rng.integers(0, 3, size=(8, 12, 32)).astype(np.int32)   # z-marching: one column of 8 planes
     pol = np.array([0, 1, 2], np.uint8)
     D, T2, kap, dt = [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.05, 0.02
     gG, f = oracle.pgse(1500.0, 0.2, 0.4, dt, gdir)
     out = {}
-    for oz in (1, 2):
+    for oz in (1, 2, 3):
         r, fld, used = _run(lb, labels, pol, bc, D, T2, kap, dt, f, gG, oz)
         assert used == (2, oz)
         out[oz] = (r, fld)
-    assert np.array_equal(out[1][1], out[2][1])
-    assert out[1][0]["S"] == out[2][0]["S"]
+    for oz in (2, 3):
+        assert np.array_equal(out[1][1], out[oz][1])
+        assert out[1][0]["S"] == out[oz][0]["S"]
     o = oracle.run(labels, 0.5, pol, bc, D, T2, kap, dt, f, gG, want_field=True)
     assert abs(out[2][0]["S"] - o["S"]) <= 1e-5 * o["S"]
     assert np.abs(out[2][1] - o["field"]).max() < 1e-4 * np.abs(o["field"]).max()
@@ -86,10 +90,68 @@ def test_auto_stages_large_planes_with_membranes(lb):
     assert used == (2, 1)
 
 
+def test_auto_marches_tall_large_planes(lb):
+    """320 planes of 512 x 256 with membranes: enough columns of 8 planes for
+    the automatic choice to march; the same bits as the staging form."""
+    rng = np.random.default_rng(5)
+    nz, ny, nx = 320, 256, 512
+    labels = (rng.random((nz // 4, ny // 8, nx // 8)) < 0.4).astype(np.int32)
+    labels = np.repeat(np.repeat(np.repeat(labels, 4, axis=0), 8, axis=1), 8, axis=2)
+    pol = np.array([0, 1], np.uint8)
+    gG, f = oracle.pgse(1500.0, 0.04, 0.06, 0.02, (0.6, 0.8, 0.0))   # parallel to the mirror z faces
+    ra, fa, used = _run(lb, labels, pol, (0, 0, 1), [2.0, 1.0], [80.0, 50.0], 0.05, 0.02, f, gG, 0)
+    assert used == (2, 3)
+    rb, fb, used = _run(lb, labels, pol, (0, 0, 1), [2.0, 1.0], [80.0, 50.0], 0.05, 0.02, f, gG, 2)
+    assert used == (2, 2)
+    assert np.array_equal(fa, fb)
+    assert ra["S"] == rb["S"]
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
+def test_marching_batch_of_geometries(lb, bc):
+    """Columns over a batch: geometries of 32 and 48 planes (columns of 16
+    planes), members with their own directions and kappa, against the
+    prefetching form bit for bit and each member's oracle run."""
+    geoms = [synth.spheres(32, 0.5, rmin=1.5, rmax=3.0, fraction=0.4, seed=7),
+             synth.spheres(48, 0.5, rmin=2.0, rmax=4.0, fraction=0.45, seed=8)]
+    dt = 0.025
+    _, f = oracle.pgse(1000.0, 0.5, 1.0, dt, (1, 0, 0))
+    spec = [(0, 1200.0, (0.0, 0.0, 1.0), 0.02), (1, 2000.0, (0.0, 0.0, 1.0), 0.05), (1, 800.0, (0.0, 0.0, 1.0), 0.0)]
+    if bc == (0, 0, 0):
+        spec += [(0, 1500.0, (0.6, 0.0, 0.8), INF)]
+    gGs = [oracle.pgse(b, 0.5, 1.0, dt, d)[0] for _, b, d, _ in spec]
+    out = {}
+    for oz in (1, 3):
+        s = lb.Solver(0)
+        s.set_option(lb.OPT_KERNEL, 2)
+        s.set_option(lb.OPT_STAGE_OWN_Z, oz)
+        s.set_geometry(geoms[0].labels, geoms[0].phase_of_label, 0.5, bc)
+        s.add_geometry(geoms[1].labels, geoms[1].phase_of_label, 0.5, bc)
+        s.set_phases([2.0, 1.0], [80.0, 50.0])
+        s.set_sequence(dt, f, gGs[0])
+        mem = lb.Solver.members(gGs, [g for g, *_ in spec], [k for *_, k in spec])
+        flds = [torch.zeros(geoms[g].n_sites, dtype=torch.complex64, device="cuda") for g, *_ in spec]
+        r = s.run_batch(mem, fields=flds)
+        torch.cuda.synchronize()
+        assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == oz
+        s.close()
+        out[oz] = (r, [fl.cpu().numpy() for fl in flds])
+    for i, (gi, _, _, kap) in enumerate(spec):
+        assert np.array_equal(out[1][1][i], out[3][1][i]), i
+        assert out[1][0]["S"][i] == out[3][0]["S"][i], i
+        g = geoms[gi]
+        o = oracle.run(g.labels, g.dx, g.phase_of_label, bc, [2.0, 1.0], [80.0, 50.0], kap, dt, f, gGs[i],
+                       want_field=True)
+        assert abs(out[3][0]["S"][i] - o["S"]) <= 1e-5 * o["S"], i
+        assert np.abs(out[3][1][i].reshape(g.labels.shape) - o["field"]).max() < 1e-4 * np.abs(o["field"]).max()
+
+
 def test_option_range(lb):
     s = lb.Solver(0)
     with pytest.raises(lb.LbmbtError):
-        s.set_option(lb.OPT_STAGE_OWN_Z, 3)
+        s.set_option(lb.OPT_STAGE_OWN_Z, 4)
+    with pytest.raises(lb.LbmbtError):
+        s.set_option(lb.OPT_STAGE_OWN_Z, -1)
     assert s.get_option(lb.OPT_STAGE_OWN_Z) == 0
     assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == 0
     s.close()
