@@ -357,6 +357,7 @@ def measure_batch(args, stream):
     t_gen = time.perf_counter() - t0
     s = lbmbt.Solver(0, stream)
     s.set_option(lbmbt.OPT_STAGE_OWN_Z, args.stage_own_z)
+    s.set_option(lbmbt.OPT_COLUMN_PLANES, args.column_planes)
     s.set_option(lbmbt.OPT_AUTOTUNE, 0 if args.no_autotune else 1)
     s.set_geometry(cyl.labels, cyl.phase_of_label, 0.5)
     for g in packs:
@@ -851,6 +852,8 @@ def main():
     ap.add_argument("--stage-own-z", type=int, default=0, choices=[0, 1, 2, 3],
                     help="bulk-copy sweep: own z values 0 auto, 1 prefetched into registers, 2 staged, "
                          "3 z-marching columns")
+    ap.add_argument("--column-planes", type=int, default=0,
+                    help="bulk-copy sweep, z-marching form: planes per column (0 auto, else a power of two)")
     ap.add_argument("--members", type=int, default=60, help="adjoint workload: number of members (<= 60)")
     ap.add_argument("--adj-steps", type=int, default=400,
                     help="adjoint workload: steps of the 6400-step schedule timed (the prefix)")
@@ -922,6 +925,7 @@ def main():
 
     s = lbmbt.Solver(local, stream)
     s.set_option(lbmbt.OPT_STAGE_OWN_Z, args.stage_own_z)
+    s.set_option(lbmbt.OPT_COLUMN_PLANES, args.column_planes)
     if not args.no_autotune:
         s.set_option(lbmbt.OPT_AUTOTUNE, 1)
     if args.block:

@@ -373,7 +373,16 @@ enum {
                                 control's error word after its producer has
                                 waited (bounded) for its own copies in
                                 flight, and the call returns LBMBT_EDEVICE.
-                                The context stays usable                  */
+                                The context stays usable                  */,
+    LBMBT_OPT_COLUMN_PLANES = 17, /* bulk-copy sweep, z-marching form: planes
+                                per column.  0 (default) auto: the longest
+                                power of two <= 32 that divides every
+                                member's nz and leaves >= 32 columns per SM
+                                (for a forced z-marching run without one,
+                                the longest that divides them).  1, 2, 4,
+                                .., 64: that length; the run fails with
+                                LBMBT_EINVAL when it does not divide every
+                                member's nz                                  */
 };
 int lbmbt_set_option(lbmbt_ctx* ctx, int option, int64_t value);
 int lbmbt_get_option(lbmbt_ctx* ctx, int option, int64_t* value);

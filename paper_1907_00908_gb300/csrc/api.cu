@@ -98,6 +98,7 @@ struct lbmbt_ctx {
     int tma_form = 0;             // own z values: 0 prefetched, 1 staged, 2 z-marching columns
     int oz_opt = 0;               // 0 auto, 1 prefetch, 2 stage, 3 z-marching
     int tma_zc = 0;               // z-marching: units per column
+    int zc_opt = 0;               // z-marching column length: 0 auto, else a power of two
     long long n_cc = 0;           // z-marching: columns of all members
     std::vector<long long> cc_start;
     long long* d_cc_start = nullptr;
@@ -737,6 +738,11 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
                 if (gz % t == 0) zc = t;
         c->tma_form = c->oz_opt == 1 ? 0 : c->oz_opt == 2 ? 1 : c->oz_opt == 3 ? 2
                       : !large ? 0 : zc >= 8 ? 2 : 1;
+        if (c->tma_form == 2 && c->zc_opt) {   // a column length set by the caller
+            if (gz % c->zc_opt != 0)
+                return fail(c, LBMBT_EINVAL, "column of %d planes does not divide every member's nz", c->zc_opt);
+            zc = c->zc_opt;
+        }
         c->tma_zc = c->tma_form == 2 ? zc : 0;
         c->n_cc = 0;
         c->cc_start.assign(c->n_members + 1, 0);
@@ -1487,6 +1493,11 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
         if (v < 0 || v > 1000000000LL) return fail(c, LBMBT_EINVAL, "test wait must be 0 (off) .. 1e9 ns");
         c->test_wait_ns = v;
         break;
+    case LBMBT_OPT_COLUMN_PLANES:
+        if (v < 0 || v > 64 || (v & (v - 1)) != 0)
+            return fail(c, LBMBT_EINVAL, "column planes must be 0 (auto) or a power of two <= 64");
+        c->zc_opt = (int)v;
+        break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);
     }
     invalidate_run(c);
@@ -1511,6 +1522,7 @@ extern "C" int lbmbt_get_option(lbmbt_ctx* c, int opt, int64_t* v)
     case LBMBT_OPT_SCHEME: *v = c->scheme; break;
     case LBMBT_OPT_GRAD_GROUPS: *v = c->grad_groups; break;
     case LBMBT_OPT_TEST_WAIT_NS: *v = c->test_wait_ns; break;
+    case LBMBT_OPT_COLUMN_PLANES: *v = c->zc_opt; break;
     case LBMBT_OPT_STAGE_OWN_Z_USED: *v = c->prepared && c->use_tma ? c->tma_form + 1 : 0; break;
     case LBMBT_OPT_KERNEL_USED: *v = c->prepared ? (c->use_tma ? 2 : 1) : 0; break;
     default: return fail(c, LBMBT_EINVAL, "unknown option %d", opt);

@@ -26,6 +26,7 @@ FACE_OWN, FACE_HALO, FACE_HALO_WRAP = 0, 1, 2
 OPT_GRAPH, OPT_AUTOTUNE, OPT_BLOCK, OPT_SPT, OPT_KERNEL, OPT_KERNEL_USED, OPT_STAGES, OPT_TMA_SHAPE = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_ADJOINT_KERNEL, OPT_ADJOINT_SHAPE, OPT_LATTICE = 9, 10, 11
 OPT_STAGE_OWN_Z, OPT_STAGE_OWN_Z_USED, OPT_SCHEME, OPT_GRAD_GROUPS, OPT_TEST_WAIT_NS = 12, 13, 14, 15, 16
+OPT_COLUMN_PLANES = 17
 
 # every entry point declared in include/lbmbt.h
 EXPORTS = [

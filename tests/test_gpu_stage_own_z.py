@@ -146,6 +146,46 @@ def test_marching_batch_of_geometries(lb, bc):
         assert np.abs(out[3][1][i].reshape(g.labels.shape) - o["field"]).max() < 1e-4 * np.abs(o["field"]).max()
 
 
+def test_column_planes_option(lb):
+    """Columns of 1, 2 and 4 of the 8 planes give the same bits as the
+    prefetching form; a length that does not divide nz is refused."""
+    rng = np.random.default_rng(23)
+    labels = rng.integers(0, 3, size=(8, 12, 32)).astype(np.int32)
+    pol = np.array([0, 1, 2], np.uint8)
+    args = ([2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.05, 0.02)
+    gG, f = oracle.pgse(1500.0, 0.2, 0.4, 0.02, (0.3, -0.5, 0.81))
+    _, ref, _ = _run(lb, labels, pol, (0, 0, 0), *args, f, gG, 1)
+    for zc in (1, 2, 4):
+        s = lb.Solver(0)
+        s.set_option(lb.OPT_KERNEL, 2)
+        s.set_option(lb.OPT_STAGE_OWN_Z, 3)
+        s.set_option(lb.OPT_COLUMN_PLANES, zc)
+        s.set_geometry(labels, pol, 0.5, (0, 0, 0))
+        s.set_phases(args[0], args[1])
+        s.set_permeability(args[2])
+        s.set_sequence(args[3], f, gG)
+        fld = torch.zeros(labels.size, dtype=torch.complex64, device="cuda")
+        s.run(field=fld)
+        torch.cuda.synchronize()
+        assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == 3
+        s.close()
+        assert np.array_equal(fld.cpu().numpy().reshape(labels.shape), ref), zc
+    s = lb.Solver(0)
+    for bad in (-1, 3, 128):
+        with pytest.raises(lb.LbmbtError):
+            s.set_option(lb.OPT_COLUMN_PLANES, bad)
+    s.set_option(lb.OPT_KERNEL, 2)
+    s.set_option(lb.OPT_STAGE_OWN_Z, 3)
+    s.set_option(lb.OPT_COLUMN_PLANES, 16)
+    s.set_geometry(labels, pol, 0.5, (0, 0, 0))
+    s.set_phases(args[0], args[1])
+    s.set_sequence(args[3], f, gG)
+    with pytest.raises(lb.LbmbtError) as e:
+        s.run()
+    assert e.value.code == -1
+    s.close()
+
+
 def test_option_range(lb):
     s = lb.Solver(0)
     with pytest.raises(lb.LbmbtError):
