@@ -104,7 +104,8 @@ struct lbmbt_ctx {
     long long* d_cc_start = nullptr;
     size_t cap_cc = 0;
     int tuned_kernel = 0;         // 0: untuned, 1 register, 2 bulk copy (auto follows it)
-    struct Tuned { int kernel, block, spt, variant, stages; };
+    int tuned_oz = 0;             // 0: untuned, else the own-z form the tuner chose (2 staged, 3 z-marching)
+    struct Tuned { int kernel, block, spt, variant, stages, oz; };
     std::map<std::string, Tuned> tune_cache;
     int tma_grid = 0;
     int sm_count = 0;
@@ -736,8 +737,9 @@ static int build_worklist(lbmbt_ctx* c, int block, int spt)
         if (c->oz_opt == 3 && !zc)
             for (int t = 32; t >= 1 && !zc; t >>= 1)
                 if (gz % t == 0) zc = t;
-        c->tma_form = c->oz_opt == 1 ? 0 : c->oz_opt == 2 ? 1 : c->oz_opt == 3 ? 2
-                      : !large ? 0 : zc >= 8 ? 2 : 1;
+        // the caller's choice, else the tuner's (large planes), else the rule
+        const int ozo = c->oz_opt != 0 ? c->oz_opt : large ? c->tuned_oz : 0;
+        c->tma_form = ozo == 1 ? 0 : ozo == 2 ? 1 : ozo == 3 ? 2 : !large ? 0 : zc >= 8 ? 2 : 1;
         if (c->tma_form == 2 && c->zc_opt) {   // a column length set by the caller
             if (gz % c->zc_opt != 0)
                 return fail(c, LBMBT_EINVAL, "column of %d planes does not divide every member's nz", c->zc_opt);
@@ -908,29 +910,39 @@ static int autotune(lbmbt_ctx* c)
     for (auto& d : c->descs) key += "/" + std::to_string(d.nx) + "x" + std::to_string(d.ny) + "x" + std::to_string(d.nz);
     auto it = c->tune_cache.find(key);
     if (it == c->tune_cache.end()) {
-        struct Cand { int kernel, block, spt, variant, stages; };
+        struct Cand { int kernel, block, spt, variant, stages, oz; };
         std::vector<Cand> cand;
         if (c->kernel_opt != 2)
             for (auto bs : {std::make_pair(128, 1), std::make_pair(256, 1), std::make_pair(512, 1),
                             std::make_pair(128, 2), std::make_pair(256, 2), std::make_pair(512, 2),
                             std::make_pair(128, 4), std::make_pair(256, 4)})
-                cand.push_back({1, bs.first, bs.second, c->tma_variant, c->tma_stages});
+                cand.push_back({1, bs.first, bs.second, c->tma_variant, c->tma_stages, c->oz_opt});
+        // on large planes with membranes the staging and the z-marching forms
+        // are both timed (which is faster varies from GPU to GPU by a few %)
+        bool large = false;
+        for (auto& d : c->descs)
+            if (d.memb && (long long)d.nx * d.ny >= TMA_OZ_PLANE) large = true;
+        std::vector<int> forms;
+        if (c->oz_opt == 0 && large) forms = {2, 3};
+        else forms = {c->oz_opt};
         if (c->kernel_opt != 1 && tma_eligible(c))
-            for (int v = 0; v < 4; ++v)
-                for (int st = 2; st <= 4; ++st) cand.push_back({2, c->block, c->spt, v, st});
+            for (int oz : forms)
+                for (int v = 0; v < 4; ++v)
+                    for (int st = 2; st <= 4; ++st) cand.push_back({2, c->block, c->spt, v, st, oz});
         const int saved_opt = c->kernel_opt, saved_block = c->block, saved_spt = c->spt;
-        const int saved_var = c->tma_variant, saved_st = c->tma_stages;
+        const int saved_var = c->tma_variant, saved_st = c->tma_stages, saved_oz = c->oz_opt;
         const bool saved_series = c->series_mode;
         c->series_mode = false;
         cudaEvent_t e0, e1;
         CU(c, cudaEventCreate(&e0));
         CU(c, cudaEventCreate(&e1));
         float best = 1e30f;
-        Cand win = {0, saved_block, saved_spt, saved_var, saved_st};
+        Cand win = {0, saved_block, saved_spt, saved_var, saved_st, 0};
         for (const Cand& cd : cand) {
             c->kernel_opt = cd.kernel;
             c->tma_variant = cd.variant;
             c->tma_stages = cd.stages;
+            c->oz_opt = cd.oz;
             if (build_worklist(c, cd.block, cd.spt) != LBMBT_OK) {  // e.g. stages do not fit
                 c->err.clear();
                 cudaGetLastError();
@@ -966,11 +978,14 @@ static int autotune(lbmbt_ctx* c)
         c->spt = saved_spt;
         c->tma_variant = saved_var;
         c->tma_stages = saved_st;
+        c->oz_opt = saved_oz;
         c->series_mode = saved_series;
-        it = c->tune_cache.emplace(key, lbmbt_ctx::Tuned{win.kernel, win.block, win.spt, win.variant, win.stages}).first;
+        it = c->tune_cache.emplace(key, lbmbt_ctx::Tuned{win.kernel, win.block, win.spt, win.variant, win.stages,
+                                                         win.kernel == 2 ? win.oz : 0}).first;
     }
     const lbmbt_ctx::Tuned& t = it->second;
     c->tuned_kernel = t.kernel;
+    c->tuned_oz = t.oz;
     c->block = t.block;
     c->spt = t.spt;
     c->tma_variant = t.variant;
@@ -1446,7 +1461,7 @@ extern "C" int lbmbt_set_option(lbmbt_ctx* c, int opt, int64_t v)
     case LBMBT_OPT_GRAPH: c->use_graph = v != 0; break;
     case LBMBT_OPT_AUTOTUNE:
         c->autotune = v != 0;
-        if (!c->autotune) c->tuned_kernel = 0;
+        if (!c->autotune) c->tuned_kernel = c->tuned_oz = 0;
         break;
     case LBMBT_OPT_BLOCK:
         if (v < 64 || v > 512 || (v & 31)) return fail(c, LBMBT_EINVAL, "block must be a multiple of 32 in 64..512");
