@@ -123,17 +123,19 @@ def links_traffic_per_launch(n):
     return j["dram_bytes_read"] + j["dram_bytes_write"]
 
 
-def traffic_per_launch(site_updates):
-    """DRAM bytes per sweep launch of `site_updates` site-member updates,
-    from the bytes per update in the committed ncu summary, or None when the
-    kernel source changed since it was captured."""
+def traffic_per_launch(site_updates, form):
+    """DRAM bytes per sweep launch of `site_updates` site-member updates in
+    the own-z form `form` ("z-marching", "staged", "prefetched"), from the
+    bytes per update in the committed ncu summary, or None when the kernel
+    source changed since it was captured or the form was not captured."""
     p = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
     if j.get("source_hash") != sweep_source_hash():
         return None
-    return float(j["bytes_per_site_member"]) * site_updates
+    f = j.get("by_form", {}).get(form)
+    return None if f is None else float(f["bytes_per_site_member"]) * site_updates
 
 
 class Clocks:
@@ -1012,7 +1014,7 @@ def main():
             extras["adjoint_full_schedule"] = measure_adjoint(args, stream, None)
 
     if rank == 0:
-        tr = traffic_per_launch(n_sites * nm)
+        tr = traffic_per_launch(n_sites * nm, shape["own_z"])
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -1030,9 +1032,11 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tr, "peak_source": peak_kind,
                          "traffic_gbs": tr / per_launch_s / 1e9 if tr is not None else None,
-                         "traffic_source": "ncu DRAM bytes on the tissue's first 128 planes, scaled by site updates "
-                                           "(profiles/sweep_traffic.json); bytes per update rise with the planes, so "
-                                           "a lower bound for the full grid" if tr is not None else None,
+                         "traffic_source": ("ncu DRAM bytes of the " + str(shape["own_z"]) + " form on the tissue's "
+                                            "first 128 planes, scaled by site updates (profiles/sweep_traffic.json)"
+                                            + ("" if shape["own_z"] == "z-marching" else
+                                               "; bytes per update rise with the planes, so a lower bound for "
+                                               "the full grid")) if tr is not None else None,
                          "bytes_per_site_member": BYTES_PER_SITE, "kernel": "sweep_tma_kernel"},
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -53,12 +53,16 @@ def test_traffic_lookup_follows_the_hash(tmp_path, monkeypatch):
     root = _tree(tmp_path, files)
     monkeypatch.setattr(bench, "ROOT", root)
     os.makedirs(os.path.join(root, "profiles"))
-    rec = {"source_hash": bench.sweep_source_hash(), "bytes_per_site_member": 120.0}
+    rec = {"source_hash": bench.sweep_source_hash(),
+           "by_form": {"z-marching": {"bytes_per_site_member": 113.5}, "staged": {"bytes_per_site_member": 120.0}}}
     with open(os.path.join(root, "profiles", "sweep_traffic.json"), "w") as fh:
         json.dump(rec, fh)
-    assert bench.traffic_per_launch(bench.N_EDGE ** 3 * 3) == 120.0 * bench.N_EDGE ** 3 * 3
+    n = bench.N_EDGE ** 3 * 3
+    assert bench.traffic_per_launch(n, "staged") == 120.0 * n
+    assert bench.traffic_per_launch(n, "z-marching") == 113.5 * n
+    assert bench.traffic_per_launch(n, "prefetched") is None    # not captured
     (tmp_path / "paper_1907_00908_gb300" / "csrc" / "sweep_tma.cu").write_text(SRC.replace("1.f", "3.f"))
-    assert bench.traffic_per_launch(1000) is None
+    assert bench.traffic_per_launch(1000, "staged") is None
 
 
 def test_phase_fractions_of_a_known_geometry():
