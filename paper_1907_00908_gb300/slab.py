@@ -73,7 +73,7 @@ class SlabGroup:
     """``n_slabs`` slabs of one grid on one GPU, one context each, one stream."""
 
     def __init__(self, labels, phase_of_label, dx, bc, n_slabs, D, T2, dt, f, members, stream, kernel=0,
-                 field=False):
+                 field=False, options=None):
         import torch
         labels = np.ascontiguousarray(labels, np.int32)
         nz, ny, nx = labels.shape
@@ -92,6 +92,8 @@ class SlabGroup:
             s = lbmbt.Solver(torch.cuda.current_device(), stream)
             if kernel:
                 s.set_option(lbmbt.OPT_KERNEL, kernel)
+            for opt, val in (options or {}).items():   # further per-context options
+                s.set_option(opt, val)
             lo, hi = face_kinds(z0, z1, nz, bc[2])
             s.set_geometry_slab(ghost_labels(labels, z0, z1, bc[2]), phase_of_label, dx, bc, z0, nz, lo, hi)
             s.set_phases(D, T2)

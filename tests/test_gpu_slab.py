@@ -55,14 +55,16 @@ def _whole(lb, geom, bc, D, T2, kap, dt, f, gG, kernel):
     return r, fld.cpu().numpy()
 
 
-def _slabs(lb, geom, bc, D, T2, kap, dt, f, gG, kernel, n_slabs):
+def _slabs(lb, geom, bc, D, T2, kap, dt, f, gG, kernel, n_slabs, options=None):
     mem = lb.Solver.members([gG], 0, kap)
     g = slab.SlabGroup(geom.labels, geom.phase_of_label, geom.dx, bc, n_slabs, D, T2, dt, f, mem,
-                       torch.cuda.current_stream(), kernel=kernel, field=True)
+                       torch.cuda.current_stream(), kernel=kernel, field=True, options=options)
     r = g.run(len(f))
     fld = g.field().cpu().numpy()
     for s in g.solvers:
         assert s.get_option(lb.OPT_KERNEL_USED) == kernel
+        if options and lb.OPT_STAGE_OWN_Z in options:
+            assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == options[lb.OPT_STAGE_OWN_Z]
     g.close()
     return r, fld
 
@@ -93,6 +95,22 @@ def test_slabs_match_whole_grid_bit_for_bit(lb, name, kernel):
         if n_slabs == 1 and c["bc"][2] == 1:
             continue   # a mirror grid in one piece is a plain geometry
         r, fld = _slabs(lb, geom, c["bc"], D, T2, kap, dt, f, gG, kernel, n_slabs)
+        assert np.array_equal(fld, ref_fld), (name, n_slabs)
+        assert abs(r["Z"][0] - ref["Z"]) <= 1e-7 * abs(ref["Z"]), (name, n_slabs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_marching_slabs_match_whole_grid_bit_for_bit(lb, name):
+    """The bulk-copy sweep's z-marching form on slabs: a column that starts
+    at a cut takes its +z pull from the halo plane (2 slabs of 16 planes
+    march in columns of 16), and the fields equal the whole grid's."""
+    c = CASES[name]
+    geom = _labels(c["kind"], c["n"])
+    D, T2, kap, dt = [2.0, 1.0, 1.5], [80.0, 50.0, 60.0], 0.04, 0.02
+    gG, f = oracle.pgse(1500.0, 0.3, 0.5, dt, c["d"])
+    ref, ref_fld = _whole(lb, geom, c["bc"], D, T2, kap, dt, f, gG, 2)
+    for n_slabs in (2, 3):
+        r, fld = _slabs(lb, geom, c["bc"], D, T2, kap, dt, f, gG, 2, n_slabs, {lb.OPT_STAGE_OWN_Z: 3})
         assert np.array_equal(fld, ref_fld), (name, n_slabs)
         assert abs(r["Z"][0] - ref["Z"]) <= 1e-7 * abs(ref["Z"]), (name, n_slabs)
 
