@@ -127,6 +127,35 @@ def test_classical_launch_shapes_and_ragged_tails(lb, block, spt):
     np.testing.assert_allclose(ser, o["series"], rtol=0, atol=S_TOL * np.abs(o["series"]).max())
 
 
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
+def test_classical_own_z_forms_agree(lb, bc):
+    """The classical pass on the bulk-copy sweep in its three own-z forms
+    (prefetched, staged, z-marching): the same bits, and the oracle."""
+    geom = synth.crop(synth.voronoi_tissue(48, 0.5, cell_diam=6.0, vessel_radius=1.5, seed=8), 32)
+    D, T2, kap, dt = [2.0, 1.0, 3.0], [80.0, 50.0, 80.0], 0.02, 0.05
+    gG, f = oracle.pgse(1500.0, 2.0, 5.0, dt, (0, 0, 1))
+    out = {}
+    for oz in (1, 2, 3):
+        s = lb.Solver(0)
+        s.set_option(lb.OPT_SCHEME, 1)
+        s.set_option(lb.OPT_KERNEL, 2)
+        s.set_option(lb.OPT_STAGE_OWN_Z, oz)
+        s.set_geometry(geom.labels, geom.phase_of_label, geom.dx, bc)
+        s.set_phases(D, T2)
+        s.set_permeability(kap)
+        s.set_sequence(dt, f, gG)
+        fld = torch.zeros(geom.n_sites, dtype=torch.complex64, device="cuda")
+        r = s.run(field=fld)
+        torch.cuda.synchronize()
+        assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == oz
+        s.close()
+        out[oz] = (r, fld.cpu().numpy().reshape(geom.labels.shape))
+    for oz in (2, 3):
+        assert np.array_equal(out[1][1], out[oz][1]), oz
+        assert out[1][0]["S"] == out[oz][0]["S"], oz
+    _check(out[3][0], out[3][1], _oracle(geom, bc, D, T2, kap, dt, f, gG))
+
+
 def test_classical_equals_hybrid_bitwise_without_gradient_and_t2(lb):
     """R = 0: the source adds exact zeros, so the classical pass gives the
     hybrid pass's field bit for bit (both on the register sweep)."""
