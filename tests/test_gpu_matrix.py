@@ -98,6 +98,9 @@ def test_random_configuration_matches_oracle(lb, seed):
     if kernel == 2 and not tma_ok:
         kernel = 1
     s.set_option(lb.OPT_KERNEL, kernel)
+    # the bulk-copy sweep's own-z form, drawn apart so the configurations stay as they were
+    own_z = int(np.random.default_rng(1000 + seed).integers(0, 4)) if kernel == 2 else 0
+    s.set_option(lb.OPT_STAGE_OWN_Z, own_z)
     s.set_geometry(c["lab"], c["pol"], 0.5, c["bc"])
     if c["dl"] is not None:
         s.set_link_distances(c["dl"])
@@ -111,6 +114,8 @@ def test_random_configuration_matches_oracle(lb, seed):
     fld = torch.zeros(n, dtype=torch.complex64, device="cuda")
     r = s.run(field=fld)
     torch.cuda.synchronize()
+    if own_z:
+        assert s.get_option(lb.OPT_STAGE_OWN_Z_USED) == own_z
     s.close()
     o = oracle.run(c["lab"], 0.5, c["pol"], c["bc"], c["D"], c["T2"], c["kap"], c["dt"], c["f"], c["gG"],
                    want_field=True, delta=None if c["dl"] is None else c["dl"].astype(np.float64),
@@ -181,6 +186,7 @@ def test_random_classical_configuration_matches_oracle(lb, seed):
     if kernel == 2 and not (c["shape"][2] % 16 == 0 and not c["d2q5"]):
         kernel = 1
     s.set_option(lb.OPT_KERNEL, kernel)
+    s.set_option(lb.OPT_STAGE_OWN_Z, int(np.random.default_rng(2000 + seed).integers(0, 4)) if kernel == 2 else 0)
     s.set_geometry(c["lab"], c["pol"], 0.5, c["bc"])
     s.set_phases(c["D"], c["T2"])
     s.set_permeability(c["kap"])
