@@ -433,6 +433,7 @@ def measure_adjoint(args, stream, K=None):
     s.set_phases(C2_D, C2_T2)
     s.set_sequence(C2_DT, f, gGs[0])
     s.set_option(lbmbt.OPT_ADJOINT_SHAPE, args.adj_shape)
+    s.set_option(lbmbt.OPT_ADJOINT_KERNEL, args.adjoint_kernel)
     mem = lbmbt.Solver.members(gGs, 0, C2_KAPPA)
     warm = mem if K < 6400 else lbmbt.Solver.members(gGs[:2], 0, C2_KAPPA)
     s.grad_batch(warm, checkpoint_every=64)   # warm-up
@@ -851,6 +852,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--adj-shape", type=int, default=2, help="bulk-copy adjoint consumer shape (0, 1 or 2)")
+    ap.add_argument("--adjoint-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="adjoint sweep: 0 auto, 1 register, 2 bulk copy")
     ap.add_argument("--stage-own-z", type=int, default=0, choices=[0, 1, 2, 3],
                     help="bulk-copy sweep: own z values 0 auto, 1 prefetched into registers, 2 staged, "
                          "3 z-marching columns")

@@ -1657,6 +1657,10 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
     CU(c, cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * NGACC * n_gslots, c->stream));
     int adj_grid = 0;
     const int adj_stages = 3;
+    // register adjoint: runs of up to 16 tiles per block, keeping >= 32
+    // blocks per SM
+    if (!c->sm_count) CU(c, cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    const int adj_run = (int)std::max<long long>(1, std::min<long long>(16, c->n_tiles / (32LL * c->sm_count)));
     if (adj_tma) {
         int per_sm = 0;
         CU(c, adj_tma_prepare(c->adj_cap, adj_stages, c->adj_shape_used, &per_sm));
@@ -1703,7 +1707,7 @@ static int grad_group(lbmbt_ctx* c, int n, const lbmbt_member* mem, int ck, doub
             if (adj_tma)
                 CU(c, launch_adjoint_tma(aa, c->n_adj_units, c->adj_cap, adj_stages, c->adj_shape_used, adj_grid,
                                          c->stream));
-            else CU(c, launch_adjoint(aa, c->n_tiles, c->tile_block, c->tile_spt, c->stream));
+            else CU(c, launch_adjoint(aa, c->n_tiles, c->tile_block, c->tile_spt, adj_run, c->stream));
             c->launches++;
             parity ^= 1;
         }

@@ -191,7 +191,8 @@ struct AdjointArgs {
     float w0, wxy, wz;            // equilibrium weights (register adjoint; the
                                   // bulk-copy adjoint has the D3Q7 ones built in)
 };
-cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, int spt, cudaStream_t st);
+// run: consecutive tiles per block (the block keeps its gradient partials over them)
+cudaError_t launch_adjoint(const AdjointArgs& a, long long n_tiles, int block, int spt, int run, cudaStream_t st);
 // Sums gacc slots [tile_start[m]*per, tile_start[m+1]*per) per member.
 cudaError_t launch_reduce_grad(const double* gacc, const long long* tile_start, int per, int n_members, double* out,
                                cudaStream_t st);
