@@ -115,8 +115,11 @@ __global__ void init_kernel(const MemberDesc* __restrict__ members, const long l
 // out one per lane, so the rule's loads and coefficients run once per link
 // instead of once per direction for the whole warp.  One list covers all SPT
 // sites of the warp's threads.  Per warp: SPT * LINK_SLOTS results (float2)
-// and as many items (site << 8 | lane << 3 | direction, 16 bits).
-constexpr int LINK_SLOTS = 32 * 6;
+// and as many items (site << 8 | lane << 3 | direction, 16 bits).  A site
+// lists at most 3 links, one per axis: direction i needs a membrane on the
+// link behind it and none on the link ahead, so i and its opposite exclude
+// each other.
+constexpr int LINK_SLOTS = 32 * 3;
 inline size_t link_smem_bytes(int block, int spt)
 {
     return (size_t)(block / 32) * spt * LINK_SLOTS * (sizeof(float2) + sizeof(uint16_t));
