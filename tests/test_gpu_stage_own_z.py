@@ -107,6 +107,33 @@ def test_auto_marches_tall_large_planes(lb):
     assert ra["S"] == rb["S"]
 
 
+def test_tuner_picks_staging_or_marching_on_large_planes(lb):
+    """With the autotuner on, a grid of large planes with membranes runs in
+    whichever of the staging and z-marching forms timed faster, with the
+    prefetching form's bits."""
+    rng = np.random.default_rng(5)
+    nz, ny, nx = 64, 256, 512
+    labels = (rng.random((nz // 4, ny // 8, nx // 8)) < 0.4).astype(np.int32)
+    labels = np.repeat(np.repeat(np.repeat(labels, 4, axis=0), 8, axis=1), 8, axis=2)
+    pol = np.array([0, 1], np.uint8)
+    gG, f = oracle.pgse(1500.0, 0.04, 0.06, 0.02, (0.6, 0.8, 0.0))
+    args = (labels, pol, (0, 0, 1), [2.0, 1.0], [80.0, 50.0], 0.05, 0.02, f, gG)
+    _, ref, _ = _run(lb, *args, 1)
+    s = lb.Solver(0)
+    s.set_option(lb.OPT_AUTOTUNE, 1)
+    s.set_geometry(labels, pol, 0.5, (0, 0, 1))
+    s.set_phases([2.0, 1.0], [80.0, 50.0])
+    s.set_permeability(0.05)
+    s.set_sequence(0.02, f, gG)
+    fld = torch.zeros(labels.size, dtype=torch.complex64, device="cuda")
+    s.run(field=fld)
+    torch.cuda.synchronize()
+    used = (s.get_option(lb.OPT_KERNEL_USED), s.get_option(lb.OPT_STAGE_OWN_Z_USED))
+    s.close()
+    assert used in ((2, 2), (2, 3), (1, 0)), used   # the register sweep may win on a short schedule
+    assert np.array_equal(fld.cpu().numpy().reshape(labels.shape), ref)
+
+
 @pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
 def test_marching_batch_of_geometries(lb, bc):
     """Columns over a batch: geometries of 32 and 48 planes (columns of 16
